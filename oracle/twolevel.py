@@ -1,0 +1,442 @@
+"""Spatiotemporal two-level method (Algorithm 1, Section 4), FP64 oracle.
+
+Test infrastructure only (see the package docstring).
+
+Problem (Section 2.1, Eq. thermalEqn, without latent heat): plate
+[0,Lx]x[0,Ly]x[0,Lz], Dirichlet T_bottom on z = 0, adiabatic elsewhere, a
+laser flux on the top surface z = Lz.  Material: rho constant,
+c(T) = c0 + c1 (T - Tref), k(T) = k0 + k1 (T - Tref); powder elements use
+powder_factor * k.
+
+Two levels (Section 3, Eqs. localProblem and globalPbmAlternate):
+  global (coarse) mesh of NXc x NYc x NZc hexes over the plate;
+  local (fine) patch of pNXc x pNYc x pNZc coarse hexes at the top surface,
+  each refined r times per direction, origin on a coarse node, following the
+  laser (Section 5.2: the local mesh moves, no projection).
+
+One macro step t_n -> t_n + Dt (Algorithm 1), this oracle's reading:
+  1. Patch motion: origin = clamp(floor((x_l - patch_len/2)/h_c + 0.5)) for
+     the laser position x_l at t_n + Dt/2 (kept if the laser is off then).
+     Fine nodes inside the old patch keep their values; new nodes get the
+     trilinear interpolant of the current coarse field.
+  2. Predictor: one backward-Euler step of size Dt on the coarse mesh from
+     T+^n -> T~+ (coefficients at T+^n, coarse source over [t_n, t_n+Dt]).
+  3. For i = 0..m-1, the time-local problem Eq. (localProblemTime): one
+     backward-Euler step of size dt = Dt/m on the patch, Dirichlet data on
+     the patch faces interior to the plate (gamma_D) equal to
+     (1-w) I(T+^n) + w I(T~+) with w = (i+1)/m (the solve of micro step i
+     produces time t_n + (i+1) dt; the printed weight i/m is available with
+     bc_weight_literal = 1), patch faces on the plate's sides adiabatic,
+     patch nodes on the plate's bottom at T_bottom.  Surface Gaussian at the
+     laser position at t_n + (i+1) dt.
+  4. Correction: inject the fine values at the coarse nodes that coincide
+     with free fine nodes, then redo the coarse backward-Euler step from
+     T+^n with those nodes held as Dirichlet data -> T+^{n+1}.
+
+Coefficients are lagged: each backward-Euler step evaluates rho c_e and k_e
+at the element mean of the step's starting temperature and the element's
+state at that time.  State rule after every step: element mean T_e of the
+new temperature; MELTED if T_e > T_melt; else POWDER if it was POWDER; else
+SOLID.  Initially an element is POWDER iff its centroid lies within
+powder_depth of the top surface, else SOLID.  The fine states live in a
+plate-wide map at fine resolution over the patch's depth range, so that
+material the patch consolidated keeps its state after the patch has moved
+on.
+
+Laser sources (Section 5.2): fine level, the surface Gaussian
+q = 3 eta P / (pi R^2) exp(-3 rho^2 / R^2) (integrates to eta P); coarse
+level, the surface analogue of the distributed source Q+ = P eta /(r d v Dt):
+intensity eta P /(R v Dt) on the axis-aligned rectangle swept by the laser
+during the macro step, R wide, integrated exactly against the bilinear hats
+(coarse_source = 0), or the fine Gaussian at t_n + Dt (coarse_source = 1).
+
+Scan path: tracks (x0, y0, x1, y1, v) run back to back from t = 0; the laser
+is at track j for t in [t_start_j, t_end_j] (first matching track) and off
+after the last one.
+"""
+from __future__ import annotations
+
+from math import floor, hypot
+
+import numpy as np
+
+from . import fem
+
+POWDER, SOLID, MELTED = 0, 1, 2
+
+
+class ScanPath:
+    """Piecewise-linear laser path; times accumulate track durations."""
+
+    def __init__(self, tracks):
+        self.tracks = [tuple(float(v) for v in t) for t in tracks]
+        self.t_start, self.t_end, self.dur = [], [], []
+        t = 0.0
+        for (x0, y0, x1, y1, v) in self.tracks:
+            d = hypot(x1 - x0, y1 - y0) / v
+            self.t_start.append(t)
+            self.dur.append(d)
+            t = t + d
+            self.t_end.append(t)
+
+    def position(self, t):
+        """(x, y) of the laser at time t, or None when it is off."""
+        for j, (x0, y0, x1, y1, v) in enumerate(self.tracks):
+            if t <= self.t_end[j]:
+                f = (t - self.t_start[j]) / self.dur[j]
+                return (x0 + f * (x1 - x0), y0 + f * (y1 - y0))
+        return None
+
+    def swept_pieces(self, ta, tb):
+        """Pieces of the path traversed in [ta, tb]: (track, tau_a, tau_b)."""
+        out = []
+        for j in range(len(self.tracks)):
+            a = max(ta, self.t_start[j])
+            b = min(tb, self.t_end[j])
+            if b > a:
+                out.append((j, a, b))
+        return out
+
+
+class Material:
+    def __init__(self, cfg):
+        self.rho = cfg["rho"]
+        self.c0, self.c1 = cfg["c0"], cfg["c1"]
+        self.k0, self.k1 = cfg["k0"], cfg["k1"]
+        self.Tref = cfg["Tref"]
+        self.powder_factor = cfg["powder_factor"]
+        self.T_melt = cfg["T_melt"]
+
+    def coefficients(self, Tbar, state):
+        """(rho c_e, k_e) at element-mean temperature Tbar and state."""
+        rc = self.rho * (self.c0 + self.c1 * (Tbar - self.Tref))
+        k = self.k0 + self.k1 * (Tbar - self.Tref)
+        k = np.where(state == POWDER, self.powder_factor * k, k)
+        return rc, k
+
+    def update_state(self, Tbar, state):
+        """State after a step whose end temperature has element means Tbar."""
+        new = np.where(state == POWDER, POWDER, SOLID).astype(np.uint8)
+        new[Tbar > self.T_melt] = MELTED
+        return new
+
+
+def initial_state(mesh, Lz, powder_depth):
+    """POWDER iff the element centroid is within powder_depth of the top."""
+    _, _, ke = mesh.elem_ijk
+    zc = mesh.origin[2] + (ke + 0.5) * mesh.hz
+    return np.where(Lz - zc < powder_depth, POWDER, SOLID).astype(np.uint8)
+
+
+def be_step(mesh, T, s_e, k_e, F, dir_idx, g):
+    """One backward-Euler step (S + K) T' = S T + F with T'[dir_idx] = g,
+    S = sum_e s_e Mhat (s_e = rho c_e / dt), K = sum_e k_e Khat; returns T'."""
+    A = mesh.assemble(s_e, k_e)
+    S = mesh.assemble(s_e, np.zeros_like(k_e))
+    b = S @ T + F
+    Tn = fem.solve_dirichlet(A, b, dir_idx, g)
+    return Tn
+
+
+def energy_terms(mesh, T, Tn, s_e, k_e, F, dir_idx, dt):
+    """Energy bookkeeping of one step (J): stored heat, laser input and the
+    heat entering through the Dirichlet rows (their reactions)."""
+    S = mesh.assemble(s_e, np.zeros_like(k_e))
+    K = mesh.assemble(np.zeros_like(s_e), k_e)
+    u = Tn - T
+    Su = S @ u
+    R = Su + K @ Tn - F
+    return dict(stored=dt * float(Su.sum()), laser=dt * float(F.sum()),
+                flux=dt * float(R[dir_idx].sum()))
+
+
+class SingleLevel:
+    """Single-level backward-Euler solve of the whole plate on one mesh with
+    the fine Gaussian source (reference for the identity tests)."""
+
+    def __init__(self, cfg, nx, ny, nz, dt):
+        self.cfg = cfg
+        self.mesh = fem.BoxMesh(nx, ny, nz, cfg["Lx"] / nx, cfg["Ly"] / ny, cfg["Lz"] / nz)
+        self.mat = Material(cfg)
+        self.path = ScanPath(cfg["tracks"])
+        self.dt = dt
+        self.T = np.full(self.mesh.nnode, float(cfg["T0"]))
+        self.state = initial_state(self.mesh, cfg["Lz"], cfg["powder_depth"])
+        _, _, k = self.mesh.node_ijk()
+        self.dir_idx = np.flatnonzero(k == 0)
+        self.nstep = 0
+
+    def step(self):
+        cfg, mesh = self.cfg, self.mesh
+        t = (self.nstep + 1) * self.dt
+        Tbar = mesh.element_mean(self.T)
+        rc, k = self.mat.coefficients(Tbar, self.state)
+        pos = self.path.position(t)
+        if pos is None:
+            F = np.zeros(mesh.nnode)
+        else:
+            F = fem.gaussian_surface_load(mesh, pos[0], pos[1], cfg["P"], cfg["eta"], cfg["radius"])
+        g = np.full(len(self.dir_idx), float(cfg["T_bottom"]))
+        Tn = be_step(mesh, self.T, rc / self.dt, k, F, self.dir_idx, g)
+        self.state = self.mat.update_state(mesh.element_mean(Tn), self.state)
+        self.T = Tn
+        self.nstep += 1
+
+
+class TwoLevel:
+    """Algorithm 1 with the readings stated in the module docstring."""
+
+    def __init__(self, cfg):
+        self.cfg = cfg
+        c = cfg
+        self.NXc, self.NYc, self.NZc = c["NXc"], c["NYc"], c["NZc"]
+        self.r, self.m = int(c["r"]), int(c["m"])
+        self.hc = (c["Lx"] / self.NXc, c["Ly"] / self.NYc, c["Lz"] / self.NZc)
+        self.coarse = fem.BoxMesh(self.NXc, self.NYc, self.NZc, *self.hc)
+        self.pN = (c["pNXc"], c["pNYc"], c["pNZc"])
+        r = self.r
+        self.hf = (self.hc[0] / r, self.hc[1] / r, self.hc[2] / r)
+        self.nf = (self.pN[0] * r, self.pN[1] * r, self.pN[2] * r)
+        self.mat = Material(c)
+        self.path = ScanPath(c["tracks"])
+        self.Dt = float(c["dt_coarse"])
+        self.dt = self.Dt / self.m
+        self.Tc = np.full(self.coarse.nnode, float(c["T0"]))
+        self.state_c = initial_state(self.coarse, c["Lz"], c["powder_depth"])
+        # plate-wide fine state map over the patch's depth range
+        self.ok = self.NZc - self.pN[2]
+        self.map_dims = (self.NXc * r, self.NYc * r, self.pN[2] * r)
+        mx, my, mz = self.map_dims
+        ke = np.arange(mz)
+        zc = (self.ok * r + ke + 0.5) * self.hf[2]
+        layer = np.where(c["Lz"] - zc < c["powder_depth"], POWDER, SOLID).astype(np.uint8)
+        self.state_map = np.broadcast_to(layer[:, None, None], (mz, my, mx)).copy()
+        _, _, kc = self.coarse.node_ijk()
+        self.coarse_bottom = np.flatnonzero(kc == 0)
+        self.n = 0
+        self.energy = dict(fine_stored=0.0, fine_laser=0.0, fine_flux=0.0,
+                           coarse_stored=0.0, coarse_laser=0.0, coarse_flux=0.0)
+        self.step_energy = []          # per-solve energy terms (fine and coarse)
+        self.origin = self._origin_for(0, None)
+        self.Tf = self._interp_fine(self.Tc, self.origin)
+        self.Tc_pred = None
+
+    # -- geometry ---------------------------------------------------------
+    def _origin_for(self, n, prev):
+        pos = self.path.position(n * self.Dt + 0.5 * self.Dt)
+        if pos is None:
+            if prev is not None:
+                return prev
+            pos = (0.5 * self.cfg["Lx"], 0.5 * self.cfg["Ly"])
+        oi = floor((pos[0] - 0.5 * self.pN[0] * self.hc[0]) / self.hc[0] + 0.5)
+        oj = floor((pos[1] - 0.5 * self.pN[1] * self.hc[1]) / self.hc[1] + 0.5)
+        oi = min(max(oi, 0), self.NXc - self.pN[0])
+        oj = min(max(oj, 0), self.NYc - self.pN[1])
+        return (int(oi), int(oj), int(self.ok))
+
+    def fine_mesh(self, origin=None):
+        o = self.origin if origin is None else origin
+        return fem.BoxMesh(*self.nf, *self.hf,
+                           origin=(o[0] * self.hc[0], o[1] * self.hc[1], o[2] * self.hc[2]))
+
+    def _fine_global_ijk(self, origin):
+        mesh = self.fine_mesh(origin)
+        i, j, k = mesh.node_ijk()
+        r = self.r
+        return i + origin[0] * r, j + origin[1] * r, k + origin[2] * r
+
+    def _interp_fine(self, Tc, origin):
+        """Trilinear interpolant of the coarse field at the patch nodes, with
+        exact fractional positions (fine index - r * coarse index) / r."""
+        gi, gj, gk = self._fine_global_ijk(origin)
+        r, C = self.r, self.coarse
+        I = np.minimum(gi // r, C.nx - 1)
+        J = np.minimum(gj // r, C.ny - 1)
+        K = np.minimum(gk // r, C.nz - 1)
+        tx, ty, tz = (gi - I * r) / r, (gj - J * r) / r, (gk - K * r) / r
+        out = np.zeros(len(gi))
+        for a in range(8):
+            ax, ay, az = a & 1, (a >> 1) & 1, (a >> 2) & 1
+            w = ((tx if ax else 1.0 - tx) * (ty if ay else 1.0 - ty)
+                 * (tz if az else 1.0 - tz))
+            out = out + w * Tc[C.node_id(I + ax, J + ay, K + az)]
+        return out
+
+    def dirichlet_faces(self, origin=None):
+        """(x-, x+, y-, y+, z-) True where the patch face is interior to the
+        plate (gamma_D).  The top face is never Dirichlet."""
+        o = self.origin if origin is None else origin
+        return (o[0] > 0, o[0] + self.pN[0] < self.NXc,
+                o[1] > 0, o[1] + self.pN[1] < self.NYc, True)
+
+    def fine_dirichlet(self, origin=None):
+        """Ids of the fine Dirichlet nodes and a mask of those on the plate
+        bottom (held at T_bottom); the others get coarse data."""
+        o = self.origin if origin is None else origin
+        mesh = self.fine_mesh(o)
+        i, j, k = mesh.node_ijk()
+        xm, xp, ym, yp, zm = self.dirichlet_faces(o)
+        nx, ny, _ = self.nf
+        d = np.zeros(mesh.nnode, dtype=bool)
+        if xm:
+            d |= i == 0
+        if xp:
+            d |= i == nx
+        if ym:
+            d |= j == 0
+        if yp:
+            d |= j == ny
+        d |= k == 0
+        idx = np.flatnonzero(d)
+        on_bottom = (k[idx] + o[2] * self.r) == 0
+        return idx, on_bottom
+
+    def injection_box(self, origin=None):
+        """Coarse node index ranges [lo, hi] (inclusive) that coincide with
+        free fine nodes."""
+        o = self.origin if origin is None else origin
+        xm, xp, ym, yp, _ = self.dirichlet_faces(o)
+        return ((o[0] + (1 if xm else 0), o[0] + self.pN[0] - (1 if xp else 0)),
+                (o[1] + (1 if ym else 0), o[1] + self.pN[1] - (1 if yp else 0)),
+                (o[2] + 1, self.NZc))
+
+    def fine_state(self, origin=None):
+        """View of the state map under the patch, in fine element order."""
+        o = self.origin if origin is None else origin
+        r = self.r
+        nx, ny, nz = self.nf
+        return self.state_map[:, o[1] * r:o[1] * r + ny, o[0] * r:o[0] * r + nx]
+
+    # -- sources -----------------------------------------------------------
+    def fine_load(self, mesh, t):
+        pos = self.path.position(t)
+        if pos is None:
+            return np.zeros(mesh.nnode)
+        c = self.cfg
+        return fem.gaussian_surface_load(mesh, pos[0], pos[1], c["P"], c["eta"], c["radius"])
+
+    def coarse_load(self, n):
+        c = self.cfg
+        t0, t1 = n * self.Dt, (n + 1) * self.Dt
+        if int(c.get("coarse_source", 0)) == 1:
+            pos = self.path.position(t1)
+            if pos is None:
+                return np.zeros(self.coarse.nnode)
+            return fem.gaussian_surface_load(self.coarse, pos[0], pos[1], c["P"], c["eta"], c["radius"])
+        R = c["radius"]
+        rects = []
+        for (j, ta, tb) in self.path.swept_pieces(t0, t1):
+            x0, y0, x1, y1, v = self.path.tracks[j]
+            fa = (ta - self.path.t_start[j]) / self.path.dur[j]
+            fb = (tb - self.path.t_start[j]) / self.path.dur[j]
+            xa, ya = x0 + fa * (x1 - x0), y0 + fa * (y1 - y0)
+            xb, yb = x0 + fb * (x1 - x0), y0 + fb * (y1 - y0)
+            q = c["eta"] * c["P"] / (R * v * self.Dt)
+            if y0 == y1:
+                rects.append((min(xa, xb), max(xa, xb), y0 - 0.5 * R, y0 + 0.5 * R, q))
+            elif x0 == x1:
+                rects.append((x0 - 0.5 * R, x0 + 0.5 * R, min(ya, yb), max(ya, yb), q))
+            else:
+                raise ValueError("box coarse source needs axis-aligned tracks")
+        return fem.box_surface_load(self.coarse, rects)
+
+    # -- Algorithm 1 ---------------------------------------------------------
+    def move_patch(self):
+        new = self._origin_for(self.n, self.origin)
+        if new == self.origin:
+            return False
+        interp = self._interp_fine(self.Tc, new)
+        old = self.origin
+        r = self.r
+        nx, ny, nz = self.nf
+        mesh = self.fine_mesh(new)
+        i, j, k = mesh.node_ijk()
+        # position of each new node in the old patch's index frame
+        oi = i + (new[0] - old[0]) * r
+        oj = j + (new[1] - old[1]) * r
+        inside = (oi >= 0) & (oi <= nx) & (oj >= 0) & (oj <= ny)
+        T = interp.copy()
+        old_id = oi + (nx + 1) * (oj + (ny + 1) * k)
+        T[inside] = self.Tf[old_id[inside]]
+        self.Tf = T
+        self.origin = new
+        return True
+
+    def _coarse_coefficients(self):
+        Tbar = self.coarse.element_mean(self.Tc)
+        return self.mat.coefficients(Tbar, self.state_c)
+
+    def predict(self):
+        self.move_patch()
+        rc, k = self._coarse_coefficients()
+        F = self.coarse_load(self.n)
+        g = np.full(len(self.coarse_bottom), float(self.cfg["T_bottom"]))
+        self.Tc_pred = be_step(self.coarse, self.Tc, rc / self.Dt, k, F, self.coarse_bottom, g)
+        self._I_now = None
+        self._I_pred = None
+
+    def fine_substep(self, i):
+        c = self.cfg
+        mesh = self.fine_mesh()
+        if self._I_now is None:
+            self._I_now = self._interp_fine(self.Tc, self.origin)
+            self._I_pred = self._interp_fine(self.Tc_pred, self.origin)
+        w = (i / self.m) if int(c.get("bc_weight_literal", 0)) else ((i + 1) / self.m)
+        idx, on_bottom = self.fine_dirichlet()
+        g = (1.0 - w) * self._I_now[idx] + w * self._I_pred[idx]
+        g[on_bottom] = c["T_bottom"]
+        st = self.fine_state()
+        st_flat = st.reshape(-1)
+        Tbar = mesh.element_mean(self.Tf)
+        rc, k = self.mat.coefficients(Tbar, st_flat)
+        t = (self.n * self.m + i + 1) * self.dt
+        F = self.fine_load(mesh, t)
+        Tn = be_step(mesh, self.Tf, rc / self.dt, k, F, idx, g)
+        e = energy_terms(mesh, self.Tf, Tn, rc / self.dt, k, F, idx, self.dt)
+        self.energy["fine_stored"] += e["stored"]
+        self.energy["fine_laser"] += e["laser"]
+        self.energy["fine_flux"] += e["flux"]
+        self.step_energy.append(("fine", e))
+        new_state = self.mat.update_state(mesh.element_mean(Tn), st_flat)
+        st[...] = new_state.reshape(st.shape)
+        self.Tf = Tn
+
+    def restrict_and_correct(self):
+        c = self.cfg
+        (i0, i1), (j0, j1), (k0, k1) = self.injection_box()
+        I, J, K = np.meshgrid(np.arange(i0, i1 + 1), np.arange(j0, j1 + 1),
+                              np.arange(k0, k1 + 1), indexing="ij")
+        I, J, K = I.ravel(), J.ravel(), K.ravel()
+        r, o = self.r, self.origin
+        fi, fj, fk = (I - o[0]) * r, (J - o[1]) * r, (K - o[2]) * r
+        nx, ny, _ = self.nf
+        inj_vals = self.Tf[fi + (nx + 1) * (fj + (ny + 1) * fk)]
+        inj_idx = self.coarse.node_id(I, J, K)
+        rc, k = self._coarse_coefficients()
+        F = self.coarse_load(self.n)
+        dir_idx = np.concatenate([self.coarse_bottom, inj_idx])
+        g = np.concatenate([np.full(len(self.coarse_bottom), float(c["T_bottom"])), inj_vals])
+        Tn = be_step(self.coarse, self.Tc, rc / self.Dt, k, F, dir_idx, g)
+        e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt)
+        self.energy["coarse_stored"] += e["stored"]
+        self.energy["coarse_laser"] += e["laser"]
+        self.energy["coarse_flux"] += e["flux"]
+        self.step_energy.append(("coarse", e))
+        self.state_c = self.mat.update_state(self.coarse.element_mean(Tn), self.state_c)
+        self.Tc = Tn
+        self.Tc_pred = None
+
+    def macro_step(self):
+        self.predict()
+        for i in range(self.m):
+            self.fine_substep(i)
+        self.restrict_and_correct()
+        self.n += 1
+
+    def run(self, n_macro):
+        for _ in range(n_macro):
+            self.macro_step()
+        return self
+
+    def melt_mask_fine(self):
+        return self.fine_state().reshape(-1) == MELTED

@@ -1,0 +1,188 @@
+"""Pins of the two-level oracle (Algorithm 1) against closed forms, identities
+and invariants (no GPU)."""
+from math import cos, pi, sin
+
+import numpy as np
+import pytest
+
+from oracle import fem
+from oracle import twolevel as TL
+from paper_2110_12932_gb300 import workloads as W
+
+
+def _constant_props(cfg):
+    cfg = dict(cfg)
+    cfg.update(c1=0.0, k1=0.0, powder_depth=0.0)
+    return cfg
+
+
+def test_discrete_eigenmode_decay():
+    """Constant properties, no laser: T - Tb = A cos(pi x/Lx) cos(pi y/Ly)
+    sin(pi z/(2 Lz)) is an exact eigenvector of the Q1 pencil (adiabatic
+    sides and top, Dirichlet bottom), so backward Euler multiplies it by
+    (1 + dt lambda_h)^-1 per step with
+    lambda_h = (k/rho c) sum_d (6/h_d^2)(1 - cos th_d)/(2 + cos th_d)."""
+    cfg = _constant_props(W.single_track_tiny())
+    cfg["P"] = 0.0
+    nx, ny, nz = 12, 6, 5
+    dt = 2e-4
+    sl = TL.SingleLevel(cfg, nx, ny, nz, dt)
+    x, y, z = sl.mesh.node_xyz()
+    Lx, Ly, Lz = cfg["Lx"], cfg["Ly"], cfg["Lz"]
+    mode = np.cos(pi * x / Lx) * np.cos(pi * y / Ly) * np.sin(pi * z / (2 * Lz))
+    A0 = 400.0
+    sl.T = cfg["T_bottom"] + A0 * mode
+    hx, hy, hz = Lx / nx, Ly / ny, Lz / nz
+    th = (pi * hx / Lx, pi * hy / Ly, pi * hz / (2 * Lz))
+    lam = sum(6 / h ** 2 * (1 - cos(t)) / (2 + cos(t)) for h, t in zip((hx, hy, hz), th))
+    lam *= cfg["k0"] / (cfg["rho"] * cfg["c0"])
+    for n in range(1, 6):
+        sl.step()
+        expect = cfg["T_bottom"] + A0 * (1 + dt * lam) ** (-n) * mode
+        assert np.abs(sl.T - expect).max() < 1e-9, n
+
+
+def test_continuum_convergence_of_eigenvalue():
+    """The discrete eigenvalue converges to the continuum one at O(h^2)."""
+    k, rc = 6.7, 4430 * 526.0
+    L = (2e-3, 1e-3, 0.5e-3)
+    lam_c = k / rc * pi ** 2 * (1 / L[0] ** 2 + 1 / L[1] ** 2 + 1 / (4 * L[2] ** 2))
+    errs = []
+    for n in (4, 8, 16, 32):
+        h = (L[0] / n, L[1] / n, L[2] / n)
+        th = (pi * h[0] / L[0], pi * h[1] / L[1], pi * h[2] / (2 * L[2]))
+        lam = k / rc * sum(6 / hh ** 2 * (1 - cos(t)) / (2 + cos(t)) for hh, t in zip(h, th))
+        errs.append(abs(lam - lam_c) / lam_c)
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.8 < q < 4.2 for q in ratios)
+
+
+def test_energy_identity_every_solve():
+    """Stored heat = laser input + heat through the Dirichlet rows, per solve,
+    on both levels (exact for the direct solves)."""
+    o = TL.TwoLevel(W.single_track_tiny())
+    o.run(8)
+    for kind, e in o.step_energy:
+        scale = max(abs(e["stored"]), abs(e["laser"]), 1e-12)
+        assert abs(e["stored"] - e["laser"] - e["flux"]) <= 1e-10 * scale, kind
+    assert o.energy["fine_laser"] > 0
+
+
+def test_patch_covering_plate_equals_single_level():
+    """Patch = whole plate: no interface, so every micro step is the
+    single-level fine backward-Euler step (identity stated in Section 5.1)."""
+    cfg = W.single_track_tiny()
+    cfg.update(NXc=8, NYc=4, NZc=2, pNXc=8, pNYc=4, pNZc=2, r=2, m=2)
+    o = TL.TwoLevel(cfg)
+    sl = TL.SingleLevel(cfg, 16, 8, 4, cfg["dt_coarse"] / 2)
+    for n in range(6):
+        o.macro_step()
+        sl.step()
+        sl.step()
+        assert o.origin == (0, 0, 0)
+        rel = np.linalg.norm(o.Tf - sl.T) / np.linalg.norm(sl.T)
+        assert rel < 1e-12, (n, rel)
+    assert np.array_equal(o.fine_state().reshape(-1), sl.state)
+
+
+def test_unit_ratios_equal_single_level_coarse():
+    """r = 1, m = 1 and the Gaussian on the coarse level: the predictor is
+    the single-level step, the patch solve reproduces it by uniqueness and
+    the correction keeps it, for any patch position."""
+    cfg = W.single_track_tiny()
+    cfg.update(r=1, m=1, coarse_source=1, pNXc=6, pNYc=4, pNZc=2)
+    o = TL.TwoLevel(cfg)
+    sl = TL.SingleLevel(cfg, cfg["NXc"], cfg["NYc"], cfg["NZc"], cfg["dt_coarse"])
+    moved = 0
+    for n in range(20):
+        before = o.origin
+        o.macro_step()
+        moved += before != o.origin
+        sl.step()
+        rel = np.linalg.norm(o.Tc - sl.T) / np.linalg.norm(sl.T)
+        assert rel < 1e-12, (n, rel)
+    assert moved >= 3
+
+
+def test_patch_motion_copies_overlap_and_interpolates_new_nodes():
+    o = TL.TwoLevel(W.single_track_tiny())
+    o.run(3)
+    # force a move by one coarse element in +x
+    old = o.origin
+    Tf_old = o.Tf.copy()
+    new = (old[0] + 1, old[1], old[2])
+    o._origin_for = lambda n, prev: new
+    assert o.move_patch()
+    r = o.r
+    nx, ny, nz = o.nf
+    mesh = o.fine_mesh()
+    i, j, k = mesh.node_ijk()
+    src_i = i + r
+    inside = src_i <= nx
+    src = src_i + (nx + 1) * (j + (ny + 1) * k)
+    assert np.array_equal(o.Tf[inside], Tf_old[src[inside]])
+    x, y, z = mesh.node_xyz()
+    interp = fem.trilinear(o.coarse, o.Tc, x, y, z)
+    assert np.allclose(o.Tf[~inside], interp[~inside], rtol=1e-13, atol=0)
+
+
+def test_state_rule():
+    mat = TL.Material(W.single_track_tiny())
+    state = np.array([TL.POWDER, TL.POWDER, TL.SOLID, TL.MELTED, TL.MELTED], dtype=np.uint8)
+    Tbar = np.array([1000.0, 2000.0, 1900.0, 1000.0, 1900.0000001])
+    new = mat.update_state(Tbar, state)
+    assert list(new) == [TL.POWDER, TL.MELTED, TL.SOLID, TL.SOLID, TL.MELTED]
+    rc, k = mat.coefficients(np.array([293.0, 293.0]), np.array([TL.POWDER, TL.SOLID]))
+    assert rc[0] == rc[1] == 4430 * 526.0
+    assert k[1] == 6.7 and abs(k[0] - 0.067) < 1e-15
+
+
+def test_initial_powder_layer():
+    o = TL.TwoLevel(W.single_track_tiny())
+    # fine elements are 31.25 um: centroids at 15.6 and 46.9 um below the top are powder
+    mz = o.map_dims[2]
+    layers = o.state_map[:, 0, 0]
+    assert list(layers[mz - 2:]) == [TL.POWDER, TL.POWDER]
+    assert np.all(layers[:mz - 2] == TL.SOLID)
+    # no coarse element (125 um) is powder
+    assert np.all(o.state_c == TL.SOLID)
+
+
+def test_scan_path_times_and_positions():
+    cfg = W.multitrack_10mm()
+    path = TL.ScanPath(cfg["tracks"])
+    assert abs(path.t_end[-1] - 0.1) < 1e-15
+    x, y = path.position(0.0)
+    assert (x, y) == (1e-3, 2.05e-3)
+    x, y = path.position(0.01 + 0.005)       # middle of the second track (returning)
+    assert abs(x - 5e-3) < 1e-15 and abs(y - 2.15e-3) < 1e-15
+    assert path.position(0.1 + 1e-9) is None
+
+
+@pytest.mark.slow
+def test_error_grows_with_time_ratio():
+    """Section 5.1's setting: identical spatial discretisation on both levels
+    (r = 1, the Gaussian on the coarse level too) isolates the temporal error
+    of the multirate scheme; at fixed micro step it is zero for m = 1 and
+    grows with the macro step Dt = m dt."""
+    base = W.single_track_tiny()
+    base.update(NXc=32, NYc=16, NZc=8, pNXc=8, pNYc=6, pNZc=3, r=1, coarse_source=1)
+    dt = 25e-6
+    nsteps = 16
+    ref = TL.SingleLevel(base, base["NXc"], base["NYc"], base["NZc"], dt)
+    for _ in range(nsteps):
+        ref.step()
+    errs = []
+    for m in (1, 2, 4, 8):
+        cfg = dict(base, m=m, dt_coarse=dt * m)
+        o = TL.TwoLevel(cfg)
+        o.run(nsteps // m)
+        mesh = o.fine_mesh()
+        x, y, z = mesh.node_xyz()
+        gi = np.rint(x / ref.mesh.hx).astype(int)
+        gj = np.rint(y / ref.mesh.hy).astype(int)
+        gk = np.rint(z / ref.mesh.hz).astype(int)
+        Tref = ref.T[ref.mesh.node_id(gi, gj, gk)]
+        errs.append(np.linalg.norm(o.Tf - Tref) / np.linalg.norm(Tref))
+    assert errs[0] < 1e-12, errs
+    assert errs[0] < errs[1] < errs[2] < errs[3], errs
