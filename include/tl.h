@@ -1,0 +1,191 @@
+/*
+ * tl.h -- C ABI of the GB300 (sm_103a) library for the fine-level transient
+ * heat solve of the spatiotemporal two-level method for laser powder bed
+ * fusion (Viguerie, Carraturo, Reali, Auricchio; arXiv:2110.12932).
+ *
+ * The paper's Algorithm 1 (Section 4) advances a coarse global temperature
+ * T+ with macro steps Dt and a fine local temperature T- on a patch that
+ * follows the laser with m micro steps dt = Dt/m:
+ *
+ *   for each macro step n:
+ *     tl_coarse_step(p, TL_PREDICT)   predictor T~+ at t_n + Dt
+ *     tl_fine_substeps(p, m)          m solves of the time-local problem
+ *                                     Eq. (localProblemTime)
+ *     tl_restrict(p)                  fine -> coarse injection
+ *     tl_coarse_step(p, TL_CORRECT)   corrected T+ at t_n + Dt
+ *
+ * Every solve is one backward-Euler step of the heat equation Eq.
+ * (thermalEqn) (Section 2.1, latent heat omitted) on a uniform mesh of
+ * trilinear hexahedra, with conductivity and heat capacity evaluated at the
+ * element-mean temperature of the step's start (lagged), a powder/solid/
+ * melted element state, and a Jacobi-preconditioned conjugate gradient
+ * solve run entirely on the GPU.
+ *
+ * Ownership: the library owns every device buffer of a problem; host
+ * buffers passed to getters belong to the caller.  Calls are ordered on the
+ * configured CUDA stream; getters and tl_sync synchronise it.  No call
+ * aborts or leaves the device waiting: every device-side wait has a time
+ * limit and failures are reported through tl_status.  A handle is not
+ * thread-safe; distinct handles are independent.
+ */
+#ifndef TL_H
+#define TL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tl_problem tl_problem;
+
+typedef enum {
+  TL_OK = 0,
+  TL_EINVAL = -1,   /* invalid configuration or argument                     */
+  TL_ENOMEM = -2,   /* a device allocation failed                            */
+  TL_ENOCONV = -3,  /* a CG solve reached max_iter; that step left T unchanged */
+  TL_ESTATE = -4,   /* call out of order (see the loop above)                */
+  TL_ECUDA = -5,    /* a CUDA runtime call failed                            */
+  TL_ETIMEOUT = -6  /* a device-side grid barrier exceeded its time limit    */
+} tl_status;
+
+typedef enum { TL_FP64 = 0, TL_FP32_REFINED = 1 } tl_precision;
+typedef enum { TL_PREDICT = 0, TL_CORRECT = 1 } tl_phase;
+typedef enum { TL_COARSE = 0, TL_FINE = 1 } tl_level;
+
+/* One straight laser track on the top surface z = Lz, traversed from
+ * (x0, y0) to (x1, y1) at `speed` m/s.  Tracks run back to back from t = 0;
+ * the laser is off after the last one (Section 5.2-5.3 scan paths). */
+typedef struct { double x0, y0, x1, y1, speed; } tl_track;
+
+/* Problem description (SI units).  The plate is [0,Lx]x[0,Ly]x[0,Lz], z up,
+ * held at T_bottom on z = 0 and adiabatic elsewhere apart from the laser.
+ * The coarse mesh has NXc x NYc x NZc hexahedra.  The fine patch covers
+ * pNXc x pNYc x pNZc coarse elements at the top surface, each refined r
+ * times per direction; its origin sits on a coarse node and follows the
+ * laser (Section 5.2).  Material (Section 2.2 with linear laws):
+ * rho c(T) = rho (c0 + c1 (T - Tref)), k(T) = k0 + k1 (T - Tref), times
+ * powder_factor for POWDER elements.  An element is POWDER initially iff its
+ * centroid lies within powder_depth of the top surface; after each solve it
+ * becomes MELTED if its mean temperature exceeds T_melt, else stays POWDER
+ * if it was, else SOLID. */
+typedef struct {
+  double Lx, Ly, Lz;
+  int NXc, NYc, NZc;
+  int pNXc, pNYc, pNZc;   /* 1 <= pN*c <= N*c                                  */
+  int r;                  /* space refinement ratio, >= 1                      */
+  int m;                  /* time ratio: micro steps per macro step, >= 1      */
+  double dt_coarse;       /* macro step Dt [s]                                 */
+  double T0, T_bottom;    /* initial temperature, bottom Dirichlet value [K]   */
+  double rho, c0, c1, k0, k1, Tref;
+  double powder_depth, powder_factor, T_melt;
+  double P, eta, radius;  /* laser power [W], absorptivity, radius R [m]       */
+  const tl_track* path;   /* ntracks tracks, copied at creation                */
+  int ntracks;
+  /* coarse-level source: 0 = the surface analogue of the paper's distributed
+   * source Q+ (Section 5.2): intensity eta P / (R v Dt) on the R-wide
+   * rectangle swept during the macro step (tracks must be axis-aligned);
+   * 1 = the fine-level Gaussian at t_n + Dt. */
+  int coarse_source;
+  /* Dirichlet weight of micro step i on gamma_D: 0 -> w = (i+1)/m (the solve
+   * produces time t_n + (i+1) dt); 1 -> the printed w = i/m. */
+  int bc_weight_literal;
+  int energy;             /* 1: accumulate the energy account of every solve   */
+  tl_precision precision; /* TL_FP64, or FP32 inner CG with FP64 defect correction */
+  double tol;             /* relative residual of each solve (FP64 measure)    */
+  double tol_inner;       /* relative residual of each FP32 inner solve        */
+  int max_iter;           /* CG iteration cap per solve (inner cap when refined) */
+  void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
+  /* optional device allocator: both NULL -> cudaMalloc / cudaFree */
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* alloc_ctx;
+} tl_config;
+
+/* Counters and energy account (J) since creation.  stored = sum_e rho c_e
+ * int_e (T^{k+1} - T^k), laser = dt sum_i F_i, flux = dt * (sum of the
+ * Dirichlet-row reactions); per solve stored = laser + flux up to the solver
+ * tolerance (discrete energy identity). */
+typedef struct {
+  int64_t macro_steps, substeps;
+  int64_t cg_iters_fine, cg_iters_coarse;    /* all inner CG iterations        */
+  int64_t outer_iters_fine, outer_iters_coarse; /* defect-correction sweeps (refined) */
+  int64_t solves_fine, solves_coarse;
+  int32_t max_iters_fine, max_iters_coarse;  /* largest per-solve inner count  */
+  int32_t origin[3];                         /* patch origin, coarse node index */
+  int64_t patch_moves;
+  int64_t launches;                          /* kernels launched by this handle */
+  double energy_fine_stored, energy_fine_laser, energy_fine_flux;
+  double energy_coarse_stored, energy_coarse_laser, energy_coarse_flux;
+  double time;                               /* simulated time t_n [s]         */
+} tl_stats;
+
+/* Validate *cfg, allocate and initialise (T = T0 on both levels, states by
+ * the powder rule, patch origin for the laser position at Dt/2).  *out is
+ * set to NULL on error.  Errors: TL_EINVAL (sizes, ratios, non-positive
+ * properties, a non-axis-aligned track with coarse_source 0), TL_ENOMEM,
+ * TL_ECUDA. */
+tl_status tl_create_problem(const tl_config* cfg, tl_problem** out);
+
+/* TL_PREDICT: move the patch for the laser position at t_n + Dt/2 (overlap
+ * nodes keep their values, new nodes take the trilinear interpolant of T+^n;
+ * Section 5.2: no projection), then solve the coarse backward-Euler step
+ * T+^n -> T~+ (Algorithm 1, predictor).  TL_CORRECT: solve the same step
+ * again with the injected nodes as Dirichlet data -> T+^{n+1}, update the
+ * coarse states, advance n (Algorithm 1, correction step).
+ * Errors: TL_ESTATE out of order, TL_EINVAL bad phase. */
+tl_status tl_coarse_step(tl_problem* p, tl_phase phase);
+
+/* Solve the next nsub micro steps of the current macro step, Eq.
+ * (localProblemTime): Dirichlet data (1-w) I(T+^n) + w I(T~+) on the patch
+ * faces interior to the plate, adiabatic patch faces on the plate's sides,
+ * T_bottom on the plate's bottom, surface Gaussian source
+ * q = 3 eta P/(pi R^2) exp(-3 rho^2/R^2) at the laser position at the end
+ * of the micro step.  Errors: TL_ESTATE (no predictor yet, or more than m
+ * micro steps in this macro step), TL_EINVAL (nsub < 0). */
+tl_status tl_fine_substeps(tl_problem* p, int nsub);
+
+/* Inject the fine temperature into the coarse nodes that coincide with free
+ * fine nodes (Algorithm 1, correction input).  Errors: TL_ESTATE unless all
+ * m micro steps of the macro step are done. */
+tl_status tl_restrict(tl_problem* p);
+
+/* Convenience: nmacro full macro steps (predict, m micro steps, restrict,
+ * correct), then a stream synchronisation; returns the first error. */
+tl_status tl_macro_steps(tl_problem* p, int nmacro);
+
+/* Synchronise the stream and return the first device-side error recorded
+ * since creation (TL_ENOCONV, TL_ETIMEOUT) or TL_OK. */
+tl_status tl_sync(tl_problem* p);
+
+/* Number of nodes of a level (coarse: (NXc+1)(NYc+1)(NZc+1); fine:
+ * (r pNXc+1)(r pNYc+1)(r pNZc+1)), or 0 for a bad argument. */
+size_t tl_node_count(const tl_problem* p, tl_level level);
+
+/* Copy a level's nodal temperature (x fastest, then y, then z) into the
+ * caller's host buffer of exactly n doubles; origin_out (may be NULL)
+ * receives the patch origin in coarse node indices.  Synchronises the
+ * stream.  Errors: TL_EINVAL (n mismatch, NULL buffer), TL_ECUDA. */
+tl_status tl_get_temperature(const tl_problem* p, tl_level level, double* host_out,
+                             size_t n, int origin_out[3]);
+
+/* Copy element states (0 POWDER, 1 SOLID, 2 MELTED): coarse, NXc*NYc*NZc;
+ * fine, the patch's r pNXc * r pNYc * r pNZc elements; x fastest.
+ * Synchronises.  Errors: TL_EINVAL, TL_ECUDA. */
+tl_status tl_get_state(const tl_problem* p, tl_level level, uint8_t* host_out, size_t n);
+
+/* Copy the counters (synchronises). */
+tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
+
+/* Release every device buffer of the problem; NULL is ignored. */
+void tl_destroy_problem(tl_problem* p);
+
+/* Static description of a status code. */
+const char* tl_status_string(tl_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TL_H */

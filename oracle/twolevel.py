@@ -186,8 +186,9 @@ class SingleLevel:
 class TwoLevel:
     """Algorithm 1 with the readings stated in the module docstring."""
 
-    def __init__(self, cfg):
+    def __init__(self, cfg, energy=True):
         self.cfg = cfg
+        self.track_energy = energy
         c = cfg
         self.NXc, self.NYc, self.NZc = c["NXc"], c["NYc"], c["NZc"]
         self.r, self.m = int(c["r"]), int(c["m"])
@@ -392,11 +393,12 @@ class TwoLevel:
         t = (self.n * self.m + i + 1) * self.dt
         F = self.fine_load(mesh, t)
         Tn = be_step(mesh, self.Tf, rc / self.dt, k, F, idx, g)
-        e = energy_terms(mesh, self.Tf, Tn, rc / self.dt, k, F, idx, self.dt)
-        self.energy["fine_stored"] += e["stored"]
-        self.energy["fine_laser"] += e["laser"]
-        self.energy["fine_flux"] += e["flux"]
-        self.step_energy.append(("fine", e))
+        if self.track_energy:
+            e = energy_terms(mesh, self.Tf, Tn, rc / self.dt, k, F, idx, self.dt)
+            self.energy["fine_stored"] += e["stored"]
+            self.energy["fine_laser"] += e["laser"]
+            self.energy["fine_flux"] += e["flux"]
+            self.step_energy.append(("fine", e))
         new_state = self.mat.update_state(mesh.element_mean(Tn), st_flat)
         st[...] = new_state.reshape(st.shape)
         self.Tf = Tn
@@ -417,11 +419,12 @@ class TwoLevel:
         dir_idx = np.concatenate([self.coarse_bottom, inj_idx])
         g = np.concatenate([np.full(len(self.coarse_bottom), float(c["T_bottom"])), inj_vals])
         Tn = be_step(self.coarse, self.Tc, rc / self.Dt, k, F, dir_idx, g)
-        e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt)
-        self.energy["coarse_stored"] += e["stored"]
-        self.energy["coarse_laser"] += e["laser"]
-        self.energy["coarse_flux"] += e["flux"]
-        self.step_energy.append(("coarse", e))
+        if self.track_energy:
+            e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt)
+            self.energy["coarse_stored"] += e["stored"]
+            self.energy["coarse_laser"] += e["laser"]
+            self.energy["coarse_flux"] += e["flux"]
+            self.step_energy.append(("coarse", e))
         self.state_c = self.mat.update_state(self.coarse.element_mean(Tn), self.state_c)
         self.Tc = Tn
         self.Tc_pred = None

@@ -1,0 +1,713 @@
+// C ABI of the two-level LPBF heat solve (declarations and contracts in
+// include/tl.h).  Host side: validation, device memory, the macro-step state
+// machine of Algorithm 1 (Section 4), laser path arithmetic, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tl.h"
+#include "tl_solve.cuh"
+
+using namespace tl;
+
+namespace {
+
+enum Phase { NEED_PREDICT = 0, IN_SUBSTEPS = 1, NEED_CORRECT = 2 };
+
+struct Level {
+  Grid3 g{};
+  Tiling t{};
+  int grid = 0;  // cooperative grid size
+  double* T = nullptr;    // current temperature
+  double* T2 = nullptr;   // coarse: predictor T~+; fine: move double buffer
+  double* u = nullptr;
+  double* r = nullptr;
+  double* F = nullptr;
+  double* p0 = nullptr;
+  double* p1 = nullptr;
+  double* q = nullptr;
+  double* X = nullptr;
+  double* dinv = nullptr;
+  double* s_e = nullptr;
+  double* k_e = nullptr;
+  double* inj = nullptr;  // coarse only
+  uint8_t* state = nullptr;
+  int st_sx = 0, st_sy = 0, st_sz = 0;
+  double Mc[8], Kc[8], Md = 0, Kd = 0, vol8 = 0, Mhat[64], Khat[64];
+};
+
+}  // namespace
+
+struct tl_problem {
+  tl_config cfg{};
+  std::vector<tl_track> tracks;
+  std::vector<double> t_start, t_end, dur;
+  Level C, Fi;
+  int oi = 0, oj = 0, ok = 0;
+  int n = 0;        // macro step index
+  int sub = 0;      // micro steps done in the current macro step
+  int phase = NEED_PREDICT;
+  long long patch_moves = 0;
+  long long launches = 0;
+  cudaStream_t stream = nullptr;
+  unsigned int* bar = nullptr;  // [count, gen]
+  int* status = nullptr;
+  double* red = nullptr;
+  int red_stride = 0;
+  DevStats* stats = nullptr;
+  std::vector<void*> allocs;
+  int nsm = 0, max_coop = 0;
+};
+
+namespace {
+
+tl_status dev_alloc(tl_problem* p, void** out, size_t bytes) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  if (p->cfg.alloc) {
+    ptr = p->cfg.alloc(bytes, (void*)p->stream, p->cfg.alloc_ctx);
+    if (!ptr) return TL_ENOMEM;
+  } else {
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? TL_ENOMEM : TL_ECUDA;
+    }
+  }
+  p->allocs.push_back(ptr);
+  *out = ptr;
+  return TL_OK;
+}
+
+template <typename T>
+tl_status alloc_n(tl_problem* p, T** out, size_t n) {
+  void* v = nullptr;
+  tl_status s = dev_alloc(p, &v, n * sizeof(T));
+  *out = (T*)v;
+  return s;
+}
+
+// Element constants of a box element hx*hy*hz (see tl_device.cuh): the Hadamard
+// eigenvalue factors Mc, Kc (1/8 folded in), the diagonal factors and the
+// explicit element matrices used for the Dirichlet reactions.
+void element_constants(Level& L) {
+  const double h[3] = {L.g.hx, L.g.hy, L.g.hz};
+  double mu[3][2], ka[3][2];
+  for (int d = 0; d < 3; ++d) {
+    mu[d][0] = h[d] / 2.0;
+    mu[d][1] = h[d] / 6.0;
+    ka[d][0] = 0.0;
+    ka[d][1] = 2.0 / h[d];
+  }
+  for (int m = 0; m < 8; ++m) {
+    int mx = m & 1, my = (m >> 1) & 1, mz = (m >> 2) & 1;
+    L.Mc[m] = 0.125 * mu[0][mx] * mu[1][my] * mu[2][mz];
+    L.Kc[m] = 0.125 * (ka[0][mx] * mu[1][my] * mu[2][mz] + mu[0][mx] * ka[1][my] * mu[2][mz] +
+                       mu[0][mx] * mu[1][my] * ka[2][mz]);
+  }
+  L.Md = (h[0] / 3.0) * (h[1] / 3.0) * (h[2] / 3.0);
+  L.Kd = (1.0 / h[0]) * (h[1] / 3.0) * (h[2] / 3.0) + (h[0] / 3.0) * (1.0 / h[1]) * (h[2] / 3.0) +
+         (h[0] / 3.0) * (h[1] / 3.0) * (1.0 / h[2]);
+  L.vol8 = h[0] * h[1] * h[2] / 8.0;
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) {
+      double m1[3], k1[3];
+      for (int d = 0; d < 3; ++d) {
+        int ad = (a >> d) & 1, bd = (b >> d) & 1;
+        m1[d] = h[d] / 6.0 * (ad == bd ? 2.0 : 1.0);
+        k1[d] = (ad == bd ? 1.0 : -1.0) / h[d];
+      }
+      L.Mhat[a * 8 + b] = m1[0] * m1[1] * m1[2];
+      L.Khat[a * 8 + b] = k1[0] * m1[1] * m1[2] + m1[0] * k1[1] * m1[2] + m1[0] * m1[1] * k1[2];
+    }
+}
+
+void choose_tiling(Level& L, int target) {
+  Tiling& t = L.t;
+  t.ex = std::min(TXE, L.g.nx);
+  t.ey = std::min(TYE, L.g.ny);
+  t.ntx = (L.g.nx + t.ex - 1) / t.ex;
+  t.nty = (L.g.ny + t.ey - 1) / t.ey;
+  long long nxy = (long long)t.ntx * t.nty;
+  long long ez = (L.g.nz * nxy + target - 1) / target;
+  t.ez = (int)std::max<long long>(1, std::min<long long>(ez, L.g.nz));
+  t.ntz = (L.g.nz + t.ez - 1) / t.ez;
+}
+
+tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
+  const size_t nn = (size_t)L.g.nnx * L.g.nny * L.g.nnz;
+  const size_t ne = (size_t)L.g.nx * L.g.ny * L.g.nz;
+  tl_status s;
+  if ((s = alloc_n(p, &L.T, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.T2, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.u, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.r, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.F, (size_t)L.g.nnx * L.g.nny)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.p0, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.p1, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.q, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.X, nn * NXB)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.dinv, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.s_e, ne)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.k_e, ne)) != TL_OK) return s;
+  if (coarse && (s = alloc_n(p, &L.inj, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.state, (size_t)L.st_sx * L.st_sy * L.st_sz)) != TL_OK) return s;
+  return TL_OK;
+}
+
+tl_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TL_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? TL_ENOMEM : TL_ECUDA;
+}
+
+// ---- laser path (Section 5.2-5.3): tracks back to back from t = 0 --------
+bool laser_at(const tl_problem* p, double t, double* x, double* y) {
+  for (size_t j = 0; j < p->tracks.size(); ++j) {
+    if (t <= p->t_end[j]) {
+      const tl_track& k = p->tracks[j];
+      double f = (t - p->t_start[j]) / p->dur[j];
+      *x = k.x0 + f * (k.x1 - k.x0);
+      *y = k.y0 + f * (k.y1 - k.y0);
+      return true;
+    }
+  }
+  return false;
+}
+
+// Patch origin (coarse node indices) centring the patch on (x, y), clamped to the plate.
+void origin_at(const tl_problem* p, double x, double y, int* oi, int* oj) {
+  const tl_config& c = p->cfg;
+  const double hcx = c.Lx / c.NXc, hcy = c.Ly / c.NYc;
+  int ii = (int)std::floor((x - 0.5 * c.pNXc * hcx) / hcx + 0.5);
+  int jj = (int)std::floor((y - 0.5 * c.pNYc * hcy) / hcy + 0.5);
+  *oi = std::min(std::max(ii, 0), c.NXc - c.pNXc);
+  *oj = std::min(std::max(jj, 0), c.NYc - c.pNYc);
+}
+
+// Origin for macro step n: laser position at t_n + Dt/2; unchanged if the laser is off.
+void origin_for(const tl_problem* p, int n, int* oi, int* oj) {
+  const double Dt = p->cfg.dt_coarse;
+  double x, y;
+  if (!laser_at(p, n * Dt + 0.5 * Dt, &x, &y)) return;
+  origin_at(p, x, y, oi, oj);
+}
+
+LoadSpec gaussian_load(const tl_problem* p, const Level& L, double t, double ox, double oy) {
+  LoadSpec ld{};
+  double x, y;
+  if (!laser_at(p, t, &x, &y) || p->cfg.P == 0.0) {
+    ld.kind = 0;
+    return ld;
+  }
+  const double R = p->cfg.radius;
+  ld.kind = 1;
+  ld.amp = 3.0 * p->cfg.eta * p->cfg.P / (M_PI * R * R);
+  ld.alpha = std::sqrt(3.0) / R;
+  ld.xc = x;
+  ld.yc = y;
+  ld.ox = ox;
+  ld.oy = oy;
+  (void)L;
+  return ld;
+}
+
+// Coarse source over [t_n, t_n + Dt]: surface analogue of Q+ = P eta/(r d v Dt)
+// (Section 5.2) on the R-wide rectangle swept along each axis-aligned track.
+LoadSpec box_load(const tl_problem* p, int n) {
+  LoadSpec ld{};
+  const tl_config& c = p->cfg;
+  const double Dt = c.dt_coarse, R = c.radius;
+  const double ta = n * Dt, tb = (n + 1) * Dt;
+  ld.kind = 2;
+  ld.ox = 0.0;
+  ld.oy = 0.0;
+  for (size_t j = 0; j < p->tracks.size() && ld.nrect < MAXRECT; ++j) {
+    double a = std::max(ta, p->t_start[j]);
+    double b = std::min(tb, p->t_end[j]);
+    if (!(b > a)) continue;
+    const tl_track& k = p->tracks[j];
+    double fa = (a - p->t_start[j]) / p->dur[j], fb = (b - p->t_start[j]) / p->dur[j];
+    double xa = k.x0 + fa * (k.x1 - k.x0), ya = k.y0 + fa * (k.y1 - k.y0);
+    double xb = k.x0 + fb * (k.x1 - k.x0), yb = k.y0 + fb * (k.y1 - k.y0);
+    double q = c.eta * c.P / (R * k.speed * Dt);
+    double* rc = ld.rect[ld.nrect];
+    if (k.y0 == k.y1) {
+      rc[0] = std::min(xa, xb); rc[1] = std::max(xa, xb);
+      rc[2] = k.y0 - 0.5 * R;   rc[3] = k.y0 + 0.5 * R;
+    } else {
+      rc[0] = k.x0 - 0.5 * R;   rc[1] = k.x0 + 0.5 * R;
+      rc[2] = std::min(ya, yb); rc[3] = std::max(ya, yb);
+    }
+    rc[4] = q;
+    ld.nrect++;
+  }
+  if (ld.nrect == 0 || c.P == 0.0) ld.kind = 0;
+  return ld;
+}
+
+void fill_common(const tl_problem* p, const Level& L, SolveArgs<double>& a) {
+  a.g = L.g;
+  a.t = L.t;
+  a.u = L.u;
+  a.r = L.r;
+  a.p0 = L.p0;
+  a.p1 = L.p1;
+  a.q = L.q;
+  a.X = L.X;
+  a.dinv = L.dinv;
+  a.s_e = L.s_e;
+  a.k_e = L.k_e;
+  a.F = L.F;
+  a.state = L.state;
+  const tl_config& c = p->cfg;
+  a.mat = Material{c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref, c.powder_factor, c.T_melt};
+  a.tol = c.tol;
+  a.max_iter = c.max_iter;
+  std::memcpy(a.Mc, L.Mc, sizeof a.Mc);
+  std::memcpy(a.Kc, L.Kc, sizeof a.Kc);
+  a.Md = L.Md;
+  a.Kd = L.Kd;
+  a.vol8 = L.vol8;
+  std::memcpy(a.Mhat, L.Mhat, sizeof a.Mhat);
+  std::memcpy(a.Khat, L.Khat, sizeof a.Khat);
+  a.bar = Barrier{p->bar, p->bar + 1, p->status};
+  a.red = p->red;
+  a.red_stride = p->red_stride;
+  a.stats = p->stats;
+}
+
+tl_status launch_solve(tl_problem* p, const Level& L, SolveArgs<double>& a) {
+  void* args[] = {(void*)&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel<double>, dim3(L.grid), dim3(NT), args, 0,
+                                              p->stream);
+  p->launches++;
+  return cuda_status(e);
+}
+
+int fine_dir_faces(const tl_problem* p) {
+  const tl_config& c = p->cfg;
+  int f = 16;  // patch bottom: interface or plate bottom, Dirichlet either way
+  if (p->oi > 0) f |= 1;
+  if (p->oi + c.pNXc < c.NXc) f |= 2;
+  if (p->oj > 0) f |= 4;
+  if (p->oj + c.pNYc < c.NYc) f |= 8;
+  return f;
+}
+
+void injection_box(const tl_problem* p, int box[6]) {
+  const tl_config& c = p->cfg;
+  int f = fine_dir_faces(p);
+  box[0] = p->oi + ((f & 1) ? 1 : 0);
+  box[1] = p->oi + c.pNXc - ((f & 2) ? 1 : 0);
+  box[2] = p->oj + ((f & 4) ? 1 : 0);
+  box[3] = p->oj + c.pNYc - ((f & 8) ? 1 : 0);
+  box[4] = p->ok + 1;
+  box[5] = c.NZc;
+}
+
+tl_status coarse_solve(tl_problem* p, bool correct) {
+  const tl_config& c = p->cfg;
+  Level& L = p->C;
+  SolveArgs<double> a{};
+  fill_common(p, L, a);
+  a.T_in = L.T;
+  a.T_out = correct ? L.T : L.T2;
+  a.st_sx = L.g.nx;
+  a.st_sy = L.g.ny;
+  a.st_ox = 0;
+  a.st_oy = 0;
+  a.dir.faces = 16;
+  if (correct) {
+    injection_box(p, a.dir.box);
+  } else {
+    a.dir.box[0] = 1; a.dir.box[1] = 0; a.dir.box[2] = 1; a.dir.box[3] = 0; a.dir.box[4] = 1; a.dir.box[5] = 0;
+  }
+  a.dv.kind = 1;
+  a.dv.T_bottom = c.T_bottom;
+  a.dv.inj = L.inj;
+  if (c.coarse_source == 1)
+    a.ld = gaussian_load(p, L, (p->n + 1) * c.dt_coarse, 0.0, 0.0);
+  else
+    a.ld = box_load(p, p->n);
+  a.dt = c.dt_coarse;
+  a.energy = correct ? c.energy : 0;
+  a.update_state = correct ? 1 : 0;
+  a.level = 0;
+  return launch_solve(p, L, a);
+}
+
+tl_status fine_solve(tl_problem* p, int i) {
+  const tl_config& c = p->cfg;
+  Level& L = p->Fi;
+  SolveArgs<double> a{};
+  fill_common(p, L, a);
+  a.T_in = L.T;
+  a.T_out = L.T;
+  a.st_sx = L.st_sx;
+  a.st_sy = L.st_sy;
+  a.st_ox = p->oi * c.r;
+  a.st_oy = p->oj * c.r;
+  a.dir.faces = fine_dir_faces(p);
+  a.dir.box[0] = 1; a.dir.box[1] = 0; a.dir.box[2] = 1; a.dir.box[3] = 0; a.dir.box[4] = 1; a.dir.box[5] = 0;
+  a.dv.kind = 0;
+  a.dv.T_bottom = c.T_bottom;
+  a.dv.w = c.bc_weight_literal ? (double)i / c.m : (double)(i + 1) / c.m;
+  a.dv.Tc0 = p->C.T;
+  a.dv.Tc1 = p->C.T2;
+  a.dv.cg = p->C.g;
+  a.dv.oi = p->oi;
+  a.dv.oj = p->oj;
+  a.dv.ok = p->ok;
+  a.dv.r = c.r;
+  const double dt = c.dt_coarse / c.m;
+  const double t = ((double)p->n * c.m + i + 1) * dt;
+  a.ld = gaussian_load(p, L, t, p->oi * (c.Lx / c.NXc), p->oj * (c.Ly / c.NYc));
+  a.dt = dt;
+  a.energy = c.energy;
+  a.update_state = 1;
+  a.level = 1;
+  return launch_solve(p, L, a);
+}
+
+tl_status validate(const tl_config* c) {
+  if (!c) return TL_EINVAL;
+  if (!(c->Lx > 0 && c->Ly > 0 && c->Lz > 0)) return TL_EINVAL;
+  if (c->NXc < 1 || c->NYc < 1 || c->NZc < 1) return TL_EINVAL;
+  if (c->pNXc < 1 || c->pNYc < 1 || c->pNZc < 1) return TL_EINVAL;
+  if (c->pNXc > c->NXc || c->pNYc > c->NYc || c->pNZc > c->NZc) return TL_EINVAL;
+  if (c->r < 1 || c->m < 1 || c->r > 64 || c->m > 1024) return TL_EINVAL;
+  if (!(c->dt_coarse > 0)) return TL_EINVAL;
+  if (!(c->rho > 0) || !(c->c0 > 0) || !(c->k0 > 0) || !(c->powder_factor > 0)) return TL_EINVAL;
+  if (!(c->radius > 0) || !(c->P >= 0) || !(c->eta >= 0)) return TL_EINVAL;
+  if (c->ntracks < 0 || (c->ntracks > 0 && !c->path)) return TL_EINVAL;
+  if (!(c->tol > 0) || c->max_iter < 1) return TL_EINVAL;
+  if (c->precision != TL_FP64 && c->precision != TL_FP32_REFINED) return TL_EINVAL;
+  if (c->precision == TL_FP32_REFINED) return TL_EINVAL;  // not available in this build yet
+  if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
+  for (int j = 0; j < c->ntracks; ++j) {
+    const tl_track& k = c->path[j];
+    if (!(k.speed > 0)) return TL_EINVAL;
+    if (k.x0 == k.x1 && k.y0 == k.y1) return TL_EINVAL;
+    if (c->coarse_source == 0 && k.x0 != k.x1 && k.y0 != k.y1) return TL_EINVAL;
+  }
+  if (c->coarse_source != 0 && c->coarse_source != 1) return TL_EINVAL;
+  const long long fx = (long long)c->pNXc * c->r, fy = (long long)c->pNYc * c->r, fz = (long long)c->pNZc * c->r;
+  if ((fx + 1) * (fy + 1) * (fz + 1) > (1LL << 31)) return TL_EINVAL;
+  return TL_OK;
+}
+
+void release(tl_problem* p) {
+  for (void* ptr : p->allocs) {
+    if (p->cfg.free)
+      p->cfg.free(ptr, (void*)p->stream, p->cfg.alloc_ctx);
+    else
+      cudaFree(ptr);
+  }
+  p->allocs.clear();
+}
+
+tl_status launch_fill(tl_problem* p, double* x, size_t n, double v) {
+  fill_kernel<<<std::max(1, std::min(1024, (int)((n + 255) / 256))), 256, 0, p->stream>>>(x, (long long)n, v);
+  return cuda_status(cudaGetLastError());
+}
+
+tl_status move_patch(tl_problem* p) {
+  int ni = p->oi, nj = p->oj;
+  origin_for(p, p->n, &ni, &nj);
+  if (ni == p->oi && nj == p->oj) return TL_OK;
+  Level& F = p->Fi;
+  const long long nn = (long long)F.g.nnx * F.g.nny * F.g.nnz;
+  int blocks = (int)std::min<long long>(4096, (nn + 255) / 256);
+  move_patch_kernel<<<blocks, 256, 0, p->stream>>>(F.g, p->C.g, F.T, F.T2, p->C.T, p->oi, p->oj, ni, nj, p->ok,
+                                                   p->cfg.r);
+  p->launches++;
+  tl_status s = cuda_status(cudaGetLastError());
+  if (s != TL_OK) return s;
+  std::swap(F.T, F.T2);
+  p->oi = ni;
+  p->oj = nj;
+  p->patch_moves++;
+  return TL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tl_status_string(tl_status s) {
+  switch (s) {
+    case TL_OK: return "ok";
+    case TL_EINVAL: return "invalid argument";
+    case TL_ENOMEM: return "device allocation failed";
+    case TL_ENOCONV: return "CG did not converge within max_iter";
+    case TL_ESTATE: return "call out of order";
+    case TL_ECUDA: return "CUDA runtime error";
+    case TL_ETIMEOUT: return "device barrier timed out";
+  }
+  return "unknown status";
+}
+
+tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
+  if (!out) return TL_EINVAL;
+  *out = nullptr;
+  tl_status s = validate(cfg);
+  if (s != TL_OK) return s;
+  tl_problem* p = new (std::nothrow) tl_problem();
+  if (!p) return TL_ENOMEM;
+  p->cfg = *cfg;
+  p->tracks.assign(cfg->path, cfg->path + cfg->ntracks);
+  p->cfg.path = nullptr;
+  double t = 0.0;
+  for (const tl_track& k : p->tracks) {
+    double d = std::hypot(k.x1 - k.x0, k.y1 - k.y0) / k.speed;
+    p->t_start.push_back(t);
+    p->dur.push_back(d);
+    t = t + d;
+    p->t_end.push_back(t);
+  }
+  p->stream = (cudaStream_t)cfg->stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel<double>, NT, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    delete p;
+    cudaGetLastError();
+    return TL_ECUDA;
+  }
+  p->max_coop = per_sm * p->nsm;
+  const tl_config& c = p->cfg;
+  const int r = c.r;
+  // coarse level
+  Level& C = p->C;
+  C.g = Grid3{c.NXc, c.NYc, c.NZc, c.NXc + 1, c.NYc + 1, c.NZc + 1, c.Lx / c.NXc, c.Ly / c.NYc, c.Lz / c.NZc};
+  C.st_sx = c.NXc; C.st_sy = c.NYc; C.st_sz = c.NZc;
+  // fine patch; its states live in a plate-wide map over the patch depth
+  Level& F = p->Fi;
+  F.g = Grid3{c.pNXc * r, c.pNYc * r, c.pNZc * r, c.pNXc * r + 1, c.pNYc * r + 1, c.pNZc * r + 1,
+              C.g.hx / r, C.g.hy / r, C.g.hz / r};
+  F.st_sx = c.NXc * r; F.st_sy = c.NYc * r; F.st_sz = c.pNZc * r;
+  element_constants(C);
+  element_constants(F);
+  choose_tiling(C, p->nsm);
+  choose_tiling(F, p->nsm);
+  C.grid = std::min(p->max_coop, C.t.ntx * C.t.nty * C.t.ntz);
+  F.grid = std::min(p->max_coop, F.t.ntx * F.t.nty * F.t.ntz);
+  p->red_stride = std::max(C.grid, F.grid);
+  if ((s = alloc_level(p, C, true)) != TL_OK || (s = alloc_level(p, F, false)) != TL_OK ||
+      (s = alloc_n(p, &p->bar, 2)) != TL_OK || (s = alloc_n(p, &p->status, 1)) != TL_OK ||
+      (s = alloc_n(p, &p->red, (size_t)RS_N * p->red_stride)) != TL_OK ||
+      (s = alloc_n(p, &p->stats, 1)) != TL_OK) {
+    release(p);
+    delete p;
+    return s;
+  }
+  p->ok = c.NZc - c.pNZc;
+  p->oi = 0;
+  p->oj = 0;
+  {
+    // laser position at Dt/2, or the plate centre when the laser is off then
+    double x = 0.5 * c.Lx, y = 0.5 * c.Ly;
+    laser_at(p, 0.5 * c.dt_coarse, &x, &y);
+    origin_at(p, x, y, &p->oi, &p->oj);
+  }
+  const size_t ncn = (size_t)C.g.nnx * C.g.nny * C.g.nnz, nfn = (size_t)F.g.nnx * F.g.nny * F.g.nnz;
+  const int nb = 256;
+  if ((s = launch_fill(p, C.T, ncn, c.T0)) != TL_OK || (s = launch_fill(p, C.T2, ncn, c.T0)) != TL_OK ||
+      (s = launch_fill(p, F.T, nfn, c.T0)) != TL_OK || (s = launch_fill(p, C.inj, ncn, c.T0)) != TL_OK) {
+    release(p);
+    delete p;
+    return s;
+  }
+  // buffers read before being written in a solve start at zero
+  for (Level* L : {&C, &F}) {
+    size_t nn = (size_t)L->g.nnx * L->g.nny * L->g.nnz;
+    cudaMemsetAsync(L->p0, 0, nn * sizeof(double), p->stream);
+    cudaMemsetAsync(L->p1, 0, nn * sizeof(double), p->stream);
+    cudaMemsetAsync(L->X, 0, nn * NXB * sizeof(double), p->stream);
+  }
+  cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned int), p->stream);
+  cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+  cudaMemsetAsync(p->stats, 0, sizeof(DevStats), p->stream);
+  init_state_kernel<<<256, nb, 0, p->stream>>>(C.state, C.st_sx, C.st_sy, C.st_sz, 0.0, C.g.hz, c.Lz,
+                                               c.powder_depth);
+  init_state_kernel<<<1024, nb, 0, p->stream>>>(F.state, F.st_sx, F.st_sy, F.st_sz, p->ok * C.g.hz, F.g.hz, c.Lz,
+                                                c.powder_depth);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    s = cuda_status(e);
+    release(p);
+    delete p;
+    return s;
+  }
+  *out = p;
+  return TL_OK;
+}
+
+tl_status tl_coarse_step(tl_problem* p, tl_phase phase) {
+  if (!p) return TL_EINVAL;
+  if (phase == TL_PREDICT) {
+    if (p->phase != NEED_PREDICT) return TL_ESTATE;
+    tl_status s = move_patch(p);
+    if (s != TL_OK) return s;
+    s = coarse_solve(p, false);
+    if (s != TL_OK) return s;
+    p->phase = IN_SUBSTEPS;
+    p->sub = 0;
+    return TL_OK;
+  }
+  if (phase == TL_CORRECT) {
+    if (p->phase != NEED_CORRECT) return TL_ESTATE;
+    tl_status s = coarse_solve(p, true);
+    if (s != TL_OK) return s;
+    p->phase = NEED_PREDICT;
+    p->n++;
+    return TL_OK;
+  }
+  return TL_EINVAL;
+}
+
+tl_status tl_fine_substeps(tl_problem* p, int nsub) {
+  if (!p || nsub < 0) return TL_EINVAL;
+  if (p->phase != IN_SUBSTEPS || p->sub + nsub > p->cfg.m) return TL_ESTATE;
+  for (int k = 0; k < nsub; ++k) {
+    tl_status s = fine_solve(p, p->sub);
+    if (s != TL_OK) return s;
+    p->sub++;
+  }
+  return TL_OK;
+}
+
+tl_status tl_restrict(tl_problem* p) {
+  if (!p) return TL_EINVAL;
+  if (p->phase != IN_SUBSTEPS || p->sub != p->cfg.m) return TL_ESTATE;
+  int box[6];
+  injection_box(p, box);
+  if (box[0] <= box[1] && box[2] <= box[3] && box[4] <= box[5]) {
+    long long nb = (long long)(box[1] - box[0] + 1) * (box[3] - box[2] + 1) * (box[5] - box[4] + 1);
+    int blocks = (int)std::min<long long>(1024, (nb + 255) / 256);
+    restrict_kernel<<<blocks, 256, 0, p->stream>>>(p->Fi.g, p->C.g, p->Fi.T, p->C.inj, box[0], box[1], box[2],
+                                                   box[3], box[4], box[5], p->oi, p->oj, p->ok, p->cfg.r);
+    p->launches++;
+    tl_status s = cuda_status(cudaGetLastError());
+    if (s != TL_OK) return s;
+  }
+  p->phase = NEED_CORRECT;
+  return TL_OK;
+}
+
+tl_status tl_sync(tl_problem* p) {
+  if (!p) return TL_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = 0;
+  e = cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  return (tl_status)st;
+}
+
+tl_status tl_macro_steps(tl_problem* p, int nmacro) {
+  if (!p || nmacro < 0) return TL_EINVAL;
+  for (int k = 0; k < nmacro; ++k) {
+    tl_status s;
+    if ((s = tl_coarse_step(p, TL_PREDICT)) != TL_OK) return s;
+    if ((s = tl_fine_substeps(p, p->cfg.m)) != TL_OK) return s;
+    if ((s = tl_restrict(p)) != TL_OK) return s;
+    if ((s = tl_coarse_step(p, TL_CORRECT)) != TL_OK) return s;
+  }
+  return tl_sync(p);
+}
+
+size_t tl_node_count(const tl_problem* p, tl_level level) {
+  if (!p) return 0;
+  const Level& L = level == TL_COARSE ? p->C : p->Fi;
+  if (level != TL_COARSE && level != TL_FINE) return 0;
+  return (size_t)L.g.nnx * L.g.nny * L.g.nnz;
+}
+
+tl_status tl_get_temperature(const tl_problem* p, tl_level level, double* host_out, size_t n, int origin_out[3]) {
+  if (!p || !host_out || (level != TL_COARSE && level != TL_FINE)) return TL_EINVAL;
+  if (n != tl_node_count(p, level)) return TL_EINVAL;
+  const Level& L = level == TL_COARSE ? p->C : p->Fi;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(host_out, L.T, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (origin_out) {
+    origin_out[0] = p->oi;
+    origin_out[1] = p->oj;
+    origin_out[2] = p->ok;
+  }
+  return TL_OK;
+}
+
+tl_status tl_get_state(const tl_problem* p, tl_level level, uint8_t* host_out, size_t n) {
+  if (!p || !host_out) return TL_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (level == TL_COARSE) {
+    const Level& C = p->C;
+    if (n != (size_t)C.g.nx * C.g.ny * C.g.nz) return TL_EINVAL;
+    e = cudaMemcpy(host_out, C.state, n, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+  }
+  if (level != TL_FINE) return TL_EINVAL;
+  const Level& F = p->Fi;
+  if (n != (size_t)F.g.nx * F.g.ny * F.g.nz) return TL_EINVAL;
+  // gather the patch window of the plate-wide map, one row at a time
+  const size_t ox = (size_t)p->oi * p->cfg.r, oy = (size_t)p->oj * p->cfg.r;
+  for (int k = 0; k < F.g.nz; ++k) {
+    const size_t plane = (size_t)F.st_sx * F.st_sy * k;
+    e = cudaMemcpy2D(host_out + (size_t)F.g.nx * F.g.ny * k, (size_t)F.g.nx, F.state + plane + oy * F.st_sx + ox,
+                     (size_t)F.st_sx, (size_t)F.g.nx, (size_t)F.g.ny, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return TL_OK;
+}
+
+tl_status tl_get_stats(const tl_problem* p, tl_stats* out) {
+  if (!p || !out) return TL_EINVAL;
+  DevStats d{};
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&d, p->stats, sizeof d, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::memset(out, 0, sizeof *out);
+  out->macro_steps = p->n;
+  out->substeps = (int64_t)p->n * p->cfg.m + (p->phase == IN_SUBSTEPS || p->phase == NEED_CORRECT ? p->sub : 0);
+  out->cg_iters_coarse = d.iters[0];
+  out->cg_iters_fine = d.iters[1];
+  out->solves_coarse = d.solves[0];
+  out->solves_fine = d.solves[1];
+  out->max_iters_coarse = d.max_iters[0];
+  out->max_iters_fine = d.max_iters[1];
+  out->origin[0] = p->oi;
+  out->origin[1] = p->oj;
+  out->origin[2] = p->ok;
+  out->patch_moves = p->patch_moves;
+  out->launches = p->launches;
+  out->energy_coarse_stored = d.e_stored[0];
+  out->energy_coarse_laser = d.e_laser[0];
+  out->energy_coarse_flux = d.e_flux[0];
+  out->energy_fine_stored = d.e_stored[1];
+  out->energy_fine_laser = d.e_laser[1];
+  out->energy_fine_flux = d.e_flux[1];
+  out->time = p->n * p->cfg.dt_coarse;
+  return TL_OK;
+}
+
+void tl_destroy_problem(tl_problem* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  release(p);
+  delete p;
+}
+
+}  // extern "C"

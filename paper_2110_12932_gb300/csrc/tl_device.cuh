@@ -1,0 +1,162 @@
+// Device-side building blocks of the two-level LPBF heat solve (sm_103a).
+//
+// Discretisation: one backward-Euler step of the heat equation (Section 2.1,
+// Eq. thermalEqn, without the latent term) on a uniform mesh of trilinear
+// hexahedra, with element-constant s_e = rho c_e / dt and k_e:
+//     (sum_e s_e Mhat + k_e Khat) T^{k+1} = (sum_e s_e Mhat) T^k + F.
+// On a box element both element matrices are Kronecker products of the 1D
+// matrices M1 = (h/6)[[2,1],[1,2]] and K1 = (1/h)[[1,-1],[-1,1]], which share
+// the eigenvectors [1,1] and [1,-1].  With the 2-point Hadamard transform H the
+// element operator is therefore H3 diag(lambda_e) H3 with eight eigenvalues
+//     lambda_e[m] = s_e Mc[m] + k_e Kc[m]   (the 1/8 of H3^-1 folded in),
+// so a matrix-free apply costs one forward and one backward separable
+// Hadamard transform plus eight multiplies per element.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tl {
+
+enum : uint8_t { POWDER = 0, SOLID = 1, MELTED = 2 };
+
+enum Status : int {
+  ST_OK = 0,
+  ST_NOCONV = -3,
+  ST_TIMEOUT = -6,
+};
+
+struct Material {
+  double rho, c0, c1, k0, k1, Tref, powder_factor, T_melt;
+};
+
+struct Grid3 {
+  int nx, ny, nz;     // elements
+  int nnx, nny, nnz;  // nodes (n* = elements + 1)
+  double hx, hy, hz;
+};
+
+__host__ __device__ inline long long node_id(const Grid3& g, int i, int j, int k) {
+  return (long long)i + (long long)g.nnx * ((long long)j + (long long)g.nny * k);
+}
+__host__ __device__ inline long long elem_id(const Grid3& g, int i, int j, int k) {
+  return (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
+}
+
+// Balanced split of n items into parts: part a covers [a n / parts, (a+1) n / parts).
+__host__ __device__ inline int split_lo(int n, int parts, int a) {
+  return (int)(((long long)a * n) / parts);
+}
+
+// ---------------------------------------------------------------------------
+// Time-limited grid barrier for cooperative (co-resident) launches.
+// Every wait gives up after `limit_ns` of global time, records ST_TIMEOUT and
+// returns false; a block that sees an error recorded by another returns
+// false too, so that all blocks leave the kernel.
+// ---------------------------------------------------------------------------
+struct Barrier {
+  unsigned int* count;
+  unsigned int* gen;
+  int* status;  // sticky device status word
+};
+
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ inline unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ inline int ld_volatile_i32(const int* p) {
+  return *(volatile const int*)p;
+}
+
+__device__ inline bool grid_sync(const Barrier& b, unsigned long long limit_ns = 1000000000ull) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int g = ld_acquire_u32(b.gen);
+    __threadfence();
+    unsigned int arrived = atomicAdd(b.count, 1u);
+    if (arrived == gridDim.x - 1) {
+      __threadfence();  // acquire side: every arrival's earlier writes
+      atomicExch(b.count, 0u);
+      st_release_u32(b.gen, g + 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(b.gen) == g) {
+        if (ld_volatile_i32(b.status) == ST_TIMEOUT) { ok = 0; break; }
+        if (global_ns() - t0 > limit_ns) {
+          atomicExch(b.status, (int)ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (ld_volatile_i32(b.status) == ST_TIMEOUT) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: per-thread partial -> block sum (fixed shuffle
+// tree) -> one slot per block; after a grid barrier every block sums the
+// slots in the same fixed order, so all blocks hold bitwise equal totals.
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ inline void block_reduce_store(double (&v)[NV], double* slots, int stride) {
+  __shared__ double s_part[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    double x = v[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) s_part[a][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double x = lane < nwarps ? s_part[a][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) slots[(size_t)a * stride + blockIdx.x] = x;
+    }
+  }
+  __syncthreads();
+}
+
+template <int NV>
+__device__ inline void grid_total(const double* slots, int stride, double (&out)[NV]) {
+  __shared__ double s_tot[NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double x = 0.0;
+      for (int s = lane; s < (int)gridDim.x; s += 32) x += __ldcg(slots + (size_t)a * stride + s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) s_tot[a] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = s_tot[a];
+  __syncthreads();
+}
+
+}  // namespace tl

@@ -1,0 +1,183 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bar (FP64 path): relative L2 temperature error <= 1e-9 on both levels, and
+element states bit-exact except where an element mean lies within 1e-6 K of
+T_melt in either run (ties are counted and must be zero on these inputs).
+"""
+import numpy as np
+import pytest
+
+from oracle import twolevel as TL
+from paper_2110_12932_gb300 import build as tlbuild
+from paper_2110_12932_gb300 import tl, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    tlbuild.build()
+    return tl.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def compare(prob, ref, what=""):
+    Tf, org = prob.temperature(tl.TL_FINE)
+    Tc, _ = prob.temperature(tl.TL_COARSE)
+    assert tuple(org) == tuple(ref.origin), (what, org, ref.origin)
+    ef, ec = rel(Tf, ref.Tf), rel(Tc, ref.Tc)
+    assert ef <= TOL and ec <= TOL, (what, ef, ec)
+    sf = prob.state(tl.TL_FINE)
+    sc = prob.state(tl.TL_COARSE)
+    ref_sf = ref.fine_state().reshape(-1)
+    mesh = ref.fine_mesh()
+    tie_f = np.abs(mesh.element_mean(ref.Tf) - ref.cfg["T_melt"]) < 1e-6
+    tie_c = np.abs(ref.coarse.element_mean(ref.Tc) - ref.cfg["T_melt"]) < 1e-6
+    assert tie_f.sum() == 0 and tie_c.sum() == 0, (what, "threshold ties")
+    assert np.array_equal(sf, ref_sf), (what, np.count_nonzero(sf != ref_sf))
+    assert np.array_equal(sc, ref.state_c), (what, np.count_nonzero(sc != ref.state_c))
+    return ef, ec
+
+
+def run_both(cfg, nmacro, check_every=1):
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg)
+    errs = []
+    done = 0
+    while done < nmacro:
+        k = min(check_every, nmacro - done)
+        prob.macro_steps(k)
+        ref.run(k)
+        done += k
+        errs.append(compare(prob, ref, f"macro {done}"))
+    return prob, ref, errs
+
+
+def test_single_track_tiny_full_run():
+    cfg = workloads.workload("single_track_tiny")
+    prob, ref, errs = run_both(cfg, cfg["macro_steps"], check_every=5)
+    st = prob.stats()
+    assert st["macro_steps"] == 50 and st["substeps"] == 200
+    assert st["patch_moves"] > 0
+    melted = np.count_nonzero(ref.state_map == TL.MELTED)
+    assert melted > 0
+    prob.close()
+
+
+def test_energy_account_matches_oracle_and_identity():
+    cfg = workloads.workload("single_track_tiny")
+    prob, ref, _ = run_both(cfg, 12, check_every=12)
+    st = prob.stats()
+    for lvl in ("fine", "coarse"):
+        s, l, f = (st[f"energy_{lvl}_{k}"] for k in ("stored", "laser", "flux"))
+        assert abs(s - l - f) <= 1e-9 * max(abs(s), abs(l)), lvl
+        for k in ("stored", "laser", "flux"):
+            o = ref.energy[f"{lvl}_{k}"]
+            assert abs(st[f"energy_{lvl}_{k}"] - o) <= 1e-8 * max(abs(o), abs(l)), (lvl, k)
+    prob.close()
+
+
+def test_ragged_tiles_and_odd_ratios():
+    # 15 x 9 x 9 fine elements: ragged y tiles; r = 3, m = 3
+    cfg = workloads.workload("single_track_tiny", NXc=13, NYc=7, NZc=5, Lx=13 * 125e-6,
+                             Ly=7 * 125e-6, Lz=5 * 125e-6, pNXc=5, pNYc=3, pNZc=3, r=3, m=3,
+                             tracks=[(0.0, 0.45e-3, 13 * 125e-6, 0.45e-3, 0.8)], macro_steps=10)
+    run_both(cfg, 10, check_every=5)
+
+
+def test_several_x_tiles():
+    # 36 x 12 x 8 fine elements: two x tiles (32 + 4) and two y tiles (8 + 4)
+    cfg = workloads.workload("single_track_tiny", pNXc=9, pNYc=3, pNZc=2, r=4, m=2)
+    run_both(cfg, 8, check_every=4)
+
+
+def test_patch_covering_plate_is_single_level():
+    cfg = workloads.workload("single_track_tiny", NXc=8, NYc=4, NZc=2, pNXc=8, pNYc=4, pNZc=2,
+                             r=2, m=2)
+    prob, ref, _ = run_both(cfg, 6, check_every=3)
+    sl = TL.SingleLevel(cfg, 16, 8, 4, cfg["dt_coarse"] / 2)
+    for _ in range(12):
+        sl.step()
+    Tf, _ = prob.temperature(tl.TL_FINE)
+    assert rel(Tf, sl.T) <= TOL
+
+
+def test_unit_ratios_gaussian_coarse_source():
+    cfg = workloads.workload("single_track_tiny", r=1, m=1, coarse_source=1, pNXc=6, pNYc=4, pNZc=2)
+    run_both(cfg, 20, check_every=10)
+
+
+def test_literal_bc_weight_and_laser_off_tail():
+    # printed weight i/m; the scan ends before the run does (laser off, patch parked)
+    cfg = workloads.workload("single_track_tiny", bc_weight_literal=1,
+                             tracks=[(0.2e-3, 0.5e-3, 1.0e-3, 0.5e-3, 0.8)])
+    run_both(cfg, 24, check_every=8)
+
+
+def test_no_tracks_stays_at_initial_temperature():
+    cfg = workloads.workload("single_track_tiny", tracks=[])
+    prob = tl.Problem(cfg)
+    prob.macro_steps(3)
+    Tf, org = prob.temperature(tl.TL_FINE)
+    assert np.all(Tf == cfg["T0"])
+    assert tuple(org) == (6, 2, 2)
+    prob.close()
+
+
+def test_multitrack_10mm_first_macro_step():
+    """Full-size fine patch (65 x 65 x 33 nodes) and coarse plate
+    (81 x 41 x 17), same launch configuration as the benchmark."""
+    cfg = workloads.workload("multitrack_10mm")
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    prob.macro_steps(1)
+    ref.run(1)
+    compare(prob, ref, "macro 1")
+    prob.close()
+
+
+def test_call_order_is_enforced():
+    cfg = workloads.workload("single_track_tiny")
+    prob = tl.Problem(cfg)
+    h = prob.h
+    assert tl.tl_fine_substeps(h, 1) == tl.TL_ESTATE
+    assert tl.tl_restrict(h) == tl.TL_ESTATE
+    assert tl.tl_coarse_step(h, tl.TL_CORRECT) == tl.TL_ESTATE
+    assert tl.tl_coarse_step(h, tl.TL_PREDICT) == tl.TL_OK
+    assert tl.tl_coarse_step(h, tl.TL_PREDICT) == tl.TL_ESTATE
+    assert tl.tl_fine_substeps(h, cfg["m"] + 1) == tl.TL_ESTATE
+    assert tl.tl_fine_substeps(h, 2) == tl.TL_OK
+    assert tl.tl_restrict(h) == tl.TL_ESTATE
+    assert tl.tl_fine_substeps(h, 2) == tl.TL_OK
+    assert tl.tl_restrict(h) == tl.TL_OK
+    assert tl.tl_coarse_step(h, tl.TL_CORRECT) == tl.TL_OK
+    assert tl.tl_sync(h) == tl.TL_OK
+    prob.close()
+
+
+def test_iteration_cap_reports_noconv_and_leaves_state():
+    cfg = workloads.workload("single_track_tiny", max_iter=1)
+    prob = tl.Problem(cfg)
+    T0f, _ = prob.temperature(tl.TL_FINE)
+    assert tl.tl_macro_steps(prob.h, 1) == tl.TL_ENOCONV
+    Tf, _ = prob.temperature(tl.TL_FINE)
+    Tc, _ = prob.temperature(tl.TL_COARSE)
+    assert np.array_equal(Tf, T0f)
+    assert np.all(Tc == cfg["T0"])
+    prob.close()
+
+
+def test_deterministic_reruns():
+    cfg = workloads.workload("single_track_tiny")
+    out = []
+    for _ in range(2):
+        prob = tl.Problem(cfg)
+        prob.macro_steps(10)
+        out.append(prob.temperature(tl.TL_FINE)[0])
+        prob.close()
+    assert np.array_equal(out[0], out[1])
