@@ -178,6 +178,50 @@ tl_status tl_get_state(const tl_problem* p, tl_level level, uint8_t* host_out, s
 /* Copy the counters (synchronises). */
 tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
 
+/* ---- Single step without device allocation ------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * may not allocate device memory while they run (a host application whose
+ * allocator owns the whole GPU, a real-time loop that forbids allocation
+ * after set-up, a plugin that is handed only its input and output buffers).
+ *
+ * tl_box_step_noalloc performs one backward-Euler step of the heat equation
+ * (the solve behind every tl_fine_substeps micro step) on the whole plate
+ * [0,Lx]x[0,Ly]x[0,Lz] meshed with nx*ny*nz hexahedra: T_bottom on z = 0,
+ * adiabatic sides and top, the surface Gaussian centred on (xc, yc) when
+ * laser_on, coefficients and powder factor from T_in and *state, states
+ * updated in place after the solve.  It allocates nothing: the caller passes
+ * device pointers to T_in and T_out ((nx+1)(ny+1)(nz+1) doubles, x fastest;
+ * they may be the same buffer) and state (nx*ny*nz bytes, read and written);
+ * all scratch comes from one fixed device array inside the library, sized for
+ * at most TL_NOALLOC_MAX_NODES nodes (about 8.4 MB, held on every GPU that
+ * loads the library until the process exits).
+ *
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  Every call shares the one array, so calls that overlap on the GPU
+ * (other threads, other streams) race and corrupt each other: serialise them.
+ * The call runs on `stream` (a cudaStream_t, NULL = legacy default stream),
+ * synchronises it and returns the solve's status: TL_OK, TL_ENOCONV (T_out and
+ * state left untouched), TL_ETIMEOUT, TL_ECUDA, or TL_EINVAL for NULL pointers,
+ * non-positive sizes or properties, or more than TL_NOALLOC_MAX_NODES nodes.
+ */
+#define TL_NOALLOC_MAX_NODES 65536
+
+typedef struct {
+  double Lx, Ly, Lz;      /* plate [m]                                          */
+  int nx, ny, nz;         /* hexahedra per direction                            */
+  double dt, T_bottom;    /* step [s], bottom Dirichlet value [K]               */
+  double rho, c0, c1, k0, k1, Tref, powder_factor, T_melt;  /* as in tl_config */
+  double P, eta, radius;  /* laser power [W], absorptivity, radius R [m]        */
+  double xc, yc;          /* laser centre at the end of the step [m]            */
+  int laser_on;           /* 0: no source                                       */
+  double tol;             /* relative CG residual                               */
+  int max_iter;           /* CG iteration cap                                   */
+} tl_box_step_desc;
+
+tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double* T_in, double* T_out,
+                              uint8_t* state, void* stream);
+
 /* Release every device buffer of the problem; NULL is ignored. */
 void tl_destroy_problem(tl_problem* p);
 

@@ -1,7 +1,7 @@
 """Compile the CUDA library ``libtl.so`` in-tree for sm_103a (GB300).
 
-The library is a single translation unit (csrc/tl_api.cu includes the device
-code); it links the CUDA runtime statically, so the only run-time dependency
+The library has two translation units (csrc/tl_api.cu, the two-level path,
+and csrc/tl_noalloc.cu, the allocation-free single step); it links the CUDA runtime statically, so the only run-time dependency
 is the driver.
 """
 from __future__ import annotations
@@ -13,7 +13,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtl.so")
-SOURCES = [os.path.join(HERE, "csrc", "tl_api.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "tl_api.cu"), os.path.join(HERE, "csrc", "tl_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("tl_device.cuh", "tl_solve.cuh")] + [
     os.path.join(ROOT, "include", "tl.h")]
 

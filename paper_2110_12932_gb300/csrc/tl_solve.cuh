@@ -626,8 +626,11 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs<R> a) {
 }
 
 // ---------------------------------------------------------------------------
-// Small kernels: patch motion and fine -> coarse injection.
+// Small kernels: patch motion and fine -> coarse injection.  Defined in the
+// two-level translation unit only (a unit that needs just the solve kernel
+// defines TL_SOLVE_KERNEL_ONLY before including this header).
 // ---------------------------------------------------------------------------
+#ifndef TL_SOLVE_KERNEL_ONLY
 
 // New fine field after the patch origin moved from (ooi, ooj) to (noi, noj)
 // (coarse node indices; z fixed): nodes inside the old patch keep their
@@ -677,5 +680,6 @@ __global__ void init_state_kernel(uint8_t* __restrict__ st, int sx, int sy, int 
     st[e] = (Lz - zc < depth) ? POWDER : SOLID;
   }
 }
+#endif  // TL_SOLVE_KERNEL_ONLY
 
 }  // namespace tl

@@ -69,10 +69,26 @@ class tl_stats(C.Structure):
     ]
 
 
+class tl_box_step_desc(C.Structure):
+    _fields_ = [
+        ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("dt", C.c_double), ("T_bottom", C.c_double),
+        ("rho", C.c_double), ("c0", C.c_double), ("c1", C.c_double),
+        ("k0", C.c_double), ("k1", C.c_double), ("Tref", C.c_double),
+        ("powder_factor", C.c_double), ("T_melt", C.c_double),
+        ("P", C.c_double), ("eta", C.c_double), ("radius", C.c_double),
+        ("xc", C.c_double), ("yc", C.c_double), ("laser_on", C.c_int),
+        ("tol", C.c_double), ("max_iter", C.c_int),
+    ]
+
+
+TL_NOALLOC_MAX_NODES = 65536
+
 EXPORTS = [
     "tl_create_problem", "tl_coarse_step", "tl_fine_substeps", "tl_restrict", "tl_macro_steps",
     "tl_sync", "tl_node_count", "tl_get_temperature", "tl_get_state", "tl_get_stats",
-    "tl_destroy_problem", "tl_status_string",
+    "tl_destroy_problem", "tl_status_string", "tl_box_step_noalloc",
 ]
 
 _lib = None
@@ -111,6 +127,9 @@ def load(path=LIB_PATH):
     lib.tl_destroy_problem.restype = None
     lib.tl_status_string.argtypes = [C.c_int]
     lib.tl_status_string.restype = C.c_char_p
+    lib.tl_box_step_noalloc.argtypes = [C.POINTER(tl_box_step_desc), C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]
+    lib.tl_box_step_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
@@ -202,6 +221,13 @@ def tl_get_stats(h):
 
 def tl_destroy_problem(h):
     load().tl_destroy_problem(h)
+
+
+def tl_box_step_noalloc(desc, T_in_ptr, T_out_ptr, state_ptr, stream=None):
+    """One allocation-free backward-Euler step (see include/tl.h); the
+    pointers are device addresses (ints), desc a tl_box_step_desc."""
+    return load().tl_box_step_noalloc(C.byref(desc), C.c_void_p(T_in_ptr), C.c_void_p(T_out_ptr),
+                                      C.c_void_p(state_ptr), C.c_void_p(stream))
 
 
 def _check(st, what):
