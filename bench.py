@@ -194,45 +194,21 @@ def l2_flush(buf):
     buf.fill_(1.0)
 
 
-def run_ours(args):
-    import torch
-
-    from paper_2110_12932_gb300 import build as tlbuild
-    from paper_2110_12932_gb300 import tl
-
-    rank, ws, local = dist_setup(args.gpus)
-    tlbuild.build()
-    tl.load()
-    cfg = workloads.workload(args.workload)
-    stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
-    nfn = fine_nodes(cfg)
+def timed_run(tl, torch, cfg, K, sp, stream, flush, sample_every=50):
+    """K macro steps of a fresh problem, each bracketed by CUDA events on the
+    library's stream, L2 flushed between steps outside the events; every
+    `sample_every`-th macro step also times each fine launch separately."""
     m = cfg["m"]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    # warm-up on a throw-away problem
-    wp = tl.Problem(cfg, stream=sp)
-    for _ in range(args.warmup):
-        wp.macro_steps(1)
-    wp.close()
-
-    # ---- device-timed run: inputs resident, per-step CUDA events, L2 flushed between steps
     prob = tl.Problem(cfg, stream=sp)
     st0 = prob.stats()
-    K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    fine_ev = []   # per fine-solve launch events (dominant kernel)
-    clocks = ClockSampler(local)
-    barrier(ws)
-    torch.cuda.synchronize()
-    clocks.start()
-    t_wall = time.perf_counter()
+    fine_ev = []
     for k in range(K):
         l2_flush(flush)
         ev[k][0].record(stream)
         prob.predict()
         for i in range(m):
-            if k % 50 == 0:
+            if k % sample_every == 0:
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 prob.fine_substeps(1)
@@ -244,36 +220,94 @@ def run_ours(args):
         prob.correct()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    status = prob.sync()
+    if status != 0:
+        raise RuntimeError(f"device status {status}")
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    st = prob.stats()
+    st["launches"] -= st0["launches"]
+    fine_ms = [a.elapsed_time(b) for a, b in fine_ev]
+    Tf, _ = prob.temperature(tl.TL_FINE)
+    Tc, _ = prob.temperature(tl.TL_COARSE)
+    sf = prob.state(tl.TL_FINE)
+    prob.close()
+    return dev_ms, fine_ms, st, Tf, Tc, sf
+
+
+def fine_flops(cfg, iters_per_launch):
+    r = cfg["r"]
+    ne = (cfg["pNXc"] * r) * (cfg["pNYc"] * r) * (cfg["pNZc"] * r)
+    nfn = fine_nodes(cfg)
+    return iters_per_launch * (FLOPS_APPLY_PER_ELEM * ne + FLOPS_VEC_PER_NODE * nfn) + 2 * FLOPS_APPLY_PER_ELEM * ne
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2110_12932_gb300 import build as tlbuild
+    from paper_2110_12932_gb300 import tl
+
+    rank, ws, local = dist_setup(args.gpus)
+    tlbuild.build()
+    tl.load()
+    cfg = workloads.workload(args.workload, precision=0, tol=1e-12)
+    cfg_ref = workloads.workload(args.workload, precision=1, tol=1e-10, tol_inner=1e-5)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    nfn = fine_nodes(cfg)
+    m = cfg["m"]
+    r = cfg["r"]
+    ne = (cfg["pNXc"] * r) * (cfg["pNYc"] * r) * (cfg["pNZc"] * r)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    K = args.steps
+
+    # warm-up on throw-away problems
+    for c in (cfg, cfg_ref):
+        wp = tl.Problem(c, stream=sp)
+        for _ in range(args.warmup):
+            wp.macro_steps(1)
+        wp.close()
+
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    dev_ms, fine_ms, st, Tf64, Tc64, sf64 = timed_run(tl, torch, cfg, K, sp, stream, flush)
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     barrier(ws)
-    st_status = prob.sync()
-    if st_status != 0:
-        raise RuntimeError(f"device status {st_status}")
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
     dev_ms = max_over_ranks(dev_ms, ws)
-    st = prob.stats()
-    launches = st["launches"] - st0["launches"]
-    fine_ms = [a.elapsed_time(b) for a, b in fine_ev]
-    fine_iters = st["cg_iters_fine"] / max(1, st["solves_fine"])
-    prob.close()
-
     work = ws * K * m * nfn
     value = work / (dev_ms / 1e3)
-
-    # dominant kernel (the fine solve): algorithmic FP64 flops per launch
-    r = cfg["r"]
-    ne = (cfg["pNXc"] * r) * (cfg["pNYc"] * r) * (cfg["pNZc"] * r)
-    flops_launch = fine_iters * (FLOPS_APPLY_PER_ELEM * ne + FLOPS_VEC_PER_NODE * nfn) + 2 * FLOPS_APPLY_PER_ELEM * ne
-    fine_launch_s = statistics.mean(fine_ms) / 1e3 if fine_ms else float("nan")
-    achieved = flops_launch / fine_launch_s / 1e12
+    fine_iters = st["cg_iters_fine"] / max(1, st["solves_fine"])
+    launch_s = statistics.mean(fine_ms) / 1e3
+    achieved = fine_flops(cfg, fine_iters) / launch_s / 1e12
     peak = 152 * 4 * 2.07e9 / 1e12   # FP64 FMA: 2 DFMA/clk/SM = 4 flop/clk/SM at 2.07 GHz
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "tl::solve_kernel<double> (fine micro step)",
-                "launch_ms": statistics.mean(fine_ms) if fine_ms else None,
-                "cg_iters_per_launch": fine_iters,
-                "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (derived); measured DFMA loop 1.20 TFLOP/s"}
+                "kernel": "tl::solve_kernel (FP64 fine micro step)",
+                "launch_ms": statistics.mean(fine_ms), "cg_iters_per_launch": fine_iters,
+                "flops_per_launch": fine_flops(cfg, fine_iters),
+                "peak_note": "FP64 pipe, derived: 152 SMs x 4 flop/clk x 2.07 GHz; a DFMA loop measured 1.20 TFLOP/s"}
+
+    # ---- the precision form on the same workload (FP32 inner CG, FP64 defect correction)
+    barrier(ws)
+    dev_ms_r, fine_ms_r, st_r, Tf32, Tc32, sf32 = timed_run(tl, torch, cfg_ref, K, sp, stream, flush)
+    dev_ms_r = max_over_ranks(dev_ms_r, ws)
+    value_r = work / (dev_ms_r / 1e3)
+    refined = {
+        "value": value_r, "unit": "DOF-substeps/s", "ms_per_step": dev_ms_r / K, "speedup_vs_fp64": value_r / value,
+        "tol": cfg_ref["tol"], "tol_inner": cfg_ref["tol_inner"],
+        "rel_l2_vs_fp64": {"fine": float(np.linalg.norm(Tf32 - Tf64) / np.linalg.norm(Tf64)),
+                           "coarse": float(np.linalg.norm(Tc32 - Tc64) / np.linalg.norm(Tc64))},
+        "melt_mask_agreement": float(np.mean((sf32 == tl.MELTED) == (sf64 == tl.MELTED))),
+        "fine_launch_ms": statistics.mean(fine_ms_r),
+        "inner_iters_per_solve": st_r["cg_iters_fine"] / max(1, st_r["solves_fine"]),
+        "outer_iters_per_solve": st_r["outer_iters_fine"] / max(1, st_r["solves_fine"]),
+        "gpu_launches": st_r["launches"] * ws,
+    }
 
     # ---- end to end through the public API: create, K steps, host read-back each step
     torch.cuda.synchronize()
@@ -303,10 +337,11 @@ def run_ours(args):
                            "m": m, "r": r, "tol": cfg["tol"], "precision": "fp64",
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "flushed (256 MB write) between timed macro steps, outside the events"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * ws,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"] * ws,
                 "clocks": clk, "wall_s": wall,
                 "cg_iters": {"fine_per_solve": fine_iters,
-                             "coarse_per_solve": st["cg_iters_coarse"] / max(1, st["solves_coarse"])}}
+                             "coarse_per_solve": st["cg_iters_coarse"] / max(1, st["solves_coarse"])},
+                "fp32_refined": refined}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -178,6 +178,17 @@ tl_status tl_get_state(const tl_problem* p, tl_level level, uint8_t* host_out, s
 /* Copy the counters (synchronises). */
 tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
 
+/* Phase timeline of the most recent solve on a level: *n_out pairs
+ * (marker, device time in ns) are recorded, the first min(n, cap) are copied
+ * to host_out[2*i], host_out[2*i+1].  Markers: 0 start, 1 coefficients /
+ * boundary data / load done, 2 right-hand side applies done, 3 initial
+ * residual done, 4 end of a CG pass, 5 refined: inner start, 6 refined: FP64
+ * correction apply done, 7 refined: outer sweep done, 8 update start, 9 end,
+ * 10 block 0 finished its share of a CG pass's apply (before the reduction).
+ * Synchronises.  Errors: TL_EINVAL, TL_ECUDA. */
+tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap,
+                              size_t* n_out);
+
 /* ---- Single step without device allocation ------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * may not allocate device memory while they run (a host application whose
@@ -193,7 +204,7 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
  * device pointers to T_in and T_out ((nx+1)(ny+1)(nz+1) doubles, x fastest;
  * they may be the same buffer) and state (nx*ny*nz bytes, read and written);
  * all scratch comes from one fixed device array inside the library, sized for
- * at most TL_NOALLOC_MAX_NODES nodes (about 8.4 MB, held on every GPU that
+ * at most TL_NOALLOC_MAX_NODES nodes (about 19.2 MB, held on every GPU that
  * loads the library until the process exits).
  *
  * The first call on a device looks up that array's device address (once per

@@ -26,15 +26,36 @@ struct Level {
   double* T2 = nullptr;   // coarse: predictor T~+; fine: move double buffer
   double* u = nullptr;
   double* r = nullptr;
+  double* r2 = nullptr;
   double* F = nullptr;
+  double* G = nullptr;
   double* p0 = nullptr;
   double* p1 = nullptr;
+  double* s0 = nullptr;
+  double* s1 = nullptr;
   double* q = nullptr;
   double* X = nullptr;
+  double* q2 = nullptr;
+  double* X2 = nullptr;
   double* dinv = nullptr;
   double* s_e = nullptr;
   double* k_e = nullptr;
+  double* lam = nullptr;
+  float* d32 = nullptr;   // refined precision only
+  float* r32 = nullptr;
+  float* r32b = nullptr;
+  float* q32 = nullptr;
+  float* X32 = nullptr;
+  float* q32b = nullptr;
+  float* X32b = nullptr;
+  float* p0f = nullptr;
+  float* p1f = nullptr;
+  float* s0f = nullptr;
+  float* s1f = nullptr;
+  float* dinv32 = nullptr;
+  float* lam32 = nullptr;
   double* inj = nullptr;  // coarse only
+  unsigned long long* trace = nullptr;  // phase timestamps of the level's last solve
   uint8_t* state = nullptr;
   int st_sx = 0, st_sy = 0, st_sz = 0;
   double Mc[8], Kc[8], Md = 0, Kd = 0, vol8 = 0, Mhat[64], Khat[64];
@@ -54,9 +75,10 @@ struct tl_problem {
   long long patch_moves = 0;
   long long launches = 0;
   cudaStream_t stream = nullptr;
-  unsigned int* bar = nullptr;  // [count, gen]
+  unsigned int* bar = nullptr;  // grid barrier words (BAR_WORDS), status included
   int* status = nullptr;
   double* red = nullptr;
+  float* red32 = nullptr;
   int red_stride = 0;
   DevStats* stats = nullptr;
   std::vector<void*> allocs;
@@ -127,16 +149,38 @@ void element_constants(Level& L) {
     }
 }
 
-void choose_tiling(Level& L, int target) {
-  Tiling& t = L.t;
-  t.ex = std::min(TXE, L.g.nx);
-  t.ey = std::min(TYE, L.g.ny);
-  t.ntx = (L.g.nx + t.ex - 1) / t.ex;
-  t.nty = (L.g.ny + t.ey - 1) / t.ey;
-  long long nxy = (long long)t.ntx * t.nty;
-  long long ez = (L.g.nz * nxy + target - 1) / target;
-  t.ez = (int)std::max<long long>(1, std::min<long long>(ez, L.g.nz));
-  t.ntz = (L.g.nz + t.ez - 1) / t.ez;
+// Tile shape for the apply.  The FP64 apply is bound by the SM's FP64 pipe, so
+// the time of a step is set by the SM that holds the most element work: the
+// model charges an SM (blocks it hosts) x (tiles per block) tiles of
+// ex*ey*ez elements at the per-element FP64 instruction count of the tile
+// shape (window columns and partial node layers cost extra), plus a fixed
+// cost per layer and tile for the block barriers, divided by the pipe
+// utilisation that one or two resident 8-warp blocks reach.
+void choose_tiling(Level& L, int nsm, int per_sm) {
+  const Grid3& g = L.g;
+  double best = 1e300;
+  Tiling bt{};
+  const int exs[] = {32, 16, 8};
+  const int eys[] = {8, 4, 2, 1};
+  for (int ex0 : exs)
+    for (int ey0 : eys)
+      for (int ez = 1; ez <= g.nz; ++ez) {
+        const int ex = std::min(ex0, g.nx), ey = std::min(ey0, g.ny);
+        const long long T = (long long)((g.nx + ex - 1) / ex) * ((g.ny + ey - 1) / ey) * ((g.nz + ez - 1) / ez);
+        const double rxy = (double)(ex + 1) * (ey + 1) / ((double)ex * ey);
+        const double rz = (double)(ez + 1) / ez;
+        const double ops = 2 * rxy + 2 * rxy * rz + 4.0 * (ex + 1) / ex + 20 + 8.0 * (ex + 1) / ex + 5 * rxy + rxy * rz;
+        const double per_tile = (double)ex * ey * ez * ops + 1500.0 * (ez + 1);
+        const long long G = std::min<long long>(T, (long long)nsm * per_sm);
+        const long long b = (G + nsm - 1) / nsm, tb = (T + G - 1) / G;
+        const double eff = b >= 2 ? 0.8 : 0.5;
+        const double cost = (double)(b * tb) * per_tile / eff;
+        if (cost < best * (1 - 1e-9)) {
+          best = cost;
+          bt = Tiling{ex, ey, ez, (g.nx + ex - 1) / ex, (g.ny + ey - 1) / ey, (g.nz + ez - 1) / ez};
+        }
+      }
+  L.t = bt;
 }
 
 tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
@@ -148,14 +192,39 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
   if ((s = alloc_n(p, &L.u, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.r, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.F, (size_t)L.g.nnx * L.g.nny)) != TL_OK) return s;
-  if ((s = alloc_n(p, &L.p0, nn)) != TL_OK) return s;
-  if ((s = alloc_n(p, &L.p1, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.G, (size_t)MAXRECT * (L.g.nnx + L.g.nny))) != TL_OK) return s;
   if ((s = alloc_n(p, &L.q, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.X, nn * NXB)) != TL_OK) return s;
+  if (p->cfg.precision == TL_FP64) {
+    if ((s = alloc_n(p, &L.r2, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.p0, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.p1, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.s0, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.s1, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.q2, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.X2, nn * NXB)) != TL_OK) return s;
+  }
   if ((s = alloc_n(p, &L.dinv, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.s_e, ne)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.k_e, ne)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.lam, 8 * ne)) != TL_OK) return s;
+  if (p->cfg.precision == TL_FP32_REFINED) {
+    if ((s = alloc_n(p, &L.d32, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.r32, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.r32b, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.q32, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.X32, nn * NXB)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.q32b, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.X32b, nn * NXB)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.p0f, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.p1f, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.s0f, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.s1f, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.dinv32, nn)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.lam32, 8 * ne)) != TL_OK) return s;
+  }
   if (coarse && (s = alloc_n(p, &L.inj, nn)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.trace, 2 * TRACE_CAP)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.state, (size_t)L.st_sx * L.st_sy * L.st_sz)) != TL_OK) return s;
   return TL_OK;
 }
@@ -251,19 +320,42 @@ LoadSpec box_load(const tl_problem* p, int n) {
   return ld;
 }
 
-void fill_common(const tl_problem* p, const Level& L, SolveArgs<double>& a) {
+void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.g = L.g;
   a.t = L.t;
   a.u = L.u;
   a.r = L.r;
+  a.r2 = L.r2;
   a.p0 = L.p0;
   a.p1 = L.p1;
+  a.s0 = L.s0;
+  a.s1 = L.s1;
   a.q = L.q;
   a.X = L.X;
+  a.q2 = L.q2;
+  a.X2 = L.X2;
   a.dinv = L.dinv;
   a.s_e = L.s_e;
   a.k_e = L.k_e;
+  a.lam = L.lam;
+  a.d32 = L.d32;
+  a.r32 = L.r32;
+  a.r32b = L.r32b;
+  a.q32 = L.q32;
+  a.X32 = L.X32;
+  a.q32b = L.q32b;
+  a.X32b = L.X32b;
+  a.p0f = L.p0f;
+  a.p1f = L.p1f;
+  a.s0f = L.s0f;
+  a.s1f = L.s1f;
+  a.dinv32 = L.dinv32;
+  a.lam32 = L.lam32;
+  a.precision = p->cfg.precision == TL_FP32_REFINED ? PREC_FP32_REFINED : PREC_FP64;
+  a.tol_inner = p->cfg.tol_inner;
+  a.max_outer = 20;
   a.F = L.F;
+  a.G = L.G;
   a.state = L.state;
   const tl_config& c = p->cfg;
   a.mat = Material{c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref, c.powder_factor, c.T_melt};
@@ -276,15 +368,17 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs<double>& a) {
   a.vol8 = L.vol8;
   std::memcpy(a.Mhat, L.Mhat, sizeof a.Mhat);
   std::memcpy(a.Khat, L.Khat, sizeof a.Khat);
-  a.bar = Barrier{p->bar, p->bar + 1, p->status};
+  a.bar = Barrier{p->bar, p->bar + BAR_GEN, p->status};
   a.red = p->red;
+  a.red32 = p->red32;
   a.red_stride = p->red_stride;
   a.stats = p->stats;
+  a.trace = L.trace;
 }
 
-tl_status launch_solve(tl_problem* p, const Level& L, SolveArgs<double>& a) {
+tl_status launch_solve(tl_problem* p, const Level& L, SolveArgs& a) {
   void* args[] = {(void*)&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel<double>, dim3(L.grid), dim3(NT), args, 0,
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(L.grid), dim3(NT), args, 0,
                                               p->stream);
   p->launches++;
   return cuda_status(e);
@@ -314,7 +408,7 @@ void injection_box(const tl_problem* p, int box[6]) {
 tl_status coarse_solve(tl_problem* p, bool correct) {
   const tl_config& c = p->cfg;
   Level& L = p->C;
-  SolveArgs<double> a{};
+  SolveArgs a{};
   fill_common(p, L, a);
   a.T_in = L.T;
   a.T_out = correct ? L.T : L.T2;
@@ -345,7 +439,7 @@ tl_status coarse_solve(tl_problem* p, bool correct) {
 tl_status fine_solve(tl_problem* p, int i) {
   const tl_config& c = p->cfg;
   Level& L = p->Fi;
-  SolveArgs<double> a{};
+  SolveArgs a{};
   fill_common(p, L, a);
   a.T_in = L.T;
   a.T_out = L.T;
@@ -388,7 +482,7 @@ tl_status validate(const tl_config* c) {
   if (c->ntracks < 0 || (c->ntracks > 0 && !c->path)) return TL_EINVAL;
   if (!(c->tol > 0) || c->max_iter < 1) return TL_EINVAL;
   if (c->precision != TL_FP64 && c->precision != TL_FP32_REFINED) return TL_EINVAL;
-  if (c->precision == TL_FP32_REFINED) return TL_EINVAL;  // not available in this build yet
+  if (c->precision == TL_FP32_REFINED && !(c->tol_inner > 0 && c->tol_inner < 1)) return TL_EINVAL;
   if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
   for (int j = 0; j < c->ntracks; ++j) {
     const tl_track& k = c->path[j];
@@ -398,7 +492,9 @@ tl_status validate(const tl_config* c) {
   }
   if (c->coarse_source != 0 && c->coarse_source != 1) return TL_EINVAL;
   const long long fx = (long long)c->pNXc * c->r, fy = (long long)c->pNYc * c->r, fz = (long long)c->pNZc * c->r;
-  if ((fx + 1) * (fy + 1) * (fz + 1) > (1LL << 31)) return TL_EINVAL;
+  // 32-bit node indices with 8 eigenvalues per element and 7 exchange arrays
+  if ((fx + 1) * (fy + 1) * (fz + 1) > (1LL << 28)) return TL_EINVAL;
+  if ((long long)(c->NXc + 1) * (c->NYc + 1) * (c->NZc + 1) > (1LL << 28)) return TL_EINVAL;
   return TL_OK;
 }
 
@@ -477,7 +573,7 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel<double>, NT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, 0);
   if (e != cudaSuccess || per_sm < 1) {
     delete p;
     cudaGetLastError();
@@ -497,19 +593,21 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   F.st_sx = c.NXc * r; F.st_sy = c.NYc * r; F.st_sz = c.pNZc * r;
   element_constants(C);
   element_constants(F);
-  choose_tiling(C, p->nsm);
-  choose_tiling(F, p->nsm);
+  choose_tiling(C, p->nsm, per_sm);
+  choose_tiling(F, p->nsm, per_sm);
   C.grid = std::min(p->max_coop, C.t.ntx * C.t.nty * C.t.ntz);
   F.grid = std::min(p->max_coop, F.t.ntx * F.t.nty * F.t.ntz);
   p->red_stride = std::max(C.grid, F.grid);
   if ((s = alloc_level(p, C, true)) != TL_OK || (s = alloc_level(p, F, false)) != TL_OK ||
-      (s = alloc_n(p, &p->bar, 2)) != TL_OK || (s = alloc_n(p, &p->status, 1)) != TL_OK ||
+      (s = alloc_n(p, &p->bar, BAR_WORDS)) != TL_OK ||
       (s = alloc_n(p, &p->red, (size_t)RS_N * p->red_stride)) != TL_OK ||
+      (s = alloc_n(p, &p->red32, (size_t)RS_N * p->red_stride)) != TL_OK ||
       (s = alloc_n(p, &p->stats, 1)) != TL_OK) {
     release(p);
     delete p;
     return s;
   }
+  p->status = (int*)(p->bar + BAR_STATUS);
   p->ok = c.NZc - c.pNZc;
   p->oi = 0;
   p->oj = 0;
@@ -530,12 +628,11 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   // buffers read before being written in a solve start at zero
   for (Level* L : {&C, &F}) {
     size_t nn = (size_t)L->g.nnx * L->g.nny * L->g.nnz;
-    cudaMemsetAsync(L->p0, 0, nn * sizeof(double), p->stream);
-    cudaMemsetAsync(L->p1, 0, nn * sizeof(double), p->stream);
     cudaMemsetAsync(L->X, 0, nn * NXB * sizeof(double), p->stream);
   }
-  cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned int), p->stream);
-  cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+  cudaMemsetAsync(p->bar, 0, BAR_WORDS * sizeof(unsigned int), p->stream);
+  cudaMemsetAsync(C.trace, 0, 2 * TRACE_CAP * sizeof(unsigned long long), p->stream);
+  cudaMemsetAsync(F.trace, 0, 2 * TRACE_CAP * sizeof(unsigned long long), p->stream);
   cudaMemsetAsync(p->stats, 0, sizeof(DevStats), p->stream);
   init_state_kernel<<<256, nb, 0, p->stream>>>(C.state, C.st_sx, C.st_sy, C.st_sz, 0.0, C.g.hz, c.Lz,
                                                c.powder_depth);
@@ -684,6 +781,8 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out) {
   out->substeps = (int64_t)p->n * p->cfg.m + (p->phase == IN_SUBSTEPS || p->phase == NEED_CORRECT ? p->sub : 0);
   out->cg_iters_coarse = d.iters[0];
   out->cg_iters_fine = d.iters[1];
+  out->outer_iters_coarse = d.outer[0];
+  out->outer_iters_fine = d.outer[1];
   out->solves_coarse = d.solves[0];
   out->solves_fine = d.solves[1];
   out->max_iters_coarse = d.max_iters[0];
@@ -700,6 +799,24 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out) {
   out->energy_fine_laser = d.e_laser[1];
   out->energy_fine_flux = d.e_flux[1];
   out->time = p->n * p->cfg.dt_coarse;
+  return TL_OK;
+}
+
+tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap, size_t* n_out) {
+  if (!p || !host_out || !n_out || (level != TL_COARSE && level != TL_FINE)) return TL_EINVAL;
+  const Level& L = level == TL_COARSE ? p->C : p->Fi;
+  std::vector<unsigned long long> buf(2 * TRACE_CAP);
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(buf.data(), L.trace, buf.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  const size_t n = std::min<size_t>((size_t)buf[0], TRACE_CAP - 1);
+  const size_t m = std::min(n, cap);
+  for (size_t i = 0; i < m; ++i) {
+    host_out[2 * i] = buf[2 * (i + 1)];
+    host_out[2 * i + 1] = buf[2 * (i + 1) + 1];
+  }
+  *n_out = n;
   return TL_OK;
 }
 

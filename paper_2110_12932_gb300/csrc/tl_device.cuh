@@ -50,14 +50,25 @@ __host__ __device__ inline int split_lo(int n, int parts, int a) {
 
 // ---------------------------------------------------------------------------
 // Time-limited grid barrier for cooperative (co-resident) launches.
-// Every wait gives up after `limit_ns` of global time, records ST_TIMEOUT and
-// returns false; a block that sees an error recorded by another returns
-// false too, so that all blocks leave the kernel.
+// Two-level arrival: blocks arrive on the counter of their group of
+// BAR_GROUP consecutive blocks; the last of a group arrives on the root
+// counter; the last group releases the generation word.  Every wait gives up
+// after `limit_ns` of global time, records ST_TIMEOUT and returns false; a
+// block that sees an error recorded by another returns false too, so that all
+// blocks leave the kernel.
+// Word layout (BAR_WORDS unsigned ints, zero at creation): [0] root counter,
+// [1 .. BAR_MAXG] group counters, [BAR_GEN] generation, [BAR_STATUS] status.
 // ---------------------------------------------------------------------------
+constexpr int BAR_GROUP = 32;
+constexpr int BAR_MAXG = 64;
+constexpr int BAR_GEN = BAR_MAXG + 1;
+constexpr int BAR_STATUS = BAR_MAXG + 2;
+constexpr int BAR_WORDS = BAR_MAXG + 3;
+
 struct Barrier {
-  unsigned int* count;
+  unsigned int* count;  // root counter followed by the group counters
   unsigned int* gen;
-  int* status;  // sticky device status word
+  int* status;          // sticky device status word
 };
 
 __device__ inline unsigned long long global_ns() {
@@ -83,15 +94,24 @@ __device__ inline bool grid_sync(const Barrier& b, unsigned long long limit_ns =
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned int g = ld_acquire_u32(b.gen);
+    const unsigned int g = ld_acquire_u32(b.gen);
     __threadfence();
-    unsigned int arrived = atomicAdd(b.count, 1u);
-    if (arrived == gridDim.x - 1) {
-      __threadfence();  // acquire side: every arrival's earlier writes
-      atomicExch(b.count, 0u);
-      st_release_u32(b.gen, g + 1u);
-    } else {
-      unsigned long long t0 = global_ns();
+    const unsigned int grp = blockIdx.x / BAR_GROUP;
+    const unsigned int ngroups = (gridDim.x + BAR_GROUP - 1) / BAR_GROUP;
+    const unsigned int gsize = min((unsigned int)BAR_GROUP, gridDim.x - grp * BAR_GROUP);
+    bool released = false;
+    if (atomicAdd(b.count + 1 + grp, 1u) == gsize - 1) {
+      __threadfence();  // acquire side: the group's arrivals
+      atomicExch(b.count + 1 + grp, 0u);
+      if (atomicAdd(b.count, 1u) == ngroups - 1) {
+        __threadfence();  // acquire side: every group's arrival
+        atomicExch(b.count, 0u);
+        st_release_u32(b.gen, g + 1u);
+        released = true;
+      }
+    }
+    if (!released) {
+      const unsigned long long t0 = global_ns();
       while (ld_acquire_u32(b.gen) == g) {
         if (ld_volatile_i32(b.status) == ST_TIMEOUT) { ok = 0; break; }
         if (global_ns() - t0 > limit_ns) {
@@ -99,7 +119,7 @@ __device__ inline bool grid_sync(const Barrier& b, unsigned long long limit_ns =
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     if (ld_volatile_i32(b.status) == ST_TIMEOUT) ok = 0;
@@ -110,18 +130,21 @@ __device__ inline bool grid_sync(const Barrier& b, unsigned long long limit_ns =
 }
 
 // ---------------------------------------------------------------------------
-// Deterministic reductions: per-thread partial -> block sum (fixed shuffle
-// tree) -> one slot per block; after a grid barrier every block sums the
-// slots in the same fixed order, so all blocks hold bitwise equal totals.
+// Deterministic reductions in the solve's own precision: per-thread partial ->
+// warp sum (fixed shuffle tree) -> per-warp partials in shared memory -> one
+// warp sums them -> one slot per block; after a grid barrier warp 0 of every
+// block sums the slots in the same fixed order, so all blocks hold bitwise
+// equal totals.  On GB300 an FP64 warp instruction occupies the SM
+// sub-partition's FP64 unit for ~64 cycles, so FP32 solves reduce in FP32.
 // ---------------------------------------------------------------------------
-template <int NV>
-__device__ inline void block_reduce_store(double (&v)[NV], double* slots, int stride) {
-  __shared__ double s_part[NV][32];
+template <int NV, typename T>
+__device__ inline void block_reduce_store(T (&v)[NV], T* slots, int stride) {
+  __shared__ T s_part[NV][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
-    double x = v[a];
+    T x = v[a];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if (lane == 0) s_part[a][warp] = x;
@@ -130,7 +153,7 @@ __device__ inline void block_reduce_store(double (&v)[NV], double* slots, int st
   if (warp == 0) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-      double x = lane < nwarps ? s_part[a][lane] : 0.0;
+      T x = lane < nwarps ? s_part[a][lane] : T(0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
       if (lane == 0) slots[(size_t)a * stride + blockIdx.x] = x;
@@ -139,14 +162,14 @@ __device__ inline void block_reduce_store(double (&v)[NV], double* slots, int st
   __syncthreads();
 }
 
-template <int NV>
-__device__ inline void grid_total(const double* slots, int stride, double (&out)[NV]) {
-  __shared__ double s_tot[NV];
+template <int NV, typename T>
+__device__ inline void grid_total(const T* slots, int stride, T (&out)[NV]) {
+  __shared__ T s_tot[NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp == 0) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-      double x = 0.0;
+      T x = T(0);
       for (int s = lane; s < (int)gridDim.x; s += 32) x += __ldcg(slots + (size_t)a * stride + s);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);

@@ -7,7 +7,7 @@
 // real-time loop that forbids allocation after set-up, a plugin handed only
 // input and output buffers.  They pass inputs and outputs; everything else
 // the solve needs lives in `g_box_scratch` below, which every GPU that loads
-// this library holds (about 8.4 MB) until the process exits.
+// this library holds (about 19.2 MB) until the process exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,14 +30,17 @@ constexpr int kMaxDevices = 64;
 
 constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
-// Worst case over all meshes with at most kMaxNodes nodes: 13 nodal FP64 arrays
-// (u, r, p0, p1, q, dinv and 7 exchange arrays), 2 element arrays (at most as
-// many elements as nodes), the top-face load (at most half the nodes), the
-// reduction slots, barrier / status words and the counters.
+// Worst case over all meshes with at most kMaxNodes nodes: 24 nodal FP64 arrays
+// (u, r x2, p x2, s x2, q x2, dinv and 2 x 7 exchange arrays), 10 per-element
+// values (s_e, k_e and 8 eigenvalues; at most as many elements as nodes), the
+// top-face load (at most half the nodes) and its 1D factor tables (nnx + nny
+// <= kMaxNodes / 4 + 2 per factor), the reduction slots, barrier / status
+// words and the counters.
 constexpr size_t kScratchBytes =
-    13 * align_up(kMaxNodes * sizeof(double)) + 2 * align_up(kMaxNodes * sizeof(double)) +
-    align_up(kMaxNodes / 2 * sizeof(double)) + align_up((size_t)RS_N * kMaxGrid * sizeof(double)) +
-    align_up(4 * sizeof(unsigned int)) + align_up(sizeof(DevStats)) + 4 * kAlign;
+    24 * align_up(kMaxNodes * sizeof(double)) + 2 * align_up(kMaxNodes * sizeof(double)) +
+    align_up(8 * kMaxNodes * sizeof(double)) +
+    align_up(kMaxNodes / 2 * sizeof(double)) + align_up((size_t)MAXRECT * (kMaxNodes / 4 + 2) * sizeof(double)) + align_up((size_t)RS_N * kMaxGrid * sizeof(double)) + align_up((size_t)RS_N * kMaxGrid * sizeof(float)) +
+    align_up(BAR_WORDS * sizeof(unsigned int)) + align_up(sizeof(DevStats)) + 4 * kAlign;
 
 }  // namespace
 
@@ -86,7 +89,7 @@ struct Carver {
   }
 };
 
-void box_constants(const Grid3& g, SolveArgs<double>& a) {
+void box_constants(const Grid3& g, SolveArgs& a) {
   const double h[3] = {g.hx, g.hy, g.hz};
   double mu[3][2], ka[3][2];
   for (int d = 0; d < 3; ++d) {
@@ -156,13 +159,13 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel<double>, NT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, 0);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return TL_ECUDA;
   }
 
-  SolveArgs<double> a{};
+  SolveArgs a{};
   a.g = Grid3{d->nx, d->ny, d->nz, (int)nnx, (int)nny, (int)nnz, d->Lx / d->nx, d->Ly / d->ny, d->Lz / d->nz};
   a.t = box_tiling(a.g, nsm);
   const int ntiles = a.t.ntx * a.t.nty * a.t.ntz;
@@ -172,20 +175,28 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
   Carver c{base};
   a.u = c.take<double>(nn);
   a.r = c.take<double>(nn);
+  a.r2 = c.take<double>(nn);
   a.p0 = c.take<double>(nn);
   a.p1 = c.take<double>(nn);
+  a.s0 = c.take<double>(nn);
+  a.s1 = c.take<double>(nn);
   a.q = c.take<double>(nn);
+  a.q2 = c.take<double>(nn);
   a.dinv = c.take<double>(nn);
   a.X = c.take<double>(nn * NXB);
+  a.X2 = c.take<double>(nn * NXB);
   a.s_e = c.take<double>(ne);
   a.k_e = c.take<double>(ne);
+  a.lam = c.take<double>(8 * ne);
   a.F = c.take<double>((size_t)(nnx * nny));
+  a.G = c.take<double>((size_t)MAXRECT * (nnx + nny));
   a.red = c.take<double>((size_t)RS_N * kMaxGrid);
-  unsigned int* words = c.take<unsigned int>(4);  // barrier count, generation, status
+  a.red32 = c.take<float>((size_t)RS_N * kMaxGrid);
+  unsigned int* words = c.take<unsigned int>(BAR_WORDS);  // barrier counters, generation, status
   a.stats = c.take<DevStats>(1);
   if (c.used > kScratchBytes) return TL_EINVAL;
   a.red_stride = kMaxGrid;
-  a.bar = Barrier{words, words + 1, (int*)(words + 2)};
+  a.bar = Barrier{words, words + BAR_GEN, (int*)(words + BAR_STATUS)};
 
   a.T_in = T_in;
   a.T_out = T_out;
@@ -219,17 +230,17 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
   // status word and the counters must start at zero.  Nothing else is read
   // before the solve writes it.
   cudaStream_t st = (cudaStream_t)stream;
-  e = cudaMemsetAsync(words, 0, 4 * sizeof(unsigned int), st);
+  e = cudaMemsetAsync(words, 0, BAR_WORDS * sizeof(unsigned int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.stats, 0, sizeof(DevStats), st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TL_ECUDA;
   }
   void* args[] = {(void*)&a};
-  e = cudaLaunchCooperativeKernel((const void*)solve_kernel<double>, dim3(grid), dim3(NT), args, 0, st);
+  e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(grid), dim3(NT), args, 0, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   int status = 0;
-  if (e == cudaSuccess) e = cudaMemcpy(&status, words + 2, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&status, words + BAR_STATUS, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TL_ECUDA;

@@ -29,8 +29,8 @@ namespace tl {
 constexpr int TXE = 32;               // max tile width in elements (x)
 constexpr int TYE = 8;                // max tile depth in elements (y)
 constexpr int WX = TXE + 1, WY = TYE + 1;
-constexpr int NT = 256;               // threads per block
-constexpr int WPT = (WX * WY + NT - 1) / NT;  // window columns per thread
+constexpr int NT = 320;               // threads per block: one window column each
+static_assert(NT >= WX * WY, "a block must cover a tile's window columns");
 constexpr int MAXRECT = 8;
 constexpr int NXB = 7;                // exchange buffers
 
@@ -47,6 +47,42 @@ __device__ inline bool is_dir(const Grid3& g, const DirSpec& d, int i, int j, in
   if ((d.faces & 16) && k == 0) return true;
   return i >= d.box[0] && i <= d.box[1] && j >= d.box[2] && j <= d.box[3] &&
          k >= d.box[4] && k <= d.box[5];
+}
+
+// Index of the first Dirichlet set holding node (i, j, k), in the order z = 0
+// face, x = 0, x = nx, y = 0, y = ny, box; -1 if the node is free.
+__device__ inline int dir_set(const Grid3& g, const DirSpec& d, int i, int j, int k) {
+  if ((d.faces & 16) && k == 0) return 0;
+  if ((d.faces & 1) && i == 0) return 1;
+  if ((d.faces & 2) && i == g.nx) return 2;
+  if ((d.faces & 4) && j == 0) return 3;
+  if ((d.faces & 8) && j == g.ny) return 4;
+  if (i >= d.box[0] && i <= d.box[1] && j >= d.box[2] && j <= d.box[3] && k >= d.box[4] && k <= d.box[5])
+    return 5;
+  return -1;
+}
+
+// Calls body(n, i, j, k) once for every Dirichlet node, the candidates of all
+// sets spread evenly over the grid's threads (a node is visited by the first
+// set that holds it).
+template <class Body>
+__device__ inline void for_dirichlet(const Grid3& g, const DirSpec& d, Body body) {
+  const int bx = d.box[1] - d.box[0] + 1, by = d.box[3] - d.box[2] + 1, bz = d.box[5] - d.box[4] + 1;
+  const int sz[6] = {(d.faces & 16) ? g.nnx * g.nny : 0, (d.faces & 1) ? g.nny * g.nnz : 0,
+                     (d.faces & 2) ? g.nny * g.nnz : 0, (d.faces & 4) ? g.nnx * g.nnz : 0,
+                     (d.faces & 8) ? g.nnx * g.nnz : 0, (bx > 0 && by > 0 && bz > 0) ? bx * by * bz : 0};
+  const int total = sz[0] + sz[1] + sz[2] + sz[3] + sz[4] + sz[5];
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < total; m += gridDim.x * blockDim.x) {
+    int set = 0, r = m;
+    while (r >= sz[set]) r -= sz[set++];
+    int i, j, k;
+    if (set == 0) { i = r % g.nnx; j = r / g.nnx; k = 0; }
+    else if (set <= 2) { j = r % g.nny; k = r / g.nny; i = set == 1 ? 0 : g.nx; }
+    else if (set <= 4) { i = r % g.nnx; k = r / g.nnx; j = set == 3 ? 0 : g.ny; }
+    else { i = d.box[0] + r % bx; j = d.box[2] + (r / bx) % by; k = d.box[4] + r / (bx * by); }
+    if (dir_set(g, d, i, j, k) != set) continue;
+    body(i + g.nnx * (j + g.nny * k), i, j, k);
+  }
 }
 
 // Dirichlet values.  kind 0 (fine patch): nodes on the plate bottom take
@@ -141,6 +177,31 @@ __device__ inline double hat_box(int i, int n, double h, double o, double x0, do
   return H;
 }
 
+// The top load is separable: F(i, j) = sum_f c_f Gx_f(i) Gy_f(j) over one
+// Gaussian factor or one factor per rectangle.  Phase 0 tabulates the 1D
+// factors (nf (nnx + nny) values) so that each transcendental is evaluated
+// once per node line instead of once per top node.
+__device__ inline int load_factors(const LoadSpec& L) { return L.kind == 1 ? 1 : (L.kind == 2 ? L.nrect : 0); }
+
+__device__ inline double load_factor(const LoadSpec& L, const Grid3& g, int f, int idx) {
+  const bool isx = idx < g.nnx;
+  const int i = isx ? idx : idx - g.nnx;
+  if (L.kind == 1)
+    return isx ? hat_gauss(i, g.nx, g.hx, L.ox, L.xc, L.alpha) : hat_gauss(i, g.ny, g.hy, L.oy, L.yc, L.alpha);
+  return isx ? hat_box(i, g.nx, g.hx, L.ox, L.rect[f][0], L.rect[f][1])
+             : hat_box(i, g.ny, g.hy, L.oy, L.rect[f][2], L.rect[f][3]);
+}
+
+__device__ inline double top_load_tab(const LoadSpec& L, const Grid3& g, const double* G, int i, int j) {
+  const int nf = load_factors(L), w = g.nnx + g.nny;
+  double F = 0.0;
+  for (int f = 0; f < nf; ++f) {
+    const double c = L.kind == 1 ? L.amp : L.rect[f][4];
+    F += c * __ldcg(G + f * w + i) * __ldcg(G + f * w + g.nnx + j);
+  }
+  return F;
+}
+
 __device__ inline double top_load(const LoadSpec& L, const Grid3& g, int i, int j) {
   if (L.kind == 1) {
     return L.amp * hat_gauss(i, g.nx, g.hx, L.ox, L.xc, L.alpha) *
@@ -161,7 +222,7 @@ __device__ inline double top_load(const LoadSpec& L, const Grid3& g, int i, int 
 // Counters written by block 0 at the end of each solve (index: 0 coarse, 1 fine).
 struct DevStats {
   double e_stored[2], e_laser[2], e_flux[2];
-  long long iters[2], solves[2];
+  long long iters[2], solves[2], outer[2];
   int max_iters[2], last_iters[2];
 };
 
@@ -170,37 +231,83 @@ struct Tiling {
   int ntx, nty, ntz;  // tile counts
 };
 
-template <typename R>
+enum Precision : int { PREC_FP64 = 0, PREC_FP32_REFINED = 1 };
+
+// Everything one launch needs.  FP64 arrays serve the plain path, the
+// right-hand side and the outer residual of the refined path; the FP32 arrays
+// (NULL in the plain path) hold the refined path's inner CG.
 struct SolveArgs {
   Grid3 g;
   Tiling t;
   const double* T_in;
   double* T_out;
-  double* u;   // increment
-  double* r;   // residual
-  R* p0;
-  R* p1;
-  R* q;
-  R* X;        // NXB exchange buffers of nnode each
-  R* dinv;
-  R* s_e;
-  R* k_e;
-  double* F;   // top-face load, (nx+1)(ny+1)
+  double* u;     // increment T^{k+1} - T^k (Dirichlet entries prescribed)
+  double* r;     // FP64 residual
+  double* r2;    // its second buffer (CG pass parity)
+  double* q;     // own partial of an FP64 apply
+  double* X;     // NXB exchange arrays of nnode each (FP64)
+  double* q2;    // second partial buffers (CG pass parity)
+  double* X2;
+  double* p0;
+  double* p1;
+  double* s0;
+  double* s1;
+  double* dinv;
+  double* s_e;
+  double* k_e;
+  double* lam;   // eight Hadamard eigenvalues per element, [8][nelem]
+  float* d32;    // refined path: inner correction
+  float* r32;
+  float* r32b;
+  float* q32;
+  float* X32;
+  float* q32b;
+  float* X32b;
+  float* p0f;
+  float* p1f;
+  float* s0f;
+  float* s1f;
+  float* dinv32;
+  float* lam32;
+  double* F;     // top-face load, (nx+1)(ny+1)
+  double* G;     // load factor tables, MAXRECT (nnx + nny)
   uint8_t* state;
   int st_sx, st_sy, st_ox, st_oy;  // element (ie,je,ke) -> state[(ke st_sy + je + st_oy) st_sx + ie + st_ox]
   DirSpec dir;
   DirValues dv;
   LoadSpec ld;
   Material mat;
-  double dt, tol;
-  int max_iter;
+  double dt, tol, tol_inner;
+  int max_iter, max_outer, precision;
   int energy, update_state, level;
   double Mc[8], Kc[8], Md, Kd, vol8;
   double Mhat[64], Khat[64];
   Barrier bar;
-  double* red;     // reduction slots [16][red_stride]
+  double* red;   // reduction slots [RS_N][red_stride]
+  float* red32;  // FP32 reduction slots of the refined path's inner CG
   int red_stride;
   DevStats* stats;
+  unsigned long long* trace;  // [TRACE_CAP][2] (marker, globaltimer ns) of this solve, or NULL
+};
+
+// Phase markers recorded by block 0 when tracing.
+enum TraceMark : int {
+  TR_START = 0, TR_PHASE0 = 1, TR_RHS = 2, TR_RESID = 3, TR_CG_PASS = 4, TR_OUTER_INIT = 5,
+  TR_OUTER_APPLY = 6, TR_OUTER_END = 7, TR_UPDATE = 8, TR_END = 9, TR_CG_APPLY = 10
+};
+constexpr int TRACE_CAP = 1024;
+
+struct Tracer {
+  unsigned long long* buf;
+  int n = 0;
+  __device__ void mark(int m) {
+    if (buf && blockIdx.x == 0 && threadIdx.x == 0 && n < TRACE_CAP - 1) {
+      buf[2 * (n + 1)] = (unsigned long long)m;
+      buf[2 * (n + 1) + 1] = global_ns();
+      ++n;
+      buf[0] = (unsigned long long)n;
+    }
+  }
 };
 
 template <typename R>
@@ -215,203 +322,387 @@ struct ApplySmem {
   R XR[4][TYE][TXE];                       // ... and to its right node column
 };
 
-// Apply one tile: for every window node n of tile `tile`, call
-// emit(slot, li, lj, n, i, j, k, y, xin) with y the tile's partial of (A x)_n
-// and xin = x_n as loaded; `load(n)` returns x_n (called once per window node).
-// lam(e, lam8) fills the eight Hadamard eigenvalues of element e.
+// Apply one tile of at most TXE x TYE x ez elements with NT >= (TXE+1)(TYE+1)
+// threads: every thread owns at most one window node column (stages 1 and 5),
+// one (element row, node column) pair (stages 2 and 4, same index) and one
+// element column (stage 3), all fixed for the tile, so the index arithmetic is
+// done once per tile.  For every window node n the tile emits
+// emit(n, slot, y, xin): y its partial of (A x)_n, xin = x_n as loaded,
+// slot = 0 if the tile owns n, else (high-x) + 2 (high-y) + 4 (high-z).
+// load(n, i, j, k, owned) returns x_n and is called exactly once per window
+// node; lam(e, l8) fills the eight Hadamard eigenvalues of element e.
 template <typename R, class Load, class Lam, class Emit>
 __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, ApplySmem<R>& sm,
                                   Load load, Lam lam, Emit emit) {
   const int tid = threadIdx.x;
-  const int tix = tile % t.ntx, tiy = (tile / t.ntx) % t.nty, tiz = tile / (t.ntx * t.nty);
+  const int txy = t.ntx * t.nty;
+  const int tiz = tile / txy, trem = tile - tiz * txy;
+  const int tiy = trem / t.ntx, tix = trem - tiy * t.ntx;
   const int ie0 = tix * t.ex, je0 = tiy * t.ey, ke0 = tiz * t.ez;
   const int ex = min(t.ex, g.nx - ie0), ey = min(t.ey, g.ny - je0), ke1 = min(ke0 + t.ez, g.nz);
-  const int wx = ex + 1, wy = ey + 1, nwin = wx * wy;
+  const int wx = ex + 1, nwin = wx * (ey + 1);
+  const int S = g.nnx * g.nny;   // node layer stride
+  const int Se = g.nx * g.ny;    // element layer stride
+  const bool has_w = tid < nwin;        // window node column
+  const bool has_r = tid < ey * wx;     // (element row, node column) pair
+  const bool has_e = tid < ey * ex;     // element column
+  const int wlj = tid / wx, wli = tid - wlj * wx;
+  const int ely = tid / ex, elx = tid - ely * ex;
+  const int wnode = (ie0 + wli) + g.nnx * (je0 + wlj);
+  const int welem = (ie0 + elx) + g.nx * (je0 + ely);
+  const int wslot = ((wli == ex && ie0 + ex < g.nx) ? 1 : 0) | ((wlj == ey && je0 + ey < g.ny) ? 2 : 0);
+  const int wi = ie0 + wli, wj = je0 + wlj;
+  const bool z_top_owned = ke1 == g.nz;  // the tile owns its top node layer only at the plate top
   int cur = 0;
-  for (int idx = tid; idx < nwin; idx += NT) {
-    int li = idx % wx, lj = idx / wx;
-    sm.X[cur][lj][li] = load(node_id(g, ie0 + li, je0 + lj, ke0));
-  }
-  R carry[WPT];
-#pragma unroll
-  for (int w = 0; w < WPT; ++w) carry[w] = R(0);
+  if (has_w) sm.X[cur][wlj][wli] = load(wnode + ke0 * S, wi, wj, ke0, wslot == 0);
+  R carry = R(0);
   __syncthreads();
   for (int ke = ke0; ke < ke1; ++ke) {
     const int nxt = cur ^ 1;
     // stage 1: next layer, z-direction Hadamard per window column
-    for (int idx = tid; idx < nwin; idx += NT) {
-      int li = idx % wx, lj = idx / wx;
-      R hi = load(node_id(g, ie0 + li, je0 + lj, ke + 1));
-      R lo = sm.X[cur][lj][li];
-      sm.X[nxt][lj][li] = hi;
-      sm.a.Z[0][lj][li] = lo + hi;
-      sm.a.Z[1][lj][li] = lo - hi;
+    if (has_w) {
+      R hi = load(wnode + (ke + 1) * S, wi, wj, ke + 1, wslot == 0 && (ke + 1 < ke1 || z_top_owned));
+      R lo = sm.X[cur][wlj][wli];
+      sm.X[nxt][wlj][wli] = hi;
+      sm.a.Z[0][wlj][wli] = lo + hi;
+      sm.a.Z[1][wlj][wli] = lo - hi;
     }
     __syncthreads();
     // stage 2: y-direction per element row and node column
-    for (int idx = tid; idx < ey * wx; idx += NT) {
-      int li = idx % wx, ly = idx / wx;
+    if (has_r) {
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
-        R a = sm.a.Z[z][ly][li], b = sm.a.Z[z][ly + 1][li];
-        sm.Y[2 * z][ly][li] = a + b;
-        sm.Y[2 * z + 1][ly][li] = a - b;
+        R a = sm.a.Z[z][wlj][wli], b = sm.a.Z[z][wlj + 1][wli];
+        sm.Y[2 * z][wlj][wli] = a + b;
+        sm.Y[2 * z + 1][wlj][wli] = a - b;
       }
     }
     __syncthreads();
     // stage 3: per element, x-direction, eigenvalue scaling, x-backward
-    for (int idx = tid; idx < ey * ex; idx += NT) {
-      int lx = idx % ex, ly = idx / ex;
+    if (has_e) {
       R l8[8];
-      lam(elem_id(g, ie0 + lx, je0 + ly, ke), l8);
+      lam(welem + ke * Se, l8);
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) {
-        R a = sm.Y[m4][ly][lx], b = sm.Y[m4][ly][lx + 1];
-        R ys = l8[2 * m4] * (a + b);
+        R a = sm.Y[m4][ely][elx], b = sm.Y[m4][ely][elx + 1];
+        R s = a + b;
         R yd = l8[2 * m4 + 1] * (a - b);
-        sm.XL[m4][ly][lx] = ys + yd;
-        sm.XR[m4][ly][lx] = ys - yd;
+        sm.XL[m4][ely][elx] = fma(l8[2 * m4], s, yd);
+        sm.XR[m4][ely][elx] = fma(l8[2 * m4], s, -yd);
       }
     }
     __syncthreads();
     // stage 4: gather x-backward per node column, y-backward
-    for (int idx = tid; idx < ey * wx; idx += NT) {
-      int li = idx % wx, ly = idx / wx;
+    if (has_r) {
       R B[4];
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) {
-        R v = li < ex ? sm.XL[m4][ly][li] : R(0);
-        if (li > 0) v += sm.XR[m4][ly][li - 1];
+        R v = wli < ex ? sm.XL[m4][wlj][wli] : R(0);
+        if (wli > 0) v += sm.XR[m4][wlj][wli - 1];
         B[m4] = v;
       }
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
-        sm.a.yb.L[z][ly][li] = B[2 * z] + B[2 * z + 1];
-        sm.a.yb.H[z][ly][li] = B[2 * z] - B[2 * z + 1];
+        sm.a.yb.L[z][wlj][wli] = B[2 * z] + B[2 * z + 1];
+        sm.a.yb.H[z][wlj][wli] = B[2 * z] - B[2 * z + 1];
       }
     }
     __syncthreads();
     // stage 5: gather y-backward per node column, z-backward, emit layer ke
-#pragma unroll
-    for (int w = 0; w < WPT; ++w) {
-      int idx = tid + w * NT;
-      if (idx < nwin) {
-        int li = idx % wx, lj = idx / wx;
-        R C0 = lj < ey ? sm.a.yb.L[0][lj][li] : R(0);
-        R C1 = lj < ey ? sm.a.yb.L[1][lj][li] : R(0);
-        if (lj > 0) {
-          C0 += sm.a.yb.H[0][lj - 1][li];
-          C1 += sm.a.yb.H[1][lj - 1][li];
-        }
-        const int i = ie0 + li, j = je0 + lj;
-        emit(li, lj, ex, ey, node_id(g, i, j, ke), i, j, ke, carry[w] + (C0 + C1), sm.X[cur][lj][li]);
-        carry[w] = C0 - C1;
+    if (has_w) {
+      R C0 = wlj < ey ? sm.a.yb.L[0][wlj][wli] : R(0);
+      R C1 = wlj < ey ? sm.a.yb.L[1][wlj][wli] : R(0);
+      if (wlj > 0) {
+        C0 += sm.a.yb.H[0][wlj - 1][wli];
+        C1 += sm.a.yb.H[1][wlj - 1][wli];
       }
+      emit(wnode + ke * S, wslot, carry + (C0 + C1), sm.X[cur][wlj][wli]);
+      carry = C0 - C1;
     }
     __syncthreads();
     cur = nxt;
   }
   // top node layer of the tile: only the contributions of element layer ke1-1
-#pragma unroll
-  for (int w = 0; w < WPT; ++w) {
-    int idx = tid + w * NT;
-    if (idx < nwin) {
-      int li = idx % wx, lj = idx / wx;
-      const int i = ie0 + li, j = je0 + lj;
-      emit(li, lj, ex, ey, node_id(g, i, j, ke1), i, j, ke1, carry[w], sm.X[cur][lj][li]);
-    }
-  }
+  if (has_w) emit(wnode + ke1 * S, wslot | (ke1 < g.nz ? 4 : 0), carry, sm.X[cur][wlj][wli]);
   __syncthreads();
 }
 
-// Which exchange buffer a window node's partial goes to: 0 = owned by this
-// tile (write to the primary array), else 1 + (high-x) + 2 (high-y) + 4 (high-z) - 1.
-__device__ inline int window_slot(const Grid3& g, const Tiling& t, int tile, int i, int j, int k) {
-  const int tix = tile % t.ntx, tiy = (tile / t.ntx) % t.nty, tiz = tile / (t.ntx * t.nty);
-  const int ie1 = min((tix + 1) * t.ex, g.nx), je1 = min((tiy + 1) * t.ey, g.ny),
-            ke1 = min((tiz + 1) * t.ez, g.nz);
-  return (i == ie1 && ie1 < g.nx ? 1 : 0) | (j == je1 && je1 < g.ny ? 2 : 0) | (k == ke1 && ke1 < g.nz ? 4 : 0);
+// Which exchange partials a node's owner adds (the tile boundaries it lies
+// on): bit 0 low-x, bit 1 low-y, bit 2 low-z of the owning tile.  Tile widths
+// in x and y are powers of two whenever there is more than one tile.
+__device__ inline int low_faces(const Grid3& g, const Tiling& t, int i, bool ly, bool lz) {
+  const bool lx = t.ntx > 1 && i > 0 && i < g.nx && (i & (t.ex - 1)) == 0;
+  return (lx ? 1 : 0) | (ly ? 2 : 0) | (lz ? 4 : 0);
 }
 
 // Full nodal value: own partial plus the neighbours' exchange partials, fixed order.
 template <typename R>
-__device__ inline R gather_partials(const Grid3& g, const Tiling& t, const R* prim, const R* X,
-                                    long long nn, long long n, int i, int j, int k) {
+__device__ inline R gather_partials(const R* prim, const R* X, int nn, int n, int lf) {
   R v = __ldcg(prim + n);
-  const bool lx = i > 0 && i < g.nx && (i % t.ex) == 0;
-  const bool ly = j > 0 && j < g.ny && (j % t.ey) == 0;
-  const bool lz = k > 0 && k < g.nz && (k % t.ez) == 0;
-  if (lx) v += __ldcg(X + 0 * nn + n);
-  if (ly) v += __ldcg(X + 1 * nn + n);
-  if (lx && ly) v += __ldcg(X + 2 * nn + n);
-  if (lz) v += __ldcg(X + 3 * nn + n);
-  if (lx && lz) v += __ldcg(X + 4 * nn + n);
-  if (ly && lz) v += __ldcg(X + 5 * nn + n);
-  if (lx && ly && lz) v += __ldcg(X + 6 * nn + n);
+  if (lf) {
+    if (lf & 1) v += __ldcg(X + 0 * nn + n);
+    if (lf & 2) v += __ldcg(X + 1 * nn + n);
+    if ((lf & 3) == 3) v += __ldcg(X + 2 * nn + n);
+    if (lf & 4) v += __ldcg(X + 3 * nn + n);
+    if ((lf & 5) == 5) v += __ldcg(X + 4 * nn + n);
+    if ((lf & 6) == 6) v += __ldcg(X + 5 * nn + n);
+    if (lf == 7) v += __ldcg(X + 6 * nn + n);
+  }
   return v;
 }
 
 template <typename R>
-__device__ inline void store_partial(R* prim, R* X, long long nn, long long n, int slot, R v, bool add) {
-  R* dst = slot == 0 ? prim + n : X + (long long)(slot - 1) * nn + n;
+__device__ inline void store_partial(R* prim, R* X, int nn, int n, int slot, R v, bool add) {
+  R* dst = slot == 0 ? prim + n : X + (slot - 1) * nn + n;
   if (add) v += *dst;
   *dst = v;
 }
 
+// Grid-wide loop over node rows (j, k): each warp takes whole rows, its lanes
+// walk i, so the only division is one per row.  body(n, i, j, k, row_low_faces).
+template <class Body>
+__device__ inline void for_nodes(const Grid3& g, const Tiling& t, Body body) {
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwg = (gridDim.x * blockDim.x) >> 5;
+  const int rows = g.nny * g.nnz;
+  for (int row = wg; row < rows; row += nwg) {
+    const int k = row / g.nny, j = row - k * g.nny;
+    const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
+    const bool lz = k > 0 && k < g.nz && (k % t.ez) == 0;
+    const int base = row * g.nnx;
+    for (int i = lane; i < g.nnx; i += 32) body(base + i, i, j, k, ly, lz);
+  }
+}
+
+// Same for elements rows (je, ke): body(e, ie, je, ke).
+template <class Body>
+__device__ inline void for_elems(const Grid3& g, Body body) {
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwg = (gridDim.x * blockDim.x) >> 5;
+  const int rows = g.ny * g.nz;
+  for (int row = wg; row < rows; row += nwg) {
+    const int ke = row / g.ny, je = row - ke * g.ny;
+    const int base = row * g.nx;
+    for (int ie = lane; ie < g.nx; ie += 32) body(base + ie, ie, je, ke);
+  }
+}
+
 enum RedSlot { RS_RZ0 = 0, RS_BB = 1, RS_PQ = 2, RS_RZ = 3, RS_RR = 4, RS_ES = 5, RS_EL = 6, RS_EF = 7, RS_N = 8 };
 
+// Buffers of one preconditioned CG on the free nodes.  Arrays that a tile
+// reads on its whole window while owners update them are double-buffered by
+// pass parity.
 template <typename R>
-__global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs<R> a) {
-  __shared__ ApplySmem<R> sm;
-  __shared__ double s_Mhat[64], s_Khat[64];
-  if (ld_volatile_i32(a.bar.status) != 0) return;  // an earlier solve failed: leave state untouched
+struct CGBufs {
+  R* x;      // solution, updated in place by the owners
+  R* r[2];   // residual
+  R* p[2];   // search direction
+  R* s[2];   // s = A p, kept by recurrence
+  R* q[2];   // own partial of w = A u
+  R* X[2];   // exchange partials of w
+  const R* dinv;
+  const R* lam;
+};
+
+// Jacobi-preconditioned CG in the single-reduction form of Chronopoulos and
+// Gear: with u = D^-1 r and w = A u,
+//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
+//   gamma = <r, u>, delta = <w, u>, beta = gamma / gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old),
+// so each iteration needs one apply and one grid reduction.  Every tile
+// applies the vector update to its whole window on the fly (owners write it
+// back) and feeds the new u straight into the apply: one grid barrier per
+// iteration.  Starts from the residual in c.r[0] with <r,r> = rr0; stops when
+// <r, r> <= thresh or after max_iter iterations.  Returns 1 converged, 0
+// capped, -1 barrier failure; *iters gets the count.
+template <typename R>
+__device__ int pcg1(const SolveArgs& a, ApplySmem<R>& sm, const CGBufs<R>& c, R thresh, int max_iter, R* red,
+                    int* iters, Tracer& tr) {
+  __shared__ R s_scal[3];
   const Grid3 g = a.g;
   const Tiling t = a.t;
-  const long long nn = (long long)g.nnx * g.nny * g.nnz;
-  const long long ne = (long long)g.nx * g.ny * g.nz;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long gstride = (long long)gridDim.x * blockDim.x;
+  const int nn = g.nnx * g.nny * g.nnz;
+  const int ne = g.nx * g.ny * g.nz;
   const int ntiles = t.ntx * t.nty * t.ntz;
+  auto lam8 = [&](int e, R (&l8)[8]) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) l8[m] = __ldcg(c.lam + m * ne + e);
+  };
+  R alpha = R(0), beta = R(0), gamma = R(0);
+  int it = 0;
+  bool conv = false;
+  // pass -1: w_0 = A u_0 (no update); passes k >= 0 update then apply w_{k+1}
+  for (int k = -1; k < max_iter; ++k) {
+    const int cur = k < 0 ? 0 : (k & 1), nxt = k < 0 ? 0 : (cur ^ 1);
+    const bool first = k == 0;
+    // pass pointers chosen by selects (no dynamic indexing into the struct)
+    const R* r_cur = cur ? c.r[1] : c.r[0];
+    const R* p_cur = cur ? c.p[1] : c.p[0];
+    const R* s_cur = cur ? c.s[1] : c.s[0];
+    const R* q_cur = cur ? c.q[1] : c.q[0];
+    const R* X_cur = cur ? c.X[1] : c.X[0];
+    R* r_nxt = nxt ? c.r[1] : c.r[0];
+    R* p_nxt = nxt ? c.p[1] : c.p[0];
+    R* s_nxt = nxt ? c.s[1] : c.s[0];
+    R* q_out = (k >= 0 && nxt) ? c.q[1] : c.q[0];
+    R* X_out = (k >= 0 && nxt) ? c.X[1] : c.X[0];
+    R vg = R(0), vd = R(0), vr = R(0);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      auto load = [&](int n, int i, int j, int kk, bool owned) -> R {
+        if (is_dir(g, a.dir, i, j, kk)) return R(0);
+        const R dv = __ldcg(c.dinv + n);
+        const R rk = __ldcg(r_cur + n);
+        if (k < 0) {
+          const R u = dv * rk;
+          if (owned) {
+            vg = fma(rk, u, vg);
+            vr = fma(rk, rk, vr);
+          }
+          return u;
+        }
+        const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
+        const bool lz = kk > 0 && kk < g.nz && (kk % t.ez) == 0;
+        const R w = gather_partials(q_cur, X_cur, nn, n, low_faces(g, t, i, ly, lz));
+        const R u = dv * rk;
+        R pv = u, sv = w;
+        if (!first) {
+          pv = fma(beta, __ldcg(p_cur + n), u);
+          sv = fma(beta, __ldcg(s_cur + n), w);
+        }
+        const R rn = fma(-alpha, sv, rk);
+        const R un = dv * rn;
+        if (owned) {
+          p_nxt[n] = pv;
+          s_nxt[n] = sv;
+          r_nxt[n] = rn;
+          c.x[n] = fma(alpha, pv, __ldcg(c.x + n));
+          vg = fma(rn, un, vg);
+          vr = fma(rn, rn, vr);
+        }
+        return un;
+      };
+      auto emit = [&](int n, int slot, R y, R xin) {
+        store_partial(q_out, X_out, nn, n, slot, y, false);
+        vd = fma(xin, y, vd);
+      };
+      apply_tile<R>(g, t, tile, sm, load, lam8, emit);
+    }
+    tr.mark(TR_CG_APPLY);
+    {
+      R v[3] = {vg, vd, vr};
+      block_reduce_store<3>(v, red + RS_PQ * a.red_stride, a.red_stride);
+    }
+    if (!grid_sync(a.bar)) return -1;
+    tr.mark(TR_CG_PASS);
+    R tot[3];
+    grid_total<3>(red + RS_PQ * a.red_stride, a.red_stride, tot);
+    if (k >= 0) {
+      ++it;
+      if (tot[2] <= thresh) {
+        conv = true;
+        break;
+      }
+    }
+    // next scalars, once per block
+    if (threadIdx.x == 0) {
+      const R gn = tot[0], dn = tot[1];
+      R b = k < 0 ? R(0) : gn / gamma;
+      R den = k < 0 ? dn : dn - b * gn / alpha;
+      s_scal[0] = gn / den;
+      s_scal[1] = b;
+      s_scal[2] = (den > R(0) && gn > R(0)) ? R(1) : R(0);
+    }
+    __syncthreads();
+    if (s_scal[2] == R(0)) break;  // breakdown (no further progress possible): stop
+    gamma = tot[0];
+    alpha = s_scal[0];
+    beta = s_scal[1];
+    __syncthreads();
+  }
+  *iters = it;
+  // the converged residual sits in r[it & 1]; callers read it from there
+  return conv ? 1 : 0;
+}
+
+__device__ inline double elem_mean(const double* T, const Grid3& g, int ie, int je, int ke) {
+  const int S = g.nnx * g.nny;
+  const int n0 = ie + g.nnx * je + S * ke;
+  double s = __ldcg(T + n0);
+  s += __ldcg(T + n0 + 1);
+  s += __ldcg(T + n0 + g.nnx);
+  s += __ldcg(T + n0 + g.nnx + 1);
+  s += __ldcg(T + n0 + S);
+  s += __ldcg(T + n0 + S + 1);
+  s += __ldcg(T + n0 + S + g.nnx);
+  s += __ldcg(T + n0 + S + g.nnx + 1);
+  return s * 0.125;
+}
+
+// Internal linkage: every translation unit that launches the solve compiles its
+// own copy (the two-level path and the allocation-free single step).
+static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) {
+  __shared__ __align__(16) unsigned char smem_raw[sizeof(ApplySmem<double>)];
+  __shared__ double s_Mhat[64], s_Khat[64];
+  ApplySmem<double>& sm64 = *reinterpret_cast<ApplySmem<double>*>(smem_raw);
+  ApplySmem<float>& sm32 = *reinterpret_cast<ApplySmem<float>*>(smem_raw);
+  if (ld_volatile_i32(a.bar.status) != 0) return;  // an earlier solve failed: leave state untouched
+  Tracer tr{a.trace};
+  tr.mark(TR_START);
+  const Grid3 g = a.g;
+  const Tiling t = a.t;
+  const int nn = g.nnx * g.nny * g.nnz;
+  const int ne = g.nx * g.ny * g.nz;
+  const int S = g.nnx * g.nny;
+  const int ntiles = t.ntx * t.nty * t.ntz;
+  const bool refined = a.precision == PREC_FP32_REFINED;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstride = gridDim.x * blockDim.x;
   if (threadIdx.x < 64) {
     s_Mhat[threadIdx.x] = a.Mhat[threadIdx.x];
     s_Khat[threadIdx.x] = a.Khat[threadIdx.x];
   }
 
-  // ---- phase 0: coefficients, Dirichlet increments, load ------------------
-  for (long long e = gtid; e < ne; e += gstride) {
-    int ie = (int)(e % g.nx), je = (int)((e / g.nx) % g.ny), ke = (int)(e / ((long long)g.nx * g.ny));
-    double s = __ldcg(a.T_in + node_id(g, ie, je, ke));
-    s += __ldcg(a.T_in + node_id(g, ie + 1, je, ke));
-    s += __ldcg(a.T_in + node_id(g, ie, je + 1, ke));
-    s += __ldcg(a.T_in + node_id(g, ie + 1, je + 1, ke));
-    s += __ldcg(a.T_in + node_id(g, ie, je, ke + 1));
-    s += __ldcg(a.T_in + node_id(g, ie + 1, je, ke + 1));
-    s += __ldcg(a.T_in + node_id(g, ie, je + 1, ke + 1));
-    s += __ldcg(a.T_in + node_id(g, ie + 1, je + 1, ke + 1));
-    const double Tb = s * 0.125;
-    const uint8_t st = a.state[((long long)ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox];
+  // ---- phase 0: coefficients and eigenvalues, Dirichlet increments, load ---
+  for_elems(g, [&](int e, int ie, int je, int ke) {
+    const double Tb = elem_mean(a.T_in, g, ie, je, ke);
+    const uint8_t st = a.state[(ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox];
     const double rc = a.mat.rho * (a.mat.c0 + a.mat.c1 * (Tb - a.mat.Tref));
     double k = a.mat.k0 + a.mat.k1 * (Tb - a.mat.Tref);
     if (st == POWDER) k = a.mat.powder_factor * k;
-    a.s_e[e] = (R)(rc / a.dt);
-    a.k_e[e] = (R)k;
-  }
-  for (long long n = gtid; n < nn; n += gstride) {
-    int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny), k = (int)(n / ((long long)g.nnx * g.nny));
-    double u = 0.0;
-    if (is_dir(g, a.dir, i, j, k)) u = dir_value(a.dv, i, j, k, n) - __ldcg(a.T_in + n);
-    a.u[n] = u;
-  }
-  for (long long n = gtid; n < (long long)g.nnx * g.nny; n += gstride) {
-    int i = (int)(n % g.nnx), j = (int)(n / g.nnx);
-    a.F[n] = top_load(a.ld, g, i, j);
+    const double se = rc * (1.0 / a.dt);
+    a.s_e[e] = se;
+    a.k_e[e] = k;
+    a.lam[e] = se * a.Mc[0];
+#pragma unroll
+    for (int m = 1; m < 8; ++m) a.lam[m * ne + e] = se * a.Mc[m] + k * a.Kc[m];
+    if (refined) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) a.lam32[m * ne + e] = (float)(se * a.Mc[m] + k * a.Kc[m]);
+    }
+  });
+  // increments: 0 on free nodes, g - T^k on Dirichlet nodes (disjoint writes)
+  for_nodes(g, t, [&](int n, int i, int j, int k, bool, bool) {
+    if (!is_dir(g, a.dir, i, j, k)) a.u[n] = 0.0;
+  });
+  for_dirichlet(g, a.dir, [&](int n, int i, int j, int k) {
+    a.u[n] = dir_value(a.dv, i, j, k, n) - __ldcg(a.T_in + n);
+  });
+  {
+    const int nf = load_factors(a.ld), w = g.nnx + g.nny;
+    for (int m = gtid; m < nf * w; m += gstride) a.G[m] = load_factor(a.ld, g, m / w, m % w);
   }
   if (!grid_sync(a.bar)) return;
+  tr.mark(TR_PHASE0);
 
   // ---- phase 1: Jacobi diagonal and right-hand side partials --------------
-  for (long long n = gtid; n < nn; n += gstride) {
-    int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny), k = (int)(n / ((long long)g.nnx * g.nny));
-    R di = R(0);
+  for (int n = gtid; n < S; n += gstride) {
+    int j = n / g.nnx, i = n - j * g.nnx;
+    a.F[n] = top_load_tab(a.ld, g, a.G, i, j);
+  }
+  for_nodes(g, t, [&](int n, int i, int j, int k, bool, bool) {
+    double di = 0.0;
     if (!is_dir(g, a.dir, i, j, k)) {
       double d = 0.0;
       for (int dz = -1; dz <= 0; ++dz)
@@ -419,170 +710,162 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs<R> a) {
           for (int dx = -1; dx <= 0; ++dx) {
             int ie = i + dx, je = j + dy, ke = k + dz;
             if (ie < 0 || je < 0 || ke < 0 || ie >= g.nx || je >= g.ny || ke >= g.nz) continue;
-            long long e = elem_id(g, ie, je, ke);
-            d += (double)__ldcg(a.s_e + e) * a.Md + (double)__ldcg(a.k_e + e) * a.Kd;
+            int e = ie + g.nx * (je + g.ny * ke);
+            d += __ldcg(a.s_e + e) * a.Md + __ldcg(a.k_e + e) * a.Kd;
           }
-      di = (R)(1.0 / d);
+      di = 1.0 / d;
     }
     a.dinv[n] = di;
-  }
+    if (refined) a.dinv32[n] = (float)di;
+  });
   {
-    // r_partial = A u_D-guess (s and k) + K T  via two passes
-    auto lam_full = [&](long long e, R (&l8)[8]) {
-      R s = __ldcg(a.s_e + e), k = __ldcg(a.k_e + e);
-      l8[0] = s * (R)a.Mc[0];
+    // partials of A u_D (u holds the Dirichlet increments, 0 elsewhere) + K T^k
+    auto lam_full = [&](int e, double (&l8)[8]) {
 #pragma unroll
-      for (int m = 1; m < 8; ++m) l8[m] = s * (R)a.Mc[m] + k * (R)a.Kc[m];
+      for (int m = 0; m < 8; ++m) l8[m] = __ldcg(a.lam + m * ne + e);
     };
-    auto lam_k = [&](long long e, R (&l8)[8]) {
-      R k = __ldcg(a.k_e + e);
-      l8[0] = R(0);
+    auto lam_k = [&](int e, double (&l8)[8]) {
+      const double k = __ldcg(a.k_e + e);
+      l8[0] = 0.0;
 #pragma unroll
-      for (int m = 1; m < 8; ++m) l8[m] = k * (R)a.Kc[m];
+      for (int m = 1; m < 8; ++m) l8[m] = k * a.Kc[m];
     };
+    auto load_u = [&](int n, int, int, int, bool) -> double { return __ldcg(a.u + n); };
+    auto load_T = [&](int n, int, int, int, bool) -> double { return __ldcg(a.T_in + n); };
+    auto emit1 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
+    auto emit2 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, true); };
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      auto load_u = [&](long long n) -> R { return (R)__ldcg(a.u + n); };
-      auto load_T = [&](long long n) -> R { return (R)__ldcg(a.T_in + n); };
-      auto emit1 = [&](int li, int lj, int ex, int ey, long long n, int i, int j, int k, R y, R xin) {
-        store_partial(a.q, a.X, nn, n, window_slot(g, t, tile, i, j, k), y, false);
-      };
-      auto emit2 = [&](int li, int lj, int ex, int ey, long long n, int i, int j, int k, R y, R xin) {
-        store_partial(a.q, a.X, nn, n, window_slot(g, t, tile, i, j, k), y, true);
-      };
-      apply_tile<R>(g, t, tile, sm, load_u, lam_full, emit1);
-      apply_tile<R>(g, t, tile, sm, load_T, lam_k, emit2);
+      apply_tile<double>(g, t, tile, sm64, load_u, lam_full, emit1);
+      apply_tile<double>(g, t, tile, sm64, load_T, lam_k, emit2);
     }
   }
   if (!grid_sync(a.bar)) return;
+  tr.mark(TR_RHS);
   {
     double v[2] = {0.0, 0.0};
-    for (long long n = gtid; n < nn; n += gstride) {
-      int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny), k = (int)(n / ((long long)g.nnx * g.nny));
+    for_nodes(g, t, [&](int n, int i, int j, int k, bool ly, bool lz) {
       double rr = 0.0;
       if (!is_dir(g, a.dir, i, j, k)) {
-        double Fn = (k == g.nz) ? __ldcg(a.F + (n - (long long)g.nnx * g.nny * g.nz)) : 0.0;
-        rr = Fn - (double)gather_partials(g, t, a.q, a.X, nn, n, i, j, k);
+        double Fn = (k == g.nz) ? __ldcg(a.F + (n - S * g.nz)) : 0.0;
+        rr = Fn - gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
       }
       a.r[n] = rr;
-      v[0] += rr * rr * (double)__ldcg(a.dinv + n);
+      v[0] += rr * rr * __ldcg(a.dinv + n);
       v[1] += rr * rr;
-    }
+    });
     block_reduce_store<2>(v, a.red + RS_RZ0 * a.red_stride, a.red_stride);
   }
   if (!grid_sync(a.bar)) return;
+  tr.mark(TR_RESID);
   double tot0[2];
   grid_total<2>(a.red + RS_RZ0 * a.red_stride, a.red_stride, tot0);
-  double rz = tot0[0];
   const double bb = tot0[1];
-
-  // ---- phase 2: preconditioned conjugate gradients ------------------------
-  int it = 0;
-  bool conv = !(bb > 0.0) || (a.tol >= 1.0);
-  double rz_prev = 1.0;
   const double thresh = a.tol * a.tol * bb;
-  while (!conv && it < a.max_iter) {
-    const double beta = it == 0 ? 0.0 : rz / rz_prev;
-    R* pold = (it & 1) ? a.p0 : a.p1;
-    R* pnew = (it & 1) ? a.p1 : a.p0;
-    double pq = 0.0;
-    auto lam_full = [&](long long e, R (&l8)[8]) {
-      R s = __ldcg(a.s_e + e), k = __ldcg(a.k_e + e);
-      l8[0] = s * (R)a.Mc[0];
-#pragma unroll
-      for (int m = 1; m < 8; ++m) l8[m] = s * (R)a.Mc[m] + k * (R)a.Kc[m];
-    };
-    const R rbeta = (R)beta;
-    const bool first = it == 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      auto load_p = [&](long long n) -> R {
-        R z = __ldcg(a.dinv + n) * (R)__ldcg(a.r + n);
-        return first ? z : z + rbeta * __ldcg(pold + n);
-      };
-      auto emit = [&](int li, int lj, int ex, int ey, long long n, int i, int j, int k, R y, R xin) {
-        int slot = window_slot(g, t, tile, i, j, k);
-        store_partial(a.q, a.X, nn, n, slot, y, false);
-        if (slot == 0) pnew[n] = xin;
-        pq += (double)(xin * y);
-      };
-      apply_tile<R>(g, t, tile, sm, load_p, lam_full, emit);
-    }
+
+  // ---- phase 2: solve ------------------------------------------------------
+  int it = 0, outer = 0;
+  bool conv = !(bb > 0.0) || (a.tol >= 1.0);
+  if (!conv && !refined) {
+    CGBufs<double> c{a.u, {a.r, a.r2}, {a.p0, a.p1}, {a.s0, a.s1}, {a.q, a.q2}, {a.X, a.X2}, a.dinv, a.lam};
+    int res = pcg1<double>(a, sm64, c, thresh, a.max_iter, a.red, &it, tr);
+    if (res < 0) return;
+    conv = res == 1;
+  }
+  // refined: FP32 CG for the correction d of the FP64 residual, FP64 update of
+  // u and of the residual r -= A d, until ||r|| <= tol ||r_0||
+  while (!conv && refined && outer < a.max_outer) {
     {
-      double v[1] = {pq};
-      block_reduce_store<1>(v, a.red + RS_PQ * a.red_stride, a.red_stride);
+      float v[2] = {0.0f, 0.0f};
+      for_nodes(g, t, [&](int n, int, int, int, bool, bool) {
+        float rf = (float)__ldcg(a.r + n);
+        a.r32[n] = rf;
+        a.d32[n] = 0.0f;
+        v[0] = fmaf(rf * rf, __ldcg(a.dinv32 + n), v[0]);
+        v[1] = fmaf(rf, rf, v[1]);
+      });
+      block_reduce_store<2>(v, a.red32 + RS_RZ0 * a.red_stride, a.red_stride);
     }
     if (!grid_sync(a.bar)) return;
-    double tp[1];
-    grid_total<1>(a.red + RS_PQ * a.red_stride, a.red_stride, tp);
-    const double alpha = rz / tp[0];
-    double v[2] = {0.0, 0.0};
-    for (long long n = gtid; n < nn; n += gstride) {
-      int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny), k = (int)(n / ((long long)g.nnx * g.nny));
-      if (is_dir(g, a.dir, i, j, k)) continue;
-      double qn = (double)gather_partials(g, t, a.q, a.X, nn, n, i, j, k);
-      double pn = (double)__ldcg(pnew + n);
-      double un = __ldcg(a.u + n) + alpha * pn;
-      double rn = __ldcg(a.r + n) - alpha * qn;
-      a.u[n] = un;
+    tr.mark(TR_OUTER_INIT);
+    float t32[2];
+    grid_total<2>(a.red32 + RS_RZ0 * a.red_stride, a.red_stride, t32);
+    int inner = 0;
+    CGBufs<float> c{a.d32, {a.r32, a.r32b}, {a.p0f, a.p1f}, {a.s0f, a.s1f}, {a.q32, a.q32b}, {a.X32, a.X32b},
+                    a.dinv32, a.lam32};
+    const float ti = (float)a.tol_inner;
+    int res = pcg1<float>(a, sm32, c, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+    if (res < 0) return;
+    it += inner;
+    ++outer;
+    // FP64 apply of the correction (exact in FP64: d is an FP32 vector)
+    auto lam_full = [&](int e, double (&l8)[8]) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) l8[m] = __ldcg(a.lam + m * ne + e);
+    };
+    auto load_d = [&](int n, int, int, int, bool) -> double { return (double)__ldcg(a.d32 + n); };
+    auto emit = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+      apply_tile<double>(g, t, tile, sm64, load_d, lam_full, emit);
+    if (!grid_sync(a.bar)) return;
+    tr.mark(TR_OUTER_APPLY);
+    double v[1] = {0.0};
+    for_nodes(g, t, [&](int n, int i, int j, int k, bool ly, bool lz) {
+      if (is_dir(g, a.dir, i, j, k)) return;
+      double y = gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
+      double rn = __ldcg(a.r + n) - y;
       a.r[n] = rn;
-      v[0] += rn * rn * (double)__ldcg(a.dinv + n);
-      v[1] += rn * rn;
-    }
-    block_reduce_store<2>(v, a.red + RS_RZ * a.red_stride, a.red_stride);
+      a.u[n] = __ldcg(a.u + n) + (double)__ldcg(a.d32 + n);
+      v[0] += rn * rn;
+    });
+    block_reduce_store<1>(v, a.red + RS_RR * a.red_stride, a.red_stride);
     if (!grid_sync(a.bar)) return;
-    double tr[2];
-    grid_total<2>(a.red + RS_RZ * a.red_stride, a.red_stride, tr);
-    rz_prev = rz;
-    rz = tr[0];
-    ++it;
-    conv = tr[1] <= thresh;
+    double trr[1];
+    grid_total<1>(a.red + RS_RR * a.red_stride, a.red_stride, trr);
+    tr.mark(TR_OUTER_END);
+    conv = trr[0] <= thresh;
   }
   const int lvl = a.level;
   if (!conv) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       atomicCAS(a.bar.status, 0, (int)ST_NOCONV);
       a.stats->iters[lvl] += it;
+      a.stats->outer[lvl] += outer;
       a.stats->last_iters[lvl] = it;
     }
     return;
   }
 
   // ---- phase 3: update, states, energy -------------------------------------
-  for (long long n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
+  tr.mark(TR_UPDATE);
+  for (int n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
   if (a.update_state || a.energy) {
     if (!grid_sync(a.bar)) return;
     double v[3] = {0.0, 0.0, 0.0};
-    for (long long e = gtid; e < ne; e += gstride) {
-      int ie = (int)(e % g.nx), je = (int)((e / g.nx) % g.ny), ke = (int)(e / ((long long)g.nx * g.ny));
+    for_elems(g, [&](int e, int ie, int je, int ke) {
       if (a.update_state) {
-        double s = __ldcg(a.T_out + node_id(g, ie, je, ke));
-        s += __ldcg(a.T_out + node_id(g, ie + 1, je, ke));
-        s += __ldcg(a.T_out + node_id(g, ie, je + 1, ke));
-        s += __ldcg(a.T_out + node_id(g, ie + 1, je + 1, ke));
-        s += __ldcg(a.T_out + node_id(g, ie, je, ke + 1));
-        s += __ldcg(a.T_out + node_id(g, ie + 1, je, ke + 1));
-        s += __ldcg(a.T_out + node_id(g, ie, je + 1, ke + 1));
-        s += __ldcg(a.T_out + node_id(g, ie + 1, je + 1, ke + 1));
-        const double Tb = s * 0.125;
-        uint8_t* sp = a.state + ((long long)ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox;
+        const double Tb = elem_mean(a.T_out, g, ie, je, ke);
+        uint8_t* sp = a.state + (ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox;
         uint8_t st = *sp;
         uint8_t ns = (st == POWDER) ? POWDER : SOLID;
         if (Tb > a.mat.T_melt) ns = MELTED;
         *sp = ns;
       }
       if (a.energy) {
-        double us = 0.0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          us += __ldcg(a.u + node_id(g, ie + (c & 1), je + ((c >> 1) & 1), ke + (c >> 2)));
-        v[0] += (double)__ldcg(a.s_e + e) * a.dt * a.vol8 * us;
+        const int n0 = ie + g.nnx * je + S * ke;
+        double us = __ldcg(a.u + n0);
+        us += __ldcg(a.u + n0 + 1);
+        us += __ldcg(a.u + n0 + g.nnx);
+        us += __ldcg(a.u + n0 + g.nnx + 1);
+        us += __ldcg(a.u + n0 + S);
+        us += __ldcg(a.u + n0 + S + 1);
+        us += __ldcg(a.u + n0 + S + g.nnx);
+        us += __ldcg(a.u + n0 + S + g.nnx + 1);
+        v[0] += __ldcg(a.s_e + e) * a.dt * a.vol8 * us;
       }
-    }
+    });
     if (a.energy) {
-      for (long long n = gtid; n < (long long)g.nnx * g.nny; n += gstride) v[1] += a.dt * __ldcg(a.F + n);
-      __syncthreads();
-      for (long long n = gtid; n < nn; n += gstride) {
-        int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny), k = (int)(n / ((long long)g.nnx * g.nny));
-        if (!is_dir(g, a.dir, i, j, k)) continue;
+      for (int n = gtid; n < S; n += gstride) v[1] += a.dt * __ldcg(a.F + n);
+      for_dirichlet(g, a.dir, [&](int n, int i, int j, int k) {
         // reaction of a Dirichlet row: (S u + K T^{k+1})_n - F_n
         double R_n = 0.0;
         for (int dz = -1; dz <= 0; ++dz)
@@ -590,20 +873,20 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs<R> a) {
             for (int dx = -1; dx <= 0; ++dx) {
               int ie = i + dx, je = j + dy, ke = k + dz;
               if (ie < 0 || je < 0 || ke < 0 || ie >= g.nx || je >= g.ny || ke >= g.nz) continue;
-              long long e = elem_id(g, ie, je, ke);
-              double se = (double)__ldcg(a.s_e + e), kk = (double)__ldcg(a.k_e + e);
+              int e = ie + g.nx * (je + g.ny * ke);
+              double se = __ldcg(a.s_e + e), kk = __ldcg(a.k_e + e);
               int la = (i - ie) + 2 * (j - je) + 4 * (k - ke);
               double acc = 0.0;
 #pragma unroll
               for (int b = 0; b < 8; ++b) {
-                long long nb = node_id(g, ie + (b & 1), je + ((b >> 1) & 1), ke + (b >> 2));
+                int nb = (ie + (b & 1)) + g.nnx * (je + ((b >> 1) & 1)) + S * (ke + (b >> 2));
                 acc += se * s_Mhat[la * 8 + b] * __ldcg(a.u + nb) + kk * s_Khat[la * 8 + b] * __ldcg(a.T_out + nb);
               }
               R_n += acc;
             }
-        if (k == g.nz) R_n -= __ldcg(a.F + (n - (long long)g.nnx * g.nny * g.nz));
+        if (k == g.nz) R_n -= __ldcg(a.F + (n - S * g.nz));
         v[2] += a.dt * R_n;
-      }
+      });
     }
     block_reduce_store<3>(v, a.red + RS_ES * a.red_stride, a.red_stride);
     if (!grid_sync(a.bar)) return;
@@ -617,8 +900,10 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs<R> a) {
       }
     }
   }
+  tr.mark(TR_END);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.stats->iters[lvl] += it;
+    a.stats->outer[lvl] += outer;
     a.stats->solves[lvl] += 1;
     a.stats->last_iters[lvl] = it;
     if (it > a.stats->max_iters[lvl]) a.stats->max_iters[lvl] = it;

@@ -88,7 +88,7 @@ TL_NOALLOC_MAX_NODES = 65536
 EXPORTS = [
     "tl_create_problem", "tl_coarse_step", "tl_fine_substeps", "tl_restrict", "tl_macro_steps",
     "tl_sync", "tl_node_count", "tl_get_temperature", "tl_get_state", "tl_get_stats",
-    "tl_destroy_problem", "tl_status_string", "tl_box_step_noalloc",
+    "tl_destroy_problem", "tl_status_string", "tl_box_step_noalloc", "tl_trace_last_solve",
 ]
 
 _lib = None
@@ -130,6 +130,8 @@ def load(path=LIB_PATH):
     lib.tl_box_step_noalloc.argtypes = [C.POINTER(tl_box_step_desc), C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p]
     lib.tl_box_step_noalloc.restype = C.c_int
+    lib.tl_trace_last_solve.argtypes = [P, C.c_int, C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_size_t)]
+    lib.tl_trace_last_solve.restype = C.c_int
     _lib = lib
     return lib
 
@@ -230,6 +232,19 @@ def tl_box_step_noalloc(desc, T_in_ptr, T_out_ptr, state_ptr, stream=None):
                                       C.c_void_p(state_ptr), C.c_void_p(stream))
 
 
+TRACE_MARKS = {0: "start", 1: "phase0", 2: "rhs", 3: "resid", 4: "cg_pass", 5: "outer_init",
+               6: "outer_apply", 7: "outer_end", 8: "update", 9: "end", 10: "cg_apply"}
+
+
+def tl_trace_last_solve(h, level, cap=1024):
+    """Returns (status, [(marker, ns), ...]) of the level's most recent solve."""
+    buf = (C.c_uint64 * (2 * cap))()
+    n = C.c_size_t()
+    st = load().tl_trace_last_solve(h, int(level), buf, cap, C.byref(n))
+    m = min(n.value, cap)
+    return st, [(int(buf[2 * i]), int(buf[2 * i + 1])) for i in range(m)]
+
+
 def _check(st, what):
     if st != TL_OK:
         raise TLError(st, what)
@@ -280,6 +295,11 @@ class Problem:
         _check(st, "tl_get_stats")
         return {name: (list(getattr(s, name)) if name == "origin" else getattr(s, name))
                 for name, _ in tl_stats._fields_}
+
+    def trace(self, level):
+        st, ev = tl_trace_last_solve(self.h, level)
+        _check(st, "tl_trace_last_solve")
+        return ev
 
     def close(self):
         if self.h:

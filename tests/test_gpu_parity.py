@@ -181,3 +181,52 @@ def test_deterministic_reruns():
         out.append(prob.temperature(tl.TL_FINE)[0])
         prob.close()
     assert np.array_equal(out[0], out[1])
+
+
+# ---- precision form: FP32 inner CG with FP64 defect correction -------------
+# Bar: relative L2 <= 1e-6 against the FP64 oracle (the form's stated
+# accuracy); the outer residual tolerance 1e-10 typically gives ~1e-10.
+
+REFINED_TOL = 1e-6
+
+
+def test_refined_single_track_tiny_against_oracle():
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    for _ in range(5):
+        prob.macro_steps(10)
+        ref.run(10)
+        Tf, org = prob.temperature(tl.TL_FINE)
+        Tc, _ = prob.temperature(tl.TL_COARSE)
+        assert tuple(org) == tuple(ref.origin)
+        assert rel(Tf, ref.Tf) <= REFINED_TOL and rel(Tc, ref.Tc) <= REFINED_TOL
+        assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+    st = prob.stats()
+    assert st["outer_iters_fine"] >= st["solves_fine"]
+    prob.close()
+
+
+def test_refined_matches_fp64_gpu_path_multitrack():
+    base = workloads.workload("multitrack_10mm")
+    p64 = tl.Problem(dict(base, precision=tl.TL_FP64, tol=1e-12))
+    p32 = tl.Problem(dict(base, precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5))
+    p64.macro_steps(6)
+    p32.macro_steps(6)
+    a, _ = p64.temperature(tl.TL_FINE)
+    b, _ = p32.temperature(tl.TL_FINE)
+    assert rel(b, a) <= REFINED_TOL
+    assert np.array_equal(p64.state(tl.TL_FINE), p32.state(tl.TL_FINE))
+    p64.close()
+    p32.close()
+
+
+def test_refined_energy_identity():
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5)
+    prob = tl.Problem(cfg)
+    prob.macro_steps(10)
+    st = prob.stats()
+    for lvl in ("fine", "coarse"):
+        s, l, f = (st[f"energy_{lvl}_{k}"] for k in ("stored", "laser", "flux"))
+        assert abs(s - l - f) <= 1e-7 * max(abs(s), abs(l)), lvl
+    prob.close()
