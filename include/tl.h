@@ -189,6 +189,46 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
 tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap,
                               size_t* n_out);
 
+/* ---- Batched jobs (many independent problems in one persistent kernel) ---
+ * A batch advances several problems together.  Each round is
+ * launches_per_round cooperative launches of one persistent kernel; in every
+ * launch each active problem performs the next solve of its own Algorithm 1
+ * sequence (predictor with the patch motion fused in, one fine micro step, or
+ * corrector with the restriction fused into its boundary data) on its own
+ * slice of the grid: slices are sized in proportion to the solves' element
+ * counts, and each problem keeps its own buffers, barrier words and
+ * reductions, so problems never wait for each other and results match the
+ * problem run alone up to rounding (the slice changes the summation order).
+ * The launches of a round are captured once as a CUDA graph and replayed;
+ * the per-launch job tables are refreshed from pinned host memory each round.
+ * Problems join and leave only between macro steps; while in a batch their
+ * work runs on the batch's stream.  The paper has no batching; it remarks that
+ * the method is embarrassingly parallel (Section 5.3). */
+typedef struct tl_batch tl_batch;
+
+/* max_jobs: at most this many active problems (<= 512, and at most the number
+ * of co-resident blocks).  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl_batch** out);
+
+/* Add a problem for macro_steps more macro steps; *id_out gets its job id.
+ * Errors: TL_ESTATE (not between macro steps), TL_ENOMEM (batch full). */
+tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out);
+
+/* Enqueue one round (asynchronous after a synchronisation with the previous
+ * round); *active_out (may be NULL) gets the number of jobs in its first
+ * launch. */
+tl_status tl_batch_round(tl_batch* b, int* active_out);
+
+/* Synchronise and report (and remove from the batch) up to cap jobs that
+ * finished their macro steps; their problems return to their own streams. */
+tl_status tl_batch_poll(tl_batch* b, int* ids, int cap, int* n_out);
+
+/* Active jobs, launches so far, graph mode (1 replayed graph, -1 direct
+ * launches because capture was unavailable, 0 no round yet). */
+tl_status tl_batch_info(const tl_batch* b, int* active, long long* launches, int* graph_mode);
+
+void tl_batch_destroy(tl_batch* b);
+
 /* ---- Single step without device allocation ------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * may not allocate device memory while they run (a host application whose

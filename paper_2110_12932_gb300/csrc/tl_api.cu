@@ -21,6 +21,7 @@ enum Phase { NEED_PREDICT = 0, IN_SUBSTEPS = 1, NEED_CORRECT = 2 };
 struct Level {
   Grid3 g{};
   Tiling t{};
+  Tiling tb{};   // tiling used in batched launches (a slice of the grid)
   int grid = 0;  // cooperative grid size
   double* T = nullptr;    // current temperature
   double* T2 = nullptr;   // coarse: predictor T~+; fine: move double buffer
@@ -405,10 +406,12 @@ void injection_box(const tl_problem* p, int box[6]) {
   box[5] = c.NZc;
 }
 
-tl_status coarse_solve(tl_problem* p, bool correct) {
+// Arguments of the coarse backward-Euler step (predictor, or corrector with the
+// injected nodes as Dirichlet data: from the restriction buffer, or read from
+// the fine field when the restriction is fused into the solve).
+void build_coarse_args(tl_problem* p, bool correct, bool fused_inject, SolveArgs& a) {
   const tl_config& c = p->cfg;
   Level& L = p->C;
-  SolveArgs a{};
   fill_common(p, L, a);
   a.T_in = L.T;
   a.T_out = correct ? L.T : L.T2;
@@ -422,9 +425,16 @@ tl_status coarse_solve(tl_problem* p, bool correct) {
   } else {
     a.dir.box[0] = 1; a.dir.box[1] = 0; a.dir.box[2] = 1; a.dir.box[3] = 0; a.dir.box[4] = 1; a.dir.box[5] = 0;
   }
-  a.dv.kind = 1;
+  a.dv.kind = (correct && fused_inject) ? 2 : 1;
   a.dv.T_bottom = c.T_bottom;
   a.dv.inj = L.inj;
+  a.dv.Tf = p->Fi.T;
+  a.dv.fg = p->Fi.g;
+  a.dv.cg = L.g;
+  a.dv.oi = p->oi;
+  a.dv.oj = p->oj;
+  a.dv.ok = p->ok;
+  a.dv.r = c.r;
   if (c.coarse_source == 1)
     a.ld = gaussian_load(p, L, (p->n + 1) * c.dt_coarse, 0.0, 0.0);
   else
@@ -433,13 +443,18 @@ tl_status coarse_solve(tl_problem* p, bool correct) {
   a.energy = correct ? c.energy : 0;
   a.update_state = correct ? 1 : 0;
   a.level = 0;
-  return launch_solve(p, L, a);
 }
 
-tl_status fine_solve(tl_problem* p, int i) {
+tl_status coarse_solve(tl_problem* p, bool correct) {
+  SolveArgs a{};
+  build_coarse_args(p, correct, false, a);
+  return launch_solve(p, p->C, a);
+}
+
+// Arguments of fine micro step i of the current macro step.
+void build_fine_args(tl_problem* p, int i, SolveArgs& a) {
   const tl_config& c = p->cfg;
   Level& L = p->Fi;
-  SolveArgs a{};
   fill_common(p, L, a);
   a.T_in = L.T;
   a.T_out = L.T;
@@ -466,7 +481,12 @@ tl_status fine_solve(tl_problem* p, int i) {
   a.energy = c.energy;
   a.update_state = 1;
   a.level = 1;
-  return launch_solve(p, L, a);
+}
+
+tl_status fine_solve(tl_problem* p, int i) {
+  SolveArgs a{};
+  build_fine_args(p, i, a);
+  return launch_solve(p, p->Fi, a);
 }
 
 tl_status validate(const tl_config* c) {
@@ -532,7 +552,68 @@ tl_status move_patch(tl_problem* p) {
   return TL_OK;
 }
 
+// Advance p's Algorithm-1 sequence by one solve for a batched launch and fill
+// its arguments: one macro step = predictor (patch motion fused into it) + m
+// micro steps + corrector (restriction fused into its boundary data).
+// *weight gets the solve's element count.
+void next_batched_solve(tl_problem* p, SolveArgs& a, long long* weight) {
+  const tl_config& c = p->cfg;
+  a = SolveArgs{};
+  if (p->phase == NEED_PREDICT) {
+    int ni = p->oi, nj = p->oj;
+    origin_for(p, p->n, &ni, &nj);
+    build_coarse_args(p, false, false, a);
+    a.t = p->C.tb;
+    if (ni != p->oi || nj != p->oj) {
+      Level& F = p->Fi;
+      a.mv = MoveSpec{1, F.T, F.T2, p->C.T, F.g, p->C.g, p->oi, p->oj, ni, nj, p->ok, c.r};
+      std::swap(F.T, F.T2);
+      p->oi = ni;
+      p->oj = nj;
+      p->patch_moves++;
+    }
+    p->phase = IN_SUBSTEPS;
+    p->sub = 0;
+    *weight = (long long)p->C.g.nx * p->C.g.ny * p->C.g.nz;
+    return;
+  }
+  if (p->phase == IN_SUBSTEPS && p->sub < c.m) {
+    build_fine_args(p, p->sub, a);
+    a.t = p->Fi.tb;
+    p->sub++;
+    *weight = (long long)p->Fi.g.nx * p->Fi.g.ny * p->Fi.g.nz;
+    return;
+  }
+  build_coarse_args(p, true, true, a);
+  a.t = p->C.tb;
+  p->phase = NEED_PREDICT;
+  p->n++;
+  *weight = (long long)p->C.g.nx * p->C.g.ny * p->C.g.nz;
+}
+
 }  // namespace
+
+struct tl_batch {
+  struct Job {
+    tl_problem* p;
+    long long target;          // macro steps to reach
+    cudaStream_t saved_stream;
+    bool active;
+  };
+  cudaStream_t stream = nullptr;
+  int R = 0;                   // cooperative launches per round
+  int cap = 0;                 // jobs per launch at most (one block each at least)
+  int max_coop = 0, nsm = 0;
+  std::vector<Job> jobs;
+  std::vector<int> finished;   // ids that reached their target, not yet polled
+  BatchTable* d_tab = nullptr; // R tables
+  SolveArgs* d_args = nullptr; // R x cap job arguments
+  BatchTable* h_tab = nullptr; // pinned staging of the same
+  SolveArgs* h_args = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_state = 0;         // 0 not tried, 1 in use, -1 capture unavailable (direct launches)
+  long long launches = 0, rounds = 0;
+};
 
 extern "C" {
 
@@ -818,6 +899,244 @@ tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* hos
   }
   *n_out = n;
   return TL_OK;
+}
+
+// ---- batched jobs --------------------------------------------------------
+
+tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl_batch** out) {
+  if (!out) return TL_EINVAL;
+  *out = nullptr;
+  if (launches_per_round < 1 || launches_per_round > 64 || max_jobs < 1 || max_jobs > BATCH_MAX) return TL_EINVAL;
+  tl_batch* b = new (std::nothrow) tl_batch();
+  if (!b) return TL_ENOMEM;
+  b->stream = (cudaStream_t)stream;
+  b->R = launches_per_round;
+  int dev = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_batch_kernel, NT, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    delete b;
+    return TL_ECUDA;
+  }
+  b->max_coop = per_sm * b->nsm;
+  b->cap = std::min(max_jobs, b->max_coop);
+  const size_t targs = (size_t)b->R * b->cap * sizeof(SolveArgs), ttab = (size_t)b->R * sizeof(BatchTable);
+  e = cudaMalloc(&b->d_tab, ttab);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_args, targs);
+  if (e == cudaSuccess) e = cudaHostAlloc(&b->h_tab, ttab, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&b->h_args, targs, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->d_tab);
+    cudaFree(b->d_args);
+    cudaFreeHost(b->h_tab);
+    cudaFreeHost(b->h_args);
+    delete b;
+    return e == cudaErrorMemoryAllocation ? TL_ENOMEM : TL_ECUDA;
+  }
+  *out = b;
+  return TL_OK;
+}
+
+tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out) {
+  if (!b || !p || macro_steps < 0 || !id_out) return TL_EINVAL;
+  if (p->phase != NEED_PREDICT) return TL_ESTATE;  // join only between macro steps
+  int active = 0;
+  for (const auto& j : b->jobs) active += j.active ? 1 : 0;
+  if (active >= b->cap) return TL_ENOMEM;            // every launch slot is taken
+  for (const auto& j : b->jobs)
+    if (j.active && j.p == p) return TL_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(p->stream);  // the problem's own pending work first
+  if (e != cudaSuccess) return cuda_status(e);
+  // tiling for a slice of the grid: about two tiles per block of a job's share
+  const int share = std::max(1, b->max_coop / std::max(1, b->cap));
+  choose_tiling(p->C, std::max(1, share / 2), 2);
+  p->C.tb = p->C.t;
+  choose_tiling(p->Fi, std::max(1, share / 2), 2);
+  p->Fi.tb = p->Fi.t;
+  choose_tiling(p->C, p->nsm, p->max_coop / std::max(1, p->nsm));  // restore the whole-grid tiling
+  choose_tiling(p->Fi, p->nsm, p->max_coop / std::max(1, p->nsm));
+  tl_batch::Job job{p, (long long)p->n + macro_steps, p->stream, true};
+  p->stream = b->stream;
+  int id = -1;
+  for (size_t k = 0; k < b->jobs.size(); ++k)
+    if (!b->jobs[k].active && b->jobs[k].p == nullptr) { id = (int)k; break; }
+  if (id < 0) {
+    id = (int)b->jobs.size();
+    b->jobs.push_back(job);
+  } else {
+    b->jobs[id] = job;
+  }
+  *id_out = id;
+  return TL_OK;
+}
+
+namespace {
+
+// Split the blocks of one launch over its jobs in proportion to their element
+// counts (at least one block each, at most the job's reduction width).
+void allocate_blocks(const std::vector<long long>& w, const std::vector<int>& capb, int B, std::vector<int>& nb) {
+  const size_t J = w.size();
+  nb.assign(J, 1);
+  long long tw = 0;
+  for (long long x : w) tw += x;
+  int used = (int)J;
+  for (size_t j = 0; j < J; ++j) {
+    int want = (int)std::floor((double)B * w[j] / std::max(1LL, tw));
+    want = std::min(std::max(want, 1), capb[j]);
+    used += want - nb[j];
+    nb[j] = want;
+  }
+  while (used > B) {  // trim the largest shares
+    size_t k = 0;
+    for (size_t j = 1; j < J; ++j)
+      if (nb[j] > nb[k]) k = j;
+    if (nb[k] <= 1) break;
+    nb[k]--;
+    used--;
+  }
+  while (used < B) {  // hand out the rest where work per block is largest
+    int k = -1;
+    double best = 0;
+    for (size_t j = 0; j < J; ++j) {
+      if (nb[j] >= capb[j]) continue;
+      double r = (double)w[j] / nb[j];
+      if (r > best) { best = r; k = (int)j; }
+    }
+    if (k < 0) break;
+    nb[k]++;
+    used++;
+  }
+}
+
+}  // namespace
+
+tl_status tl_batch_round(tl_batch* b, int* active_out) {
+  if (!b) return TL_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(b->stream);  // staging buffers free again
+  if (e != cudaSuccess) return cuda_status(e);
+  int active = 0;
+  for (int k = 0; k < b->R; ++k) {
+    BatchTable& tab = b->h_tab[k];
+    SolveArgs* args = b->h_args + (size_t)k * b->cap;
+    std::vector<long long> w;
+    std::vector<int> capb;
+    int nj = 0;
+    for (size_t id = 0; id < b->jobs.size(); ++id) {
+      auto& j = b->jobs[id];
+      if (!j.active) continue;
+      if (j.p->n >= j.target && j.p->phase == NEED_PREDICT) {
+        j.active = false;
+        b->finished.push_back((int)id);
+        continue;
+      }
+      long long wt = 0;
+      next_batched_solve(j.p, args[nj], &wt);
+      const Tiling& t = args[nj].t;
+      capb.push_back(std::min(j.p->red_stride, t.ntx * t.nty * t.ntz));
+      w.push_back(wt);
+      j.p->launches++;
+      ++nj;
+    }
+    if (k == 0) active = nj;
+    std::vector<int> nb;
+    allocate_blocks(w, capb, b->max_coop, nb);
+    tab.njobs = nj;
+    tab.first[0] = 0;
+    for (int q = 0; q < nj; ++q) tab.first[q + 1] = tab.first[q] + nb[q];
+  }
+  if (active_out) *active_out = active;
+  e = cudaMemcpyAsync(b->d_tab, b->h_tab, (size_t)b->R * sizeof(BatchTable), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_args, b->h_args, (size_t)b->R * b->cap * sizeof(SolveArgs), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  auto launch_all = [&]() -> cudaError_t {
+    for (int k = 0; k < b->R; ++k) {
+      const BatchTable* tp = b->d_tab + k;
+      const SolveArgs* ap = b->d_args + (size_t)k * b->cap;
+      void* kargs[] = {(void*)&tp, (void*)&ap};
+      cudaError_t le = cudaLaunchCooperativeKernel((const void*)solve_batch_kernel, dim3(b->max_coop), dim3(NT),
+                                                   kargs, 0, b->stream);
+      if (le != cudaSuccess) return le;
+    }
+    return cudaSuccess;
+  };
+  if (b->graph_state == 0) {  // capture the round once; replay it every round
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = launch_all();
+      e = cudaStreamEndCapture(b->stream, &graph);
+      if (le == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+      else if (e == cudaSuccess) e = le;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+      b->graph_state = -1;
+    } else {
+      b->graph_state = 1;
+    }
+  }
+  e = b->graph_state == 1 ? cudaGraphLaunch(b->exec, b->stream) : launch_all();
+  if (e != cudaSuccess) return cuda_status(e);
+  b->launches += b->R;
+  b->rounds++;
+  return TL_OK;
+}
+
+tl_status tl_batch_poll(tl_batch* b, int* ids, int cap, int* n_out) {
+  if (!b || !n_out || (cap > 0 && !ids)) return TL_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  // jobs that just reached their target are retired here too
+  for (size_t id = 0; id < b->jobs.size(); ++id) {
+    auto& j = b->jobs[id];
+    if (j.active && j.p->n >= j.target && j.p->phase == NEED_PREDICT) {
+      j.active = false;
+      b->finished.push_back((int)id);
+    }
+  }
+  int n = 0;
+  while (!b->finished.empty() && n < cap) {
+    const int id = b->finished.front();
+    b->finished.erase(b->finished.begin());
+    auto& j = b->jobs[id];
+    j.p->stream = j.saved_stream;  // the problem leaves the batch
+    j.p = nullptr;
+    ids[n++] = id;
+  }
+  *n_out = n;
+  return TL_OK;
+}
+
+tl_status tl_batch_info(const tl_batch* b, int* active, long long* launches, int* graph_mode) {
+  if (!b) return TL_EINVAL;
+  int a = 0;
+  for (const auto& j : b->jobs) a += j.active ? 1 : 0;
+  if (active) *active = a;
+  if (launches) *launches = b->launches;
+  if (graph_mode) *graph_mode = b->graph_state;
+  return TL_OK;
+}
+
+void tl_batch_destroy(tl_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (auto& j : b->jobs)
+    if (j.p) j.p->stream = j.saved_stream;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->d_tab);
+  cudaFree(b->d_args);
+  cudaFreeHost(b->h_tab);
+  cudaFreeHost(b->h_args);
+  delete b;
 }
 
 void tl_destroy_problem(tl_problem* p) {

@@ -59,6 +59,12 @@ __host__ __device__ inline int split_lo(int n, int parts, int a) {
 // Word layout (BAR_WORDS unsigned ints, zero at creation): [0] root counter,
 // [1 .. BAR_MAXG] group counters, [BAR_GEN] generation, [BAR_STATUS] status.
 // ---------------------------------------------------------------------------
+// The block range a solve runs on: a whole cooperative grid, or one job's
+// slice of a batched grid.  bid is the block's index within the slice.
+struct VGrid {
+  int bid, nblk;
+};
+
 constexpr int BAR_GROUP = 32;
 constexpr int BAR_MAXG = 64;
 constexpr int BAR_GEN = BAR_MAXG + 1;
@@ -89,16 +95,16 @@ __device__ inline int ld_volatile_i32(const int* p) {
   return *(volatile const int*)p;
 }
 
-__device__ inline bool grid_sync(const Barrier& b, unsigned long long limit_ns = 1000000000ull) {
+__device__ inline bool grid_sync(const Barrier& b, const VGrid& vg, unsigned long long limit_ns = 1000000000ull) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned int g = ld_acquire_u32(b.gen);
     __threadfence();
-    const unsigned int grp = blockIdx.x / BAR_GROUP;
-    const unsigned int ngroups = (gridDim.x + BAR_GROUP - 1) / BAR_GROUP;
-    const unsigned int gsize = min((unsigned int)BAR_GROUP, gridDim.x - grp * BAR_GROUP);
+    const unsigned int grp = (unsigned int)vg.bid / BAR_GROUP;
+    const unsigned int ngroups = ((unsigned int)vg.nblk + BAR_GROUP - 1) / BAR_GROUP;
+    const unsigned int gsize = min((unsigned int)BAR_GROUP, (unsigned int)vg.nblk - grp * BAR_GROUP);
     bool released = false;
     if (atomicAdd(b.count + 1 + grp, 1u) == gsize - 1) {
       __threadfence();  // acquire side: the group's arrivals
@@ -138,7 +144,7 @@ __device__ inline bool grid_sync(const Barrier& b, unsigned long long limit_ns =
 // sub-partition's FP64 unit for ~64 cycles, so FP32 solves reduce in FP32.
 // ---------------------------------------------------------------------------
 template <int NV, typename T>
-__device__ inline void block_reduce_store(T (&v)[NV], T* slots, int stride) {
+__device__ inline void block_reduce_store(T (&v)[NV], T* slots, int stride, const VGrid& vg) {
   __shared__ T s_part[NV][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
@@ -156,21 +162,21 @@ __device__ inline void block_reduce_store(T (&v)[NV], T* slots, int stride) {
       T x = lane < nwarps ? s_part[a][lane] : T(0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) slots[(size_t)a * stride + blockIdx.x] = x;
+      if (lane == 0) slots[(size_t)a * stride + vg.bid] = x;
     }
   }
   __syncthreads();
 }
 
 template <int NV, typename T>
-__device__ inline void grid_total(const T* slots, int stride, T (&out)[NV]) {
+__device__ inline void grid_total(const T* slots, int stride, T (&out)[NV], const VGrid& vg) {
   __shared__ T s_tot[NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp == 0) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
       T x = T(0);
-      for (int s = lane; s < (int)gridDim.x; s += 32) x += __ldcg(slots + (size_t)a * stride + s);
+      for (int s = lane; s < vg.nblk; s += 32) x += __ldcg(slots + (size_t)a * stride + s);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
       if (lane == 0) s_tot[a] = x;

@@ -66,13 +66,13 @@ __device__ inline int dir_set(const Grid3& g, const DirSpec& d, int i, int j, in
 // sets spread evenly over the grid's threads (a node is visited by the first
 // set that holds it).
 template <class Body>
-__device__ inline void for_dirichlet(const Grid3& g, const DirSpec& d, Body body) {
+__device__ inline void for_dirichlet(const Grid3& g, const DirSpec& d, const VGrid& vg, Body body) {
   const int bx = d.box[1] - d.box[0] + 1, by = d.box[3] - d.box[2] + 1, bz = d.box[5] - d.box[4] + 1;
   const int sz[6] = {(d.faces & 16) ? g.nnx * g.nny : 0, (d.faces & 1) ? g.nny * g.nnz : 0,
                      (d.faces & 2) ? g.nny * g.nnz : 0, (d.faces & 4) ? g.nnx * g.nnz : 0,
                      (d.faces & 8) ? g.nnx * g.nnz : 0, (bx > 0 && by > 0 && bz > 0) ? bx * by * bz : 0};
   const int total = sz[0] + sz[1] + sz[2] + sz[3] + sz[4] + sz[5];
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < total; m += gridDim.x * blockDim.x) {
+  for (int m = vg.bid * blockDim.x + threadIdx.x; m < total; m += vg.nblk * blockDim.x) {
     int set = 0, r = m;
     while (r >= sz[set]) r -= sz[set++];
     int i, j, k;
@@ -88,14 +88,16 @@ __device__ inline void for_dirichlet(const Grid3& g, const DirSpec& d, Body body
 // Dirichlet values.  kind 0 (fine patch): nodes on the plate bottom take
 // T_bottom, the others the blend (1-w) I(Tc0) + w I(Tc1) of the trilinear
 // interpolants of two coarse fields.  kind 1 (coarse): k = 0 takes T_bottom,
-// the box nodes take the injected fine values `inj`.
+// the box nodes take the injected fine values `inj`; kind 2: the same values
+// read straight from the fine field (batched path).
 struct DirValues {
   int kind;
   double T_bottom, w;
   const double* Tc0;
   const double* Tc1;
   const double* inj;
-  Grid3 cg;
+  const double* Tf;  // kind 2: the fine field itself (injection fused into the solve)
+  Grid3 cg, fg;
   int oi, oj, ok, r;
 };
 
@@ -113,7 +115,7 @@ __device__ inline double trilinear_at(const double* Tc, const Grid3& cg, int gi,
 }
 
 __device__ inline double dir_value(const DirValues& dv, int i, int j, int k, long long n) {
-  if (dv.kind == 0) {
+  if (dv.kind == 0) {  // fine patch
     int gi = i + dv.oi * dv.r, gj = j + dv.oj * dv.r, gk = k + dv.ok * dv.r;
     if (gk == 0) return dv.T_bottom;
     double a = trilinear_at(dv.Tc0, dv.cg, gi, gj, gk, dv.r);
@@ -121,6 +123,8 @@ __device__ inline double dir_value(const DirValues& dv, int i, int j, int k, lon
     return (1.0 - dv.w) * a + dv.w * b;
   }
   if (k == 0) return dv.T_bottom;
+  if (dv.kind == 2)  // coarse node (i, j, k) of the injection box: the coinciding fine node
+    return __ldcg(dv.Tf + node_id(dv.fg, (i - dv.oi) * dv.r, (j - dv.oj) * dv.r, (k - dv.ok) * dv.r));
   return __ldcg(dv.inj + n);
 }
 
@@ -231,6 +235,18 @@ struct Tiling {
   int ntx, nty, ntz;  // tile counts
 };
 
+// Patch motion fused into a coarse predictor solve (batched path): the new
+// fine field dst takes src where the old and new patches overlap and the
+// trilinear interpolant of Tc elsewhere.
+struct MoveSpec {
+  int active;
+  const double* src;
+  double* dst;
+  const double* Tc;
+  Grid3 fg, cg;
+  int ooi, ooj, noi, noj, ok, r;
+};
+
 enum Precision : int { PREC_FP64 = 0, PREC_FP32_REFINED = 1 };
 
 // Everything one launch needs.  FP64 arrays serve the plain path, the
@@ -288,6 +304,7 @@ struct SolveArgs {
   int red_stride;
   DevStats* stats;
   unsigned long long* trace;  // [TRACE_CAP][2] (marker, globaltimer ns) of this solve, or NULL
+  MoveSpec mv;
 };
 
 // Phase markers recorded by block 0 when tracing.
@@ -299,9 +316,10 @@ constexpr int TRACE_CAP = 1024;
 
 struct Tracer {
   unsigned long long* buf;
+  int bid;
   int n = 0;
   __device__ void mark(int m) {
-    if (buf && blockIdx.x == 0 && threadIdx.x == 0 && n < TRACE_CAP - 1) {
+    if (buf && bid == 0 && threadIdx.x == 0 && n < TRACE_CAP - 1) {
       buf[2 * (n + 1)] = (unsigned long long)m;
       buf[2 * (n + 1) + 1] = global_ns();
       ++n;
@@ -461,10 +479,10 @@ __device__ inline void store_partial(R* prim, R* X, int nn, int n, int slot, R v
 // Grid-wide loop over node rows (j, k): each warp takes whole rows, its lanes
 // walk i, so the only division is one per row.  body(n, i, j, k, row_low_faces).
 template <class Body>
-__device__ inline void for_nodes(const Grid3& g, const Tiling& t, Body body) {
+__device__ inline void for_nodes(const Grid3& g, const Tiling& t, const VGrid& vg, Body body) {
   const int lane = threadIdx.x & 31;
-  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwg = (gridDim.x * blockDim.x) >> 5;
+  const int wg = (vg.bid * blockDim.x + threadIdx.x) >> 5;
+  const int nwg = (vg.nblk * blockDim.x) >> 5;
   const int rows = g.nny * g.nnz;
   for (int row = wg; row < rows; row += nwg) {
     const int k = row / g.nny, j = row - k * g.nny;
@@ -477,10 +495,10 @@ __device__ inline void for_nodes(const Grid3& g, const Tiling& t, Body body) {
 
 // Same for elements rows (je, ke): body(e, ie, je, ke).
 template <class Body>
-__device__ inline void for_elems(const Grid3& g, Body body) {
+__device__ inline void for_elems(const Grid3& g, const VGrid& vg, Body body) {
   const int lane = threadIdx.x & 31;
-  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwg = (gridDim.x * blockDim.x) >> 5;
+  const int wg = (vg.bid * blockDim.x + threadIdx.x) >> 5;
+  const int nwg = (vg.nblk * blockDim.x) >> 5;
   const int rows = g.ny * g.nz;
   for (int row = wg; row < rows; row += nwg) {
     const int ke = row / g.ny, je = row - ke * g.ny;
@@ -518,8 +536,8 @@ struct CGBufs {
 // <r, r> <= thresh or after max_iter iterations.  Returns 1 converged, 0
 // capped, -1 barrier failure; *iters gets the count.
 template <typename R>
-__device__ int pcg1(const SolveArgs& a, ApplySmem<R>& sm, const CGBufs<R>& c, R thresh, int max_iter, R* red,
-                    int* iters, Tracer& tr) {
+__device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const CGBufs<R>& c, R thresh,
+                    int max_iter, R* red, int* iters, Tracer& tr) {
   __shared__ R s_scal[3];
   const Grid3 g = a.g;
   const Tiling t = a.t;
@@ -548,8 +566,8 @@ __device__ int pcg1(const SolveArgs& a, ApplySmem<R>& sm, const CGBufs<R>& c, R 
     R* s_nxt = nxt ? c.s[1] : c.s[0];
     R* q_out = (k >= 0 && nxt) ? c.q[1] : c.q[0];
     R* X_out = (k >= 0 && nxt) ? c.X[1] : c.X[0];
-    R vg = R(0), vd = R(0), vr = R(0);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    R sg = R(0), vd = R(0), vr = R(0);
+    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
       auto load = [&](int n, int i, int j, int kk, bool owned) -> R {
         if (is_dir(g, a.dir, i, j, kk)) return R(0);
         const R dv = __ldcg(c.dinv + n);
@@ -557,7 +575,7 @@ __device__ int pcg1(const SolveArgs& a, ApplySmem<R>& sm, const CGBufs<R>& c, R 
         if (k < 0) {
           const R u = dv * rk;
           if (owned) {
-            vg = fma(rk, u, vg);
+            sg = fma(rk, u, sg);
             vr = fma(rk, rk, vr);
           }
           return u;
@@ -578,7 +596,7 @@ __device__ int pcg1(const SolveArgs& a, ApplySmem<R>& sm, const CGBufs<R>& c, R 
           s_nxt[n] = sv;
           r_nxt[n] = rn;
           c.x[n] = fma(alpha, pv, __ldcg(c.x + n));
-          vg = fma(rn, un, vg);
+          sg = fma(rn, un, sg);
           vr = fma(rn, rn, vr);
         }
         return un;
@@ -591,13 +609,13 @@ __device__ int pcg1(const SolveArgs& a, ApplySmem<R>& sm, const CGBufs<R>& c, R 
     }
     tr.mark(TR_CG_APPLY);
     {
-      R v[3] = {vg, vd, vr};
-      block_reduce_store<3>(v, red + RS_PQ * a.red_stride, a.red_stride);
+      R v[3] = {sg, vd, vr};
+      block_reduce_store<3>(v, red + RS_PQ * a.red_stride, a.red_stride, vg);
     }
-    if (!grid_sync(a.bar)) return -1;
+    if (!grid_sync(a.bar, vg)) return -1;
     tr.mark(TR_CG_PASS);
     R tot[3];
-    grid_total<3>(red + RS_PQ * a.red_stride, a.red_stride, tot);
+    grid_total<3>(red + RS_PQ * a.red_stride, a.red_stride, tot, vg);
     if (k >= 0) {
       ++it;
       if (tot[2] <= thresh) {
@@ -640,15 +658,14 @@ __device__ inline double elem_mean(const double* T, const Grid3& g, int ie, int 
   return s * 0.125;
 }
 
-// Internal linkage: every translation unit that launches the solve compiles its
-// own copy (the two-level path and the allocation-free single step).
-static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) {
+// One backward-Euler solve on the block range vg (all of it or one job's slice).
+__device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   __shared__ __align__(16) unsigned char smem_raw[sizeof(ApplySmem<double>)];
   __shared__ double s_Mhat[64], s_Khat[64];
   ApplySmem<double>& sm64 = *reinterpret_cast<ApplySmem<double>*>(smem_raw);
   ApplySmem<float>& sm32 = *reinterpret_cast<ApplySmem<float>*>(smem_raw);
   if (ld_volatile_i32(a.bar.status) != 0) return;  // an earlier solve failed: leave state untouched
-  Tracer tr{a.trace};
+  Tracer tr{a.trace, vg.bid};
   tr.mark(TR_START);
   const Grid3 g = a.g;
   const Tiling t = a.t;
@@ -657,15 +674,29 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
   const int S = g.nnx * g.nny;
   const int ntiles = t.ntx * t.nty * t.ntz;
   const bool refined = a.precision == PREC_FP32_REFINED;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gstride = gridDim.x * blockDim.x;
+  const int gtid = vg.bid * blockDim.x + threadIdx.x;
+  const int gstride = vg.nblk * blockDim.x;
   if (threadIdx.x < 64) {
     s_Mhat[threadIdx.x] = a.Mhat[threadIdx.x];
     s_Khat[threadIdx.x] = a.Khat[threadIdx.x];
   }
 
   // ---- phase 0: coefficients and eigenvalues, Dirichlet increments, load ---
-  for_elems(g, [&](int e, int ie, int je, int ke) {
+  if (a.mv.active) {  // fused patch motion; independent of this (coarse) solve's data
+    const MoveSpec& mv = a.mv;
+    const int fnn = mv.fg.nnx * mv.fg.nny * mv.fg.nnz;
+    for (int n = gtid; n < fnn; n += gstride) {
+      const int i = n % mv.fg.nnx, j = (n / mv.fg.nnx) % mv.fg.nny, k = n / (mv.fg.nnx * mv.fg.nny);
+      const int oi = i + (mv.noi - mv.ooi) * mv.r, oj = j + (mv.noj - mv.ooj) * mv.r;
+      double v;
+      if (oi >= 0 && oi <= mv.fg.nx && oj >= 0 && oj <= mv.fg.ny)
+        v = __ldcg(mv.src + node_id(mv.fg, oi, oj, k));
+      else
+        v = trilinear_at(mv.Tc, mv.cg, i + mv.noi * mv.r, j + mv.noj * mv.r, k + mv.ok * mv.r, mv.r);
+      mv.dst[n] = v;
+    }
+  }
+  for_elems(g, vg, [&](int e, int ie, int je, int ke) {
     const double Tb = elem_mean(a.T_in, g, ie, je, ke);
     const uint8_t st = a.state[(ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox];
     const double rc = a.mat.rho * (a.mat.c0 + a.mat.c1 * (Tb - a.mat.Tref));
@@ -678,22 +709,29 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
 #pragma unroll
     for (int m = 1; m < 8; ++m) a.lam[m * ne + e] = se * a.Mc[m] + k * a.Kc[m];
     if (refined) {
+      const float sf = (float)se, kf = (float)k;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) a.lam32[m * ne + e] = (float)(se * a.Mc[m] + k * a.Kc[m]);
+      for (int m = 0; m < 8; ++m) a.lam32[m * ne + e] = fmaf(sf, (float)a.Mc[m], kf * (float)a.Kc[m]);
     }
   });
   // increments: 0 on free nodes, g - T^k on Dirichlet nodes (disjoint writes)
-  for_nodes(g, t, [&](int n, int i, int j, int k, bool, bool) {
+  for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool, bool) {
     if (!is_dir(g, a.dir, i, j, k)) a.u[n] = 0.0;
   });
-  for_dirichlet(g, a.dir, [&](int n, int i, int j, int k) {
+  for_dirichlet(g, a.dir, vg, [&](int n, int i, int j, int k) {
     a.u[n] = dir_value(a.dv, i, j, k, n) - __ldcg(a.T_in + n);
   });
   {
+    // one table entry per block first (thread 0, then 32, ...): the erf / exp
+    // chains run on many SMs at once instead of in one block
     const int nf = load_factors(a.ld), w = g.nnx + g.nny;
-    for (int m = gtid; m < nf * w; m += gstride) a.G[m] = load_factor(a.ld, g, m / w, m % w);
+    const int lanes = (blockDim.x + 31) / 32;
+    const int slot = (threadIdx.x % 32 == 0) ? threadIdx.x / 32 : -1;
+    if (slot >= 0)
+      for (int m = vg.bid + vg.nblk * slot; m < nf * w; m += vg.nblk * lanes)
+        a.G[m] = load_factor(a.ld, g, m / w, m % w);
   }
-  if (!grid_sync(a.bar)) return;
+  if (!grid_sync(a.bar, vg)) return;
   tr.mark(TR_PHASE0);
 
   // ---- phase 1: Jacobi diagonal and right-hand side partials --------------
@@ -701,7 +739,7 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
     int j = n / g.nnx, i = n - j * g.nnx;
     a.F[n] = top_load_tab(a.ld, g, a.G, i, j);
   }
-  for_nodes(g, t, [&](int n, int i, int j, int k, bool, bool) {
+  for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool, bool) {
     double di = 0.0;
     if (!is_dir(g, a.dir, i, j, k)) {
       double d = 0.0;
@@ -734,16 +772,16 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
     auto load_T = [&](int n, int, int, int, bool) -> double { return __ldcg(a.T_in + n); };
     auto emit1 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
     auto emit2 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, true); };
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
       apply_tile<double>(g, t, tile, sm64, load_u, lam_full, emit1);
       apply_tile<double>(g, t, tile, sm64, load_T, lam_k, emit2);
     }
   }
-  if (!grid_sync(a.bar)) return;
+  if (!grid_sync(a.bar, vg)) return;
   tr.mark(TR_RHS);
   {
     double v[2] = {0.0, 0.0};
-    for_nodes(g, t, [&](int n, int i, int j, int k, bool ly, bool lz) {
+    for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool ly, bool lz) {
       double rr = 0.0;
       if (!is_dir(g, a.dir, i, j, k)) {
         double Fn = (k == g.nz) ? __ldcg(a.F + (n - S * g.nz)) : 0.0;
@@ -753,12 +791,12 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
       v[0] += rr * rr * __ldcg(a.dinv + n);
       v[1] += rr * rr;
     });
-    block_reduce_store<2>(v, a.red + RS_RZ0 * a.red_stride, a.red_stride);
+    block_reduce_store<2>(v, a.red + RS_RZ0 * a.red_stride, a.red_stride, vg);
   }
-  if (!grid_sync(a.bar)) return;
+  if (!grid_sync(a.bar, vg)) return;
   tr.mark(TR_RESID);
   double tot0[2];
-  grid_total<2>(a.red + RS_RZ0 * a.red_stride, a.red_stride, tot0);
+  grid_total<2>(a.red + RS_RZ0 * a.red_stride, a.red_stride, tot0, vg);
   const double bb = tot0[1];
   const double thresh = a.tol * a.tol * bb;
 
@@ -767,7 +805,7 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
   bool conv = !(bb > 0.0) || (a.tol >= 1.0);
   if (!conv && !refined) {
     CGBufs<double> c{a.u, {a.r, a.r2}, {a.p0, a.p1}, {a.s0, a.s1}, {a.q, a.q2}, {a.X, a.X2}, a.dinv, a.lam};
-    int res = pcg1<double>(a, sm64, c, thresh, a.max_iter, a.red, &it, tr);
+    int res = pcg1<double>(a, vg, sm64, c, thresh, a.max_iter, a.red, &it, tr);
     if (res < 0) return;
     conv = res == 1;
   }
@@ -776,24 +814,24 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
   while (!conv && refined && outer < a.max_outer) {
     {
       float v[2] = {0.0f, 0.0f};
-      for_nodes(g, t, [&](int n, int, int, int, bool, bool) {
+      for_nodes(g, t, vg, [&](int n, int, int, int, bool, bool) {
         float rf = (float)__ldcg(a.r + n);
         a.r32[n] = rf;
         a.d32[n] = 0.0f;
         v[0] = fmaf(rf * rf, __ldcg(a.dinv32 + n), v[0]);
         v[1] = fmaf(rf, rf, v[1]);
       });
-      block_reduce_store<2>(v, a.red32 + RS_RZ0 * a.red_stride, a.red_stride);
+      block_reduce_store<2>(v, a.red32 + RS_RZ0 * a.red_stride, a.red_stride, vg);
     }
-    if (!grid_sync(a.bar)) return;
+    if (!grid_sync(a.bar, vg)) return;
     tr.mark(TR_OUTER_INIT);
     float t32[2];
-    grid_total<2>(a.red32 + RS_RZ0 * a.red_stride, a.red_stride, t32);
+    grid_total<2>(a.red32 + RS_RZ0 * a.red_stride, a.red_stride, t32, vg);
     int inner = 0;
     CGBufs<float> c{a.d32, {a.r32, a.r32b}, {a.p0f, a.p1f}, {a.s0f, a.s1f}, {a.q32, a.q32b}, {a.X32, a.X32b},
                     a.dinv32, a.lam32};
     const float ti = (float)a.tol_inner;
-    int res = pcg1<float>(a, sm32, c, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+    int res = pcg1<float>(a, vg, sm32, c, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
     if (res < 0) return;
     it += inner;
     ++outer;
@@ -804,12 +842,12 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
     };
     auto load_d = [&](int n, int, int, int, bool) -> double { return (double)__ldcg(a.d32 + n); };
     auto emit = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk)
       apply_tile<double>(g, t, tile, sm64, load_d, lam_full, emit);
-    if (!grid_sync(a.bar)) return;
+    if (!grid_sync(a.bar, vg)) return;
     tr.mark(TR_OUTER_APPLY);
     double v[1] = {0.0};
-    for_nodes(g, t, [&](int n, int i, int j, int k, bool ly, bool lz) {
+    for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool ly, bool lz) {
       if (is_dir(g, a.dir, i, j, k)) return;
       double y = gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
       double rn = __ldcg(a.r + n) - y;
@@ -817,16 +855,16 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
       a.u[n] = __ldcg(a.u + n) + (double)__ldcg(a.d32 + n);
       v[0] += rn * rn;
     });
-    block_reduce_store<1>(v, a.red + RS_RR * a.red_stride, a.red_stride);
-    if (!grid_sync(a.bar)) return;
+    block_reduce_store<1>(v, a.red + RS_RR * a.red_stride, a.red_stride, vg);
+    if (!grid_sync(a.bar, vg)) return;
     double trr[1];
-    grid_total<1>(a.red + RS_RR * a.red_stride, a.red_stride, trr);
+    grid_total<1>(a.red + RS_RR * a.red_stride, a.red_stride, trr, vg);
     tr.mark(TR_OUTER_END);
     conv = trr[0] <= thresh;
   }
   const int lvl = a.level;
   if (!conv) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (vg.bid == 0 && threadIdx.x == 0) {
       atomicCAS(a.bar.status, 0, (int)ST_NOCONV);
       a.stats->iters[lvl] += it;
       a.stats->outer[lvl] += outer;
@@ -839,9 +877,9 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
   tr.mark(TR_UPDATE);
   for (int n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
   if (a.update_state || a.energy) {
-    if (!grid_sync(a.bar)) return;
+    if (!grid_sync(a.bar, vg)) return;
     double v[3] = {0.0, 0.0, 0.0};
-    for_elems(g, [&](int e, int ie, int je, int ke) {
+    for_elems(g, vg, [&](int e, int ie, int je, int ke) {
       if (a.update_state) {
         const double Tb = elem_mean(a.T_out, g, ie, je, ke);
         uint8_t* sp = a.state + (ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox;
@@ -865,7 +903,7 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
     });
     if (a.energy) {
       for (int n = gtid; n < S; n += gstride) v[1] += a.dt * __ldcg(a.F + n);
-      for_dirichlet(g, a.dir, [&](int n, int i, int j, int k) {
+      for_dirichlet(g, a.dir, vg, [&](int n, int i, int j, int k) {
         // reaction of a Dirichlet row: (S u + K T^{k+1})_n - F_n
         double R_n = 0.0;
         for (int dz = -1; dz <= 0; ++dz)
@@ -888,11 +926,11 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
         v[2] += a.dt * R_n;
       });
     }
-    block_reduce_store<3>(v, a.red + RS_ES * a.red_stride, a.red_stride);
-    if (!grid_sync(a.bar)) return;
-    if (blockIdx.x == 0) {
+    block_reduce_store<3>(v, a.red + RS_ES * a.red_stride, a.red_stride, vg);
+    if (!grid_sync(a.bar, vg)) return;
+    if (vg.bid == 0) {
       double te[3];
-      grid_total<3>(a.red + RS_ES * a.red_stride, a.red_stride, te);
+      grid_total<3>(a.red + RS_ES * a.red_stride, a.red_stride, te, vg);
       if (threadIdx.x == 0 && a.energy) {
         a.stats->e_stored[lvl] += te[0];
         a.stats->e_laser[lvl] += te[1];
@@ -901,13 +939,55 @@ static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) 
     }
   }
   tr.mark(TR_END);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (vg.bid == 0 && threadIdx.x == 0) {
     a.stats->iters[lvl] += it;
     a.stats->outer[lvl] += outer;
     a.stats->solves[lvl] += 1;
     a.stats->last_iters[lvl] = it;
     if (it > a.stats->max_iters[lvl]) a.stats->max_iters[lvl] = it;
   }
+}
+
+
+// Internal linkage: every translation unit that launches the solve compiles its
+// own copy (the two-level path and the allocation-free single step).
+static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) {
+  solve_body(a, VGrid{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// A batch of independent solves in one cooperative launch: job j runs on the
+// blocks [first[j], first[j+1]) with its own barrier words, reduction slots
+// and buffers, so jobs never wait for each other.  The job's arguments are
+// copied to shared memory once per block.
+constexpr int BATCH_MAX = 512;
+struct BatchTable {
+  int njobs;
+  int first[BATCH_MAX + 1];
+};
+
+static __global__ void __launch_bounds__(NT, 2) solve_batch_kernel(const BatchTable* __restrict__ tab,
+                                                                  const SolveArgs* __restrict__ jobs) {
+  __shared__ SolveArgs s_args;
+  __shared__ int s_job;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = tab->njobs - 1;
+    while (lo < hi) {  // last job whose first block <= blockIdx.x
+      const int mid = (lo + hi + 1) / 2;
+      if (tab->first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_job = lo;
+  }
+  __syncthreads();
+  const int j = s_job;
+  const int b0 = tab->first[j], nb = tab->first[j + 1] - b0;
+  if ((int)blockIdx.x >= tab->first[tab->njobs] || nb <= 0) return;  // block not assigned this round
+  {
+    const int* src = reinterpret_cast<const int*>(jobs + j);
+    int* dst = reinterpret_cast<int*>(&s_args);
+    for (int w = threadIdx.x; w < (int)(sizeof(SolveArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  solve_body(s_args, VGrid{(int)blockIdx.x - b0, nb});
 }
 
 // ---------------------------------------------------------------------------

@@ -89,6 +89,7 @@ EXPORTS = [
     "tl_create_problem", "tl_coarse_step", "tl_fine_substeps", "tl_restrict", "tl_macro_steps",
     "tl_sync", "tl_node_count", "tl_get_temperature", "tl_get_state", "tl_get_stats",
     "tl_destroy_problem", "tl_status_string", "tl_box_step_noalloc", "tl_trace_last_solve",
+    "tl_batch_create", "tl_batch_add", "tl_batch_round", "tl_batch_poll", "tl_batch_info", "tl_batch_destroy",
 ]
 
 _lib = None
@@ -132,6 +133,18 @@ def load(path=LIB_PATH):
     lib.tl_box_step_noalloc.restype = C.c_int
     lib.tl_trace_last_solve.argtypes = [P, C.c_int, C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_size_t)]
     lib.tl_trace_last_solve.restype = C.c_int
+    lib.tl_batch_create.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(P)]
+    lib.tl_batch_create.restype = C.c_int
+    lib.tl_batch_add.argtypes = [P, P, C.c_int, C.POINTER(C.c_int)]
+    lib.tl_batch_add.restype = C.c_int
+    lib.tl_batch_round.argtypes = [P, C.POINTER(C.c_int)]
+    lib.tl_batch_round.restype = C.c_int
+    lib.tl_batch_poll.argtypes = [P, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
+    lib.tl_batch_poll.restype = C.c_int
+    lib.tl_batch_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+    lib.tl_batch_info.restype = C.c_int
+    lib.tl_batch_destroy.argtypes = [P]
+    lib.tl_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -304,6 +317,60 @@ class Problem:
     def close(self):
         if self.h:
             tl_destroy_problem(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many problems advanced together by one persistent kernel per launch
+    (see include/tl.h, batched jobs)."""
+
+    def __init__(self, launches_per_round=10, max_jobs=256, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.tl_batch_create(C.c_void_p(stream), int(launches_per_round), int(max_jobs), C.byref(h)),
+               "tl_batch_create")
+        self.h = h
+        self.jobs = {}
+
+    def add(self, prob, macro_steps):
+        jid = C.c_int()
+        _check(load().tl_batch_add(self.h, prob.h, int(macro_steps), C.byref(jid)), "tl_batch_add")
+        self.jobs[jid.value] = prob
+        return jid.value
+
+    def round(self):
+        act = C.c_int()
+        _check(load().tl_batch_round(self.h, C.byref(act)), "tl_batch_round")
+        return act.value
+
+    def poll(self, cap=512):
+        ids = (C.c_int * cap)()
+        n = C.c_int()
+        _check(load().tl_batch_poll(self.h, ids, cap, C.byref(n)), "tl_batch_poll")
+        return [self.jobs.pop(ids[i]) for i in range(n.value)]
+
+    def info(self):
+        a, l, g = C.c_int(), C.c_longlong(), C.c_int()
+        _check(load().tl_batch_info(self.h, C.byref(a), C.byref(l), C.byref(g)), "tl_batch_info")
+        return {"active": a.value, "launches": l.value, "graph_mode": g.value}
+
+    def run(self):
+        """Rounds until every job finished; returns the problems in finishing order."""
+        done = []
+        while self.jobs:
+            self.round()
+            done += self.poll()
+        return done
+
+    def close(self):
+        if self.h:
+            load().tl_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
