@@ -190,17 +190,16 @@ tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* hos
                               size_t* n_out);
 
 /* ---- Batched jobs (many independent problems in one persistent kernel) ---
- * A batch advances several problems together.  Each round is
- * launches_per_round cooperative launches of one persistent kernel; in every
- * launch each active problem performs the next solve of its own Algorithm 1
- * sequence (predictor with the patch motion fused in, one fine micro step, or
- * corrector with the restriction fused into its boundary data) on its own
- * slice of the grid: slices are sized in proportion to the solves' element
- * counts, and each problem keeps its own buffers, barrier words and
- * reductions, so problems never wait for each other and results match the
- * problem run alone up to rounding (the slice changes the summation order).
- * The launches of a round are captured once as a CUDA graph and replayed;
- * the per-launch job tables are refreshed from pinned host memory each round.
+ * A batch advances several problems together.  Each round is one cooperative
+ * launch of one persistent kernel in which every active problem performs the
+ * next launches_per_round solves of its own Algorithm 1 sequence (predictor
+ * with the patch motion fused in, fine micro steps, corrector with the
+ * restriction fused into its boundary data) back to back on its own slice of
+ * the grid: slices are sized in proportion to the round's element counts,
+ * and each problem keeps its own buffers, barrier words and reductions, so
+ * problems meet only at the end of a round and results match the problem run
+ * alone up to rounding (the slice changes the summation order).  The job
+ * table of a round is built on the host and copied from pinned memory.
  * Problems join and leave only between macro steps; while in a batch their
  * work runs on the batch's stream.  The paper has no batching; it remarks that
  * the method is embarrassingly parallel (Section 5.3). */
@@ -223,8 +222,8 @@ tl_status tl_batch_round(tl_batch* b, int* active_out);
  * finished their macro steps; their problems return to their own streams. */
 tl_status tl_batch_poll(tl_batch* b, int* ids, int cap, int* n_out);
 
-/* Active jobs, launches so far, graph mode (1 replayed graph, -1 direct
- * launches because capture was unavailable, 0 no round yet). */
+/* Active jobs, launches (rounds) so far, graph mode (always 0: a round is a
+ * single launch). */
 tl_status tl_batch_info(const tl_batch* b, int* active, long long* launches, int* graph_mode);
 
 void tl_batch_destroy(tl_batch* b);

@@ -161,7 +161,7 @@ void choose_tiling(Level& L, int nsm, int per_sm) {
   const Grid3& g = L.g;
   double best = 1e300;
   Tiling bt{};
-  const int exs[] = {32, 16, 8};
+  const int exs[] = {16, 8};
   const int eys[] = {8, 4, 2, 1};
   for (int ex0 : exs)
     for (int ey0 : eys)
@@ -174,7 +174,7 @@ void choose_tiling(Level& L, int nsm, int per_sm) {
         const double per_tile = (double)ex * ey * ez * ops + 1500.0 * (ez + 1);
         const long long G = std::min<long long>(T, (long long)nsm * per_sm);
         const long long b = (G + nsm - 1) / nsm, tb = (T + G - 1) / G;
-        const double eff = b >= 2 ? 0.8 : 0.5;
+        const double eff = b >= 4 ? 0.85 : (b >= 2 ? 0.7 : 0.4);
         const double cost = (double)(b * tb) * per_tile / eff;
         if (cost < best * (1 - 1e-9)) {
           best = cost;
@@ -611,7 +611,7 @@ struct tl_batch {
   BatchTable* h_tab = nullptr; // pinned staging of the same
   SolveArgs* h_args = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int graph_state = 0;         // 0 not tried, 1 in use, -1 capture unavailable (direct launches)
+  int graph_state = 0;         // rounds are single launches; no graph
   long long launches = 0, rounds = 0;
 };
 
@@ -923,7 +923,7 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
   }
   b->max_coop = per_sm * b->nsm;
   b->cap = std::min(max_jobs, b->max_coop);
-  const size_t targs = (size_t)b->R * b->cap * sizeof(SolveArgs), ttab = (size_t)b->R * sizeof(BatchTable);
+  const size_t targs = (size_t)b->R * b->cap * sizeof(SolveArgs), ttab = sizeof(BatchTable);
   e = cudaMalloc(&b->d_tab, ttab);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_args, targs);
   if (e == cudaSuccess) e = cudaHostAlloc(&b->h_tab, ttab, cudaHostAllocDefault);
@@ -951,14 +951,10 @@ tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out)
     if (j.active && j.p == p) return TL_EINVAL;
   cudaError_t e = cudaStreamSynchronize(p->stream);  // the problem's own pending work first
   if (e != cudaSuccess) return cuda_status(e);
-  // tiling for a slice of the grid: about two tiles per block of a job's share
-  const int share = std::max(1, b->max_coop / std::max(1, b->cap));
-  choose_tiling(p->C, std::max(1, share / 2), 2);
+  // the whole-grid tiling: a job that runs (almost) alone in its launch can
+  // then spread over most of the grid; crowded launches loop over tiles
   p->C.tb = p->C.t;
-  choose_tiling(p->Fi, std::max(1, share / 2), 2);
   p->Fi.tb = p->Fi.t;
-  choose_tiling(p->C, p->nsm, p->max_coop / std::max(1, p->nsm));  // restore the whole-grid tiling
-  choose_tiling(p->Fi, p->nsm, p->max_coop / std::max(1, p->nsm));
   tl_batch::Job job{p, (long long)p->n + macro_steps, p->stream, true};
   p->stream = b->stream;
   int id = -1;
@@ -1018,75 +1014,72 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
   if (!b) return TL_EINVAL;
   cudaError_t e = cudaStreamSynchronize(b->stream);  // staging buffers free again
   if (e != cudaSuccess) return cuda_status(e);
-  int active = 0;
-  for (int k = 0; k < b->R; ++k) {
-    BatchTable& tab = b->h_tab[k];
-    SolveArgs* args = b->h_args + (size_t)k * b->cap;
-    std::vector<long long> w;
-    std::vector<int> capb;
-    int nj = 0;
-    for (size_t id = 0; id < b->jobs.size(); ++id) {
+  BatchTable& tab = *b->h_tab;
+  std::vector<long long> w;
+  std::vector<int> capb;
+  int nj = 0;
+  for (size_t id = 0; id < b->jobs.size(); ++id) {
+    auto& j = b->jobs[id];
+    if (!j.active) continue;
+    if (j.p->n >= j.target && j.p->phase == NEED_PREDICT) {
+      j.active = false;
+      b->finished.push_back((int)id);
+      continue;
+    }
+    // the job's next R solves (fewer if it reaches its target first)
+    SolveArgs* args = b->h_args + (size_t)nj * b->R;
+    long long work = 0;
+    int ns = 0, cap_tiles = 1 << 30;
+    while (ns < b->R && !(j.p->n >= j.target && j.p->phase == NEED_PREDICT)) {
+      long long wt = 0;
+      next_batched_solve(j.p, args[ns], &wt);
+      const Tiling& t = args[ns].t;
+      cap_tiles = std::min(cap_tiles, t.ntx * t.nty * t.ntz);
+      work += wt;
+      j.p->launches++;
+      ++ns;
+    }
+    tab.nsolves[nj] = ns;
+    capb.push_back(j.p->red_stride);
+    w.push_back(work);
+    ++nj;
+  }
+  if (active_out) *active_out = nj;
+  std::vector<int> nb;
+  allocate_blocks(w, capb, b->max_coop, nb);
+  // tile each solve for the slice it got: few large tiles in a crowded round,
+  // many in a sparse one (tiling only sets how the slice walks the mesh)
+  {
+    int q = 0;
+    for (size_t id = 0; id < b->jobs.size() && q < nj; ++id) {
       auto& j = b->jobs[id];
       if (!j.active) continue;
-      if (j.p->n >= j.target && j.p->phase == NEED_PREDICT) {
-        j.active = false;
-        b->finished.push_back((int)id);
-        continue;
-      }
-      long long wt = 0;
-      next_batched_solve(j.p, args[nj], &wt);
-      const Tiling& t = args[nj].t;
-      capb.push_back(std::min(j.p->red_stride, t.ntx * t.nty * t.ntz));
-      w.push_back(wt);
-      j.p->launches++;
-      ++nj;
+      Level tmpc = j.p->C, tmpf = j.p->Fi;
+      choose_tiling(tmpc, nb[q], 1);
+      choose_tiling(tmpf, nb[q], 1);
+      SolveArgs* args = b->h_args + (size_t)q * b->R;
+      for (int sv = 0; sv < tab.nsolves[q]; ++sv)
+        args[sv].t = (args[sv].level == 1) ? tmpf.t : tmpc.t;
+      ++q;
     }
-    if (k == 0) active = nj;
-    std::vector<int> nb;
-    allocate_blocks(w, capb, b->max_coop, nb);
-    tab.njobs = nj;
-    tab.first[0] = 0;
-    for (int q = 0; q < nj; ++q) tab.first[q + 1] = tab.first[q] + nb[q];
   }
-  if (active_out) *active_out = active;
-  e = cudaMemcpyAsync(b->d_tab, b->h_tab, (size_t)b->R * sizeof(BatchTable), cudaMemcpyHostToDevice, b->stream);
+  tab.njobs = nj;
+  tab.per_job = b->R;
+  tab.first[0] = 0;
+  for (int q = 0; q < nj; ++q) tab.first[q + 1] = tab.first[q] + nb[q];
+  if (nj == 0) return TL_OK;
+  e = cudaMemcpyAsync(b->d_tab, b->h_tab, sizeof(BatchTable), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_args, b->h_args, (size_t)b->R * b->cap * sizeof(SolveArgs), cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(b->d_args, b->h_args, (size_t)nj * b->R * sizeof(SolveArgs), cudaMemcpyHostToDevice,
                         b->stream);
   if (e != cudaSuccess) return cuda_status(e);
-  auto launch_all = [&]() -> cudaError_t {
-    for (int k = 0; k < b->R; ++k) {
-      const BatchTable* tp = b->d_tab + k;
-      const SolveArgs* ap = b->d_args + (size_t)k * b->cap;
-      void* kargs[] = {(void*)&tp, (void*)&ap};
-      cudaError_t le = cudaLaunchCooperativeKernel((const void*)solve_batch_kernel, dim3(b->max_coop), dim3(NT),
-                                                   kargs, 0, b->stream);
-      if (le != cudaSuccess) return le;
-    }
-    return cudaSuccess;
-  };
-  if (b->graph_state == 0) {  // capture the round once; replay it every round
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t le = launch_all();
-      e = cudaStreamEndCapture(b->stream, &graph);
-      if (le == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
-      else if (e == cudaSuccess) e = le;
-    }
-    if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      if (b->exec) cudaGraphExecDestroy(b->exec);
-      b->exec = nullptr;
-      b->graph_state = -1;
-    } else {
-      b->graph_state = 1;
-    }
-  }
-  e = b->graph_state == 1 ? cudaGraphLaunch(b->exec, b->stream) : launch_all();
+  const BatchTable* tp = b->d_tab;
+  const SolveArgs* ap = b->d_args;
+  void* kargs[] = {(void*)&tp, (void*)&ap};
+  e = cudaLaunchCooperativeKernel((const void*)solve_batch_kernel, dim3(tab.first[nj]), dim3(NT), kargs, 0,
+                                  b->stream);
   if (e != cudaSuccess) return cuda_status(e);
-  b->launches += b->R;
+  b->launches++;
   b->rounds++;
   return TL_OK;
 }

@@ -24,7 +24,7 @@ using namespace tl;
 namespace {
 
 constexpr size_t kMaxNodes = TL_NOALLOC_MAX_NODES;
-constexpr int kMaxGrid = 512;        // cooperative grid cap (2 blocks per SM on up to 256 SMs)
+constexpr int kMaxGrid = 1024;       // cooperative grid cap (4 blocks per SM on up to 256 SMs)
 constexpr size_t kAlign = 256;
 constexpr int kMaxDevices = 64;
 

@@ -26,10 +26,11 @@
 
 namespace tl {
 
-constexpr int TXE = 32;               // max tile width in elements (x)
+constexpr int TXE = 16;               // max tile width in elements (x)
 constexpr int TYE = 8;                // max tile depth in elements (y)
 constexpr int WX = TXE + 1, WY = TYE + 1;
-constexpr int NT = 320;               // threads per block: one window column each
+constexpr int NT = 160;               // threads per block: one window column each
+constexpr int MIN_BLOCKS = 4;         // resident blocks per SM the register budget targets
 static_assert(NT >= WX * WY, "a block must cover a tile's window columns");
 constexpr int MAXRECT = 8;
 constexpr int NXB = 7;                // exchange buffers
@@ -377,6 +378,10 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
   __syncthreads();
   for (int ke = ke0; ke < ke1; ++ke) {
     const int nxt = cur ^ 1;
+    // eigenvalues of this layer's element: issued now, used in stage 3, so
+    // their latency overlaps the input loads of stage 1
+    R l8[8];
+    if (has_e) lam(welem + ke * Se, l8);
     // stage 1: next layer, z-direction Hadamard per window column
     if (has_w) {
       R hi = load(wnode + (ke + 1) * S, wi, wj, ke + 1, wslot == 0 && (ke + 1 < ke1 || z_top_owned));
@@ -398,8 +403,6 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
     __syncthreads();
     // stage 3: per element, x-direction, eigenvalue scaling, x-backward
     if (has_e) {
-      R l8[8];
-      lam(welem + ke * Se, l8);
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) {
         R a = sm.Y[m4][ely][elx], b = sm.Y[m4][ely][elx + 1];
@@ -951,21 +954,24 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
 
 // Internal linkage: every translation unit that launches the solve compiles its
 // own copy (the two-level path and the allocation-free single step).
-static __global__ void __launch_bounds__(NT, 2) solve_kernel(const SolveArgs a) {
+static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_kernel(const SolveArgs a) {
   solve_body(a, VGrid{(int)blockIdx.x, (int)gridDim.x});
 }
 
-// A batch of independent solves in one cooperative launch: job j runs on the
-// blocks [first[j], first[j+1]) with its own barrier words, reduction slots
-// and buffers, so jobs never wait for each other.  The job's arguments are
+// A batch of independent jobs in one cooperative launch: job j runs on the
+// blocks [first[j], first[j+1]) and performs its next nsolves[j] solves back
+// to back (job-local grid barrier in between), each with its own barrier
+// words, reduction slots and buffers, so jobs meet only at the launch's end.
+// The arguments of job j's s-th solve are jobs[j * per_job + s]; each is
 // copied to shared memory once per block.
 constexpr int BATCH_MAX = 512;
 struct BatchTable {
-  int njobs;
+  int njobs, per_job;
   int first[BATCH_MAX + 1];
+  int nsolves[BATCH_MAX];
 };
 
-static __global__ void __launch_bounds__(NT, 2) solve_batch_kernel(const BatchTable* __restrict__ tab,
+static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_batch_kernel(const BatchTable* __restrict__ tab,
                                                                   const SolveArgs* __restrict__ jobs) {
   __shared__ SolveArgs s_args;
   __shared__ int s_job;
@@ -979,15 +985,23 @@ static __global__ void __launch_bounds__(NT, 2) solve_batch_kernel(const BatchTa
   }
   __syncthreads();
   const int j = s_job;
+  if (tab->njobs <= 0 || (int)blockIdx.x >= tab->first[tab->njobs]) return;  // block not assigned
   const int b0 = tab->first[j], nb = tab->first[j + 1] - b0;
-  if ((int)blockIdx.x >= tab->first[tab->njobs] || nb <= 0) return;  // block not assigned this round
-  {
-    const int* src = reinterpret_cast<const int*>(jobs + j);
+  if (nb <= 0) return;
+  const VGrid vg{(int)blockIdx.x - b0, nb};
+  const int ns = tab->nsolves[j];
+  for (int sv = 0; sv < ns; ++sv) {
+    const int* src = reinterpret_cast<const int*>(jobs + (size_t)j * tab->per_job + sv);
     int* dst = reinterpret_cast<int*>(&s_args);
+    __syncthreads();  // the previous solve is done with s_args
     for (int w = threadIdx.x; w < (int)(sizeof(SolveArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    solve_body(s_args, vg);
+    if (sv + 1 < ns) {
+      if (!grid_sync(s_args.bar, vg)) return;  // the next solve reads this one's results
+      if (ld_volatile_i32(s_args.bar.status) != 0) return;
+    }
   }
-  __syncthreads();
-  solve_body(s_args, VGrid{(int)blockIdx.x - b0, nb});
 }
 
 // ---------------------------------------------------------------------------
