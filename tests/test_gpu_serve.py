@@ -1,0 +1,61 @@
+"""Continuous batching: jobs that arrive while others run are admitted as
+slots and memory free up; each result equals the job run alone (within the
+parity tolerance of its precision)."""
+import numpy as np
+import pytest
+
+from paper_2110_12932_gb300 import build as tlbuild
+from paper_2110_12932_gb300 import serve, tl, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    tlbuild.build()
+    return tl.load()
+
+
+def _jobs():
+    base = workloads.workload("single_track_tiny")
+    jobs = [
+        dict(base, macro_steps=12),
+        dict(base, macro_steps=7, P=150.0, pNXc=9, pNYc=3, pNZc=2, r=4, m=2),
+        dict(base, macro_steps=9, precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5),
+        dict(base, macro_steps=5, tracks=[(0.2e-3, 0.3e-3, 1.8e-3, 0.3e-3, 1.2)]),
+        dict(base, macro_steps=10, NXc=13, NYc=7, NZc=5, Lx=13 * 125e-6, Ly=7 * 125e-6, Lz=5 * 125e-6,
+             pNXc=5, pNYc=3, pNZc=3, r=3, m=3, tracks=[(0.0, 0.45e-3, 13 * 125e-6, 0.45e-3, 0.8)]),
+    ]
+    return jobs
+
+
+def test_results_same_alone_and_in_the_mix():
+    jobs = _jobs()
+    alone = []
+    for cfg in jobs:
+        p = tl.Problem(cfg)
+        p.macro_steps(cfg["macro_steps"])
+        alone.append(p.temperature(tl.TL_FINE)[0])
+        p.close()
+    arrivals = [(0.0, jobs[0]), (0.0, jobs[1]), (0.005, jobs[2]), (0.01, jobs[3]), (0.02, jobs[4])]
+    # room for two resident jobs at a time: the later ones wait for a slot
+    cap = 2.2 * max(serve.job_bytes(c) for c in jobs)
+    got = {}
+    srv = serve.Server(mem_cap_bytes=cap, max_jobs=2, launches_per_round=4)
+    rep = srv.run(arrivals, on_done=lambda k, p, rec: got.__setitem__(k, p.temperature(tl.TL_FINE)[0]))
+    srv.close()
+    assert rep["jobs"] == len(jobs) and rep["all_ok"]
+    assert rep["peak_admitted_bytes"] <= cap
+    waited = [d for d in rep["done"] if d["admitted"] > d["arrival"] + 1e-3]
+    assert waited, "some job must have waited for a slot"
+    for k, cfg in enumerate(jobs):
+        tol = 1e-6 if cfg.get("precision", 0) == tl.TL_FP32_REFINED else 1e-9
+        rel = np.linalg.norm(got[k] - alone[k]) / np.linalg.norm(alone[k])
+        assert rel <= tol, (k, rel)
+    assert rep["job_latency_s"]["p99"] >= rep["job_latency_s"]["p50"] > 0
+    assert rep["coarse_step_latency_ms"]["p50"] > 0
+
+
+def test_fifo_reference_latencies():
+    lat = serve.fifo_one_at_a_time([(0.0, None), (0.5, None), (0.6, None)], [1.0, 1.0, 1.0])
+    assert lat == [1.0, 1.5, 2.4]
