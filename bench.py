@@ -33,6 +33,10 @@ WORKLOAD = "multitrack_10mm"
 METRIC = "fine DOF-substeps/s"
 FLOPS_APPLY_PER_ELEM = 65   # Hadamard-factored matrix-free apply, FP64 flops per element
 FLOPS_VEC_PER_NODE = 14     # PCG vector update, fused dots, p = z + beta p
+# dram__bytes_read.sum + dram__bytes_write.sum of one FP64 fine micro-step launch of
+# this workload, from the ncu capture summarised in
+# profiles/solve_kernel_fp64_multitrack_10mm.md (the patch is L2-resident)
+FINE_LAUNCH_DRAM_BYTES = 4.737024e6 + 2.491904e6
 
 
 def parse():
@@ -43,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "roofline"],
                     help="plain: the 10 mm multi-track plate (FP64 headline + precision form); "
                          "batch: 64 uneven jobs in the batched FP32-refined form")
     ap.add_argument("--jobs", type=int, default=64)
@@ -294,7 +298,7 @@ def run_ours(args):
     achieved = fine_flops(cfg, fine_iters) / launch_s / 1e12
     peak = 152 * 4 * 2.07e9 / 1e12   # FP64 FMA: 2 DFMA/clk/SM = 4 flop/clk/SM at 2.07 GHz
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": FINE_LAUNCH_DRAM_BYTES,
                 "kernel": "tl::solve_kernel (FP64 fine micro step)",
                 "launch_ms": statistics.mean(fine_ms), "cg_iters_per_launch": fine_iters,
                 "flops_per_launch": fine_flops(cfg, fine_iters),
@@ -553,6 +557,59 @@ def run_serve(args):
     return 0
 
 
+# Algorithmic bytes per node of one single-reduction CG pass (window update
+# fused into the matrix-free apply): reads dinv, r, w-partial, p, s, x and
+# writes p, s, r, x, w-partial (11 nodal values) plus the element data the
+# apply reads (FP32: s_e, k_e; FP64: eight eigenvalues), elements ~ nodes.
+PASS_BYTES = {"fp32": 11 * 4 + 2 * 4, "fp64": 11 * 8 + 8 * 8}
+PASS_FLOPS_FP64 = FLOPS_APPLY_PER_ELEM + FLOPS_VEC_PER_NODE
+
+
+def run_roofline(args):
+    """A 256 x 256 x 128-element fine patch (8.5M nodes; 32 x 32 x 16 coarse
+    elements refined 8x, plate 40 x 40 x 20 coarse): one micro step in each
+    precision, per-pass times from the device phase tracer."""
+    import torch
+
+    from paper_2110_12932_gb300 import build as tlbuild
+    from paper_2110_12932_gb300 import tl
+
+    tlbuild.build()
+    tl.load()
+    base = workloads.workload("multitrack_10mm", Lx=5e-3, Ly=5e-3, Lz=2.5e-3, NXc=40, NYc=40, NZc=20,
+                              pNXc=32, pNYc=32, pNZc=16, r=8, m=8,
+                              tracks=[(1e-3, 2.5e-3, 4e-3, 2.5e-3, 0.8)])
+    nn = fine_nodes(base)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        cfg = dict(base, precision=1 if prec == "fp32" else 0, tol=1e-10 if prec == "fp32" else 1e-12)
+        p = tl.Problem(cfg)
+        p.macro_steps(1)           # warm-up macro step
+        p.predict()
+        p.fine_substeps(1)
+        torch.cuda.synchronize()
+        ev = p.trace(tl.TL_FINE)
+        p.close()
+        passes = [(b - a) / 1e9 for (m0, a), (m1, b) in zip(ev, ev[1:]) if m1 == 4]  # CG pass ends
+        # a pass spans apply + reduction + barrier: time from one pass end to the next
+        ends = [b for (m, b) in ev if m == 4]
+        dts = [(y - x) / 1e9 for x, y in zip(ends, ends[1:])]
+        t = statistics.median(dts) if dts else float("nan")
+        byt = PASS_BYTES[prec] * nn
+        o = {"pass_us": 1e6 * t, "passes": len(ends), "bytes_per_pass": byt, "GBps": byt / t / 1e9,
+             "frac_of_measured_hbm": byt / t / 1e9 / 6688.8}
+        if prec == "fp64":
+            fl = PASS_FLOPS_FP64 * nn
+            o.update({"TFLOPs": fl / t / 1e12, "frac_of_fp64_peak": fl / t / 1e12 / 1.25856})
+        out[prec] = o
+    line = {"metric": "CG pass throughput (matrix-free apply + fused update)", "mode": "roofline",
+            "config": {"fine_nodes": nn, "fine_elements": 256 * 256 * 128,
+                       "bytes_per_node": PASS_BYTES, "fp64_flops_per_node": PASS_FLOPS_FP64},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -561,6 +618,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "roofline":
+        return run_roofline(args)
     return run_ours(args)
 
 

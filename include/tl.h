@@ -184,7 +184,10 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
  * boundary data / load done, 2 right-hand side applies done, 3 initial
  * residual done, 4 end of a CG pass, 5 refined: inner start, 6 refined: FP64
  * correction apply done, 7 refined: outer sweep done, 8 update start, 9 end,
- * 10 block 0 finished its share of a CG pass's apply (before the reduction).
+ * 10 block 0 finished its share of a CG pass's apply (before the reduction);
+ * value markers, whose second word holds the IEEE bits of a double instead of
+ * a time: 11 <r,r> after a CG pass, 12 the recurrence term that stopped a CG
+ * on a non-positive value.
  * Synchronises.  Errors: TL_EINVAL, TL_ECUDA. */
 tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap,
                               size_t* n_out);

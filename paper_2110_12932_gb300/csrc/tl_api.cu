@@ -54,7 +54,7 @@ struct Level {
   float* s0f = nullptr;
   float* s1f = nullptr;
   float* dinv32 = nullptr;
-  float* lam32 = nullptr;
+  float* sk32 = nullptr;
   double* inj = nullptr;  // coarse only
   unsigned long long* trace = nullptr;  // phase timestamps of the level's last solve
   uint8_t* state = nullptr;
@@ -222,7 +222,7 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
     if ((s = alloc_n(p, &L.s0f, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.s1f, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.dinv32, nn)) != TL_OK) return s;
-    if ((s = alloc_n(p, &L.lam32, 8 * ne)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.sk32, 2 * ne)) != TL_OK) return s;
   }
   if (coarse && (s = alloc_n(p, &L.inj, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.trace, 2 * TRACE_CAP)) != TL_OK) return s;
@@ -351,7 +351,7 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.s0f = L.s0f;
   a.s1f = L.s1f;
   a.dinv32 = L.dinv32;
-  a.lam32 = L.lam32;
+  a.sk32 = L.sk32;
   a.precision = p->cfg.precision == TL_FP32_REFINED ? PREC_FP32_REFINED : PREC_FP64;
   a.tol_inner = p->cfg.tol_inner;
   a.max_outer = 20;
@@ -379,8 +379,8 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
 
 tl_status launch_solve(tl_problem* p, const Level& L, SolveArgs& a) {
   void* args[] = {(void*)&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(L.grid), dim3(NT), args, 0,
-                                              p->stream);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(L.grid), dim3(NT), args,
+                                              STAGE_BYTES, p->stream);
   p->launches++;
   return cuda_status(e);
 }
@@ -654,7 +654,9 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, 0);
+    e = cudaFuncSetAttribute((const void*)solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, STAGE_BYTES);
   if (e != cudaSuccess || per_sm < 1) {
     delete p;
     cudaGetLastError();
@@ -915,7 +917,10 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_batch_kernel, NT, 0);
+    e = cudaFuncSetAttribute((const void*)solve_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             STAGE_BYTES);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_batch_kernel, NT, STAGE_BYTES);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     delete b;
@@ -1076,8 +1081,8 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
   const BatchTable* tp = b->d_tab;
   const SolveArgs* ap = b->d_args;
   void* kargs[] = {(void*)&tp, (void*)&ap};
-  e = cudaLaunchCooperativeKernel((const void*)solve_batch_kernel, dim3(tab.first[nj]), dim3(NT), kargs, 0,
-                                  b->stream);
+  e = cudaLaunchCooperativeKernel((const void*)solve_batch_kernel, dim3(tab.first[nj]), dim3(NT), kargs,
+                                  STAGE_BYTES, b->stream);
   if (e != cudaSuccess) return cuda_status(e);
   b->launches++;
   b->rounds++;

@@ -159,7 +159,9 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, 0);
+    e = cudaFuncSetAttribute((const void*)solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, STAGE_BYTES);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return TL_ECUDA;
@@ -237,7 +239,7 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
     return TL_ECUDA;
   }
   void* args[] = {(void*)&a};
-  e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(grid), dim3(NT), args, 0, st);
+  e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(grid), dim3(NT), args, STAGE_BYTES, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   int status = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&status, words + BAR_STATUS, sizeof(int), cudaMemcpyDeviceToHost);

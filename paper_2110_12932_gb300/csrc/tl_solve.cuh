@@ -31,6 +31,18 @@ constexpr int TYE = 8;                // max tile depth in elements (y)
 constexpr int WX = TXE + 1, WY = TYE + 1;
 constexpr int NT = 160;               // threads per block: one window column each
 constexpr int MIN_BLOCKS = 4;         // resident blocks per SM the register budget targets
+constexpr int NRAW = 13;              // staged raw inputs per window node (CG pass: 6 + 7 partials)
+constexpr int STAGE_BYTES = 2 * NRAW * NT * 8;  // dynamic shared memory: two layers in flight
+
+// Asynchronous global -> shared copies of 4 or 8 bytes (per-thread groups).
+template <int BYTES>
+__device__ inline void cp_async(void* smem, const void* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 static_assert(NT >= WX * WY, "a block must cover a tile's window columns");
 constexpr int MAXRECT = 8;
 constexpr int NXB = 7;                // exchange buffers
@@ -285,7 +297,7 @@ struct SolveArgs {
   float* s0f;
   float* s1f;
   float* dinv32;
-  float* lam32;
+  float* sk32;   // refined path: FP32 s_e, k_e ([2][nelem]); eigenvalues rebuilt in registers
   double* F;     // top-face load, (nx+1)(ny+1)
   double* G;     // load factor tables, MAXRECT (nnx + nny)
   uint8_t* state;
@@ -311,7 +323,9 @@ struct SolveArgs {
 // Phase markers recorded by block 0 when tracing.
 enum TraceMark : int {
   TR_START = 0, TR_PHASE0 = 1, TR_RHS = 2, TR_RESID = 3, TR_CG_PASS = 4, TR_OUTER_INIT = 5,
-  TR_OUTER_APPLY = 6, TR_OUTER_END = 7, TR_UPDATE = 8, TR_END = 9, TR_CG_APPLY = 10
+  TR_OUTER_APPLY = 6, TR_OUTER_END = 7, TR_UPDATE = 8, TR_END = 9, TR_CG_APPLY = 10,
+  TR_RR = 11,      // value marker: second word = <r,r> of the pass (IEEE double bits)
+  TR_BREAK = 12    // value marker: CG stopped on a non-positive recurrence term
 };
 constexpr int TRACE_CAP = 1024;
 
@@ -323,6 +337,14 @@ struct Tracer {
     if (buf && bid == 0 && threadIdx.x == 0 && n < TRACE_CAP - 1) {
       buf[2 * (n + 1)] = (unsigned long long)m;
       buf[2 * (n + 1) + 1] = global_ns();
+      ++n;
+      buf[0] = (unsigned long long)n;
+    }
+  }
+  __device__ void value(int m, double v) {
+    if (buf && bid == 0 && threadIdx.x == 0 && n < TRACE_CAP - 1) {
+      buf[2 * (n + 1)] = (unsigned long long)m;
+      buf[2 * (n + 1) + 1] = (unsigned long long)__double_as_longlong(v);
       ++n;
       buf[0] = (unsigned long long)n;
     }
@@ -346,13 +368,22 @@ struct ApplySmem {
 // one (element row, node column) pair (stages 2 and 4, same index) and one
 // element column (stage 3), all fixed for the tile, so the index arithmetic is
 // done once per tile.  For every window node n the tile emits
-// emit(n, slot, y, xin): y its partial of (A x)_n, xin = x_n as loaded,
+// emit(n, slot, y, xin): y its partial of (A x)_n, xin = x_n as consumed,
 // slot = 0 if the tile owns n, else (high-x) + 2 (high-y) + 4 (high-z).
-// load(n, i, j, k, owned) returns x_n and is called exactly once per window
-// node; lam(e, l8) fills the eight Hadamard eigenvalues of element e.
-template <typename R, class Load, class Lam, class Emit>
-__device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, ApplySmem<R>& sm,
-                                  Load load, Lam lam, Emit emit) {
+// Inputs are staged one layer ahead: fetch(n, i, j, k, owned, raw) issues
+// asynchronous copies of the raw data node n needs into the thread's staging
+// slots raw[s * NT], and finish(n, i, j, k, owned, raw) turns them into x_n
+// (called exactly once per window node, after the copies landed).  The
+// copies for layer k+2 are issued while layer k is being processed.
+// lam(e, l8) fills the eight Hadamard eigenvalues of element e.
+// Element data (the eigenvalues' inputs) are either loaded into registers at
+// the start of each layer (LAM_STAGED false: lam(e, nullptr, l8) reads
+// global memory) or staged one layer ahead in slots NRAW.. of the same ring
+// (LAM_STAGED true: lam_fetch(e, slots) issues the copies, lam(e, slots, l8)
+// builds the eigenvalues).  NS = slots per buffer and thread.
+template <typename R, bool LAM_STAGED, int NS, class Fetch, class Finish, class LamFetch, class Lam, class Emit>
+__device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, ApplySmem<R>& sm, R* stage,
+                                  Fetch fetch, Finish finish, LamFetch lam_fetch, Lam lam, Emit emit) {
   const int tid = threadIdx.x;
   const int txy = t.ntx * t.nty;
   const int tiz = tile / txy, trem = tile - tiz * txy;
@@ -372,24 +403,43 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
   const int wslot = ((wli == ex && ie0 + ex < g.nx) ? 1 : 0) | ((wlj == ey && je0 + ey < g.ny) ? 2 : 0);
   const int wi = ie0 + wli, wj = je0 + wlj;
   const bool z_top_owned = ke1 == g.nz;  // the tile owns its top node layer only at the plate top
+  R* raw0 = stage + tid;                 // staging buffer of node layers with (k - ke0) even
+  R* raw1 = stage + NS * NT + tid;       // ... odd
+  auto owned_at = [&](int k) { return wslot == 0 && (k < ke1 || z_top_owned); };
+  if (has_w) fetch(wnode + ke0 * S, wi, wj, ke0, owned_at(ke0), raw0);
+  cp_async_commit();
+  if (has_w) fetch(wnode + (ke0 + 1) * S, wi, wj, ke0 + 1, owned_at(ke0 + 1), raw1);
+  // element layer k sits in the buffer of node layer k + 1
+  if (LAM_STAGED && has_e) lam_fetch(welem + ke0 * Se, raw1 + NRAW * NT);
+  cp_async_commit();
+  cp_async_wait<1>();
   int cur = 0;
-  if (has_w) sm.X[cur][wlj][wli] = load(wnode + ke0 * S, wi, wj, ke0, wslot == 0);
+  if (has_w) sm.X[cur][wlj][wli] = finish(wnode + ke0 * S, wi, wj, ke0, owned_at(ke0), raw0);
   R carry = R(0);
   __syncthreads();
   for (int ke = ke0; ke < ke1; ++ke) {
     const int nxt = cur ^ 1;
-    // eigenvalues of this layer's element: issued now, used in stage 3, so
-    // their latency overlaps the input loads of stage 1
+    // eigenvalues of this layer's element: from registers loaded now (used in
+    // stage 3), or built in stage 3 from the staged element data
     R l8[8];
-    if (has_e) lam(welem + ke * Se, l8);
-    // stage 1: next layer, z-direction Hadamard per window column
+    if (!LAM_STAGED && has_e) lam(welem + ke * Se, nullptr, l8);
+    // stage 1: next layer (already staged), z-direction Hadamard per window column
+    cp_async_wait<0>();
+    R* rnext = ((ke + 1 - ke0) & 1) ? raw1 : raw0;
+    R* rfree = ((ke - ke0) & 1) ? raw1 : raw0;
     if (has_w) {
-      R hi = load(wnode + (ke + 1) * S, wi, wj, ke + 1, wslot == 0 && (ke + 1 < ke1 || z_top_owned));
+      R hi = finish(wnode + (ke + 1) * S, wi, wj, ke + 1, owned_at(ke + 1), rnext);
+      if (ke + 2 <= ke1) fetch(wnode + (ke + 2) * S, wi, wj, ke + 2, owned_at(ke + 2), rfree);
       R lo = sm.X[cur][wlj][wli];
       sm.X[nxt][wlj][wli] = hi;
       sm.a.Z[0][wlj][wli] = lo + hi;
       sm.a.Z[1][wlj][wli] = lo - hi;
     }
+    if (LAM_STAGED && has_e) {
+      lam(welem + ke * Se, rnext + NRAW * NT, l8);
+      if (ke + 1 < ke1) lam_fetch(welem + (ke + 1) * Se, rfree + NRAW * NT);
+    }
+    cp_async_commit();
     __syncthreads();
     // stage 2: y-direction per element row and node column
     if (has_r) {
@@ -445,8 +495,24 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
   }
   // top node layer of the tile: only the contributions of element layer ke1-1
   if (has_w) emit(wnode + ke1 * S, wslot | (ke1 < g.nz ? 4 : 0), carry, sm.X[cur][wlj][wli]);
+  cp_async_wait<0>();
   __syncthreads();
 }
+
+// Staging helpers for plain inputs: one array value per node.
+template <typename R, typename T>
+struct StageArray {
+  const T* src;
+  __device__ void operator()(int n, int, int, int, bool, R* raw) const {
+    cp_async<sizeof(T)>(raw, src + n);
+  }
+};
+template <typename R, typename T>
+struct FinishArray {
+  __device__ R operator()(int, int, int, int, bool, const R* raw) const {
+    return (R)(*reinterpret_cast<const T*>(raw));
+  }
+};
 
 // Which exchange partials a node's owner adds (the tile boundaries it lies
 // on): bit 0 low-x, bit 1 low-y, bit 2 low-z of the owning tile.  Tile widths
@@ -538,19 +604,15 @@ struct CGBufs {
 // iteration.  Starts from the residual in c.r[0] with <r,r> = rr0; stops when
 // <r, r> <= thresh or after max_iter iterations.  Returns 1 converged, 0
 // capped, -1 barrier failure; *iters gets the count.
-template <typename R>
-__device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const CGBufs<R>& c, R thresh,
-                    int max_iter, R* red, int* iters, Tracer& tr) {
+template <typename R, bool LAM_STAGED, int NS, class LamFetch, class Lam>
+__device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* stage, const CGBufs<R>& c,
+                    LamFetch lam_fetch, Lam lam8, R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
   __shared__ R s_scal[3];
   const Grid3 g = a.g;
   const Tiling t = a.t;
   const int nn = g.nnx * g.nny * g.nnz;
   const int ne = g.nx * g.ny * g.nz;
   const int ntiles = t.ntx * t.nty * t.ntz;
-  auto lam8 = [&](int e, R (&l8)[8]) {
-#pragma unroll
-    for (int m = 0; m < 8; ++m) l8[m] = __ldcg(c.lam + m * ne + e);
-  };
   R alpha = R(0), beta = R(0), gamma = R(0);
   int it = 0;
   bool conv = false;
@@ -571,10 +633,36 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const
     R* X_out = (k >= 0 && nxt) ? c.X[1] : c.X[0];
     R sg = R(0), vd = R(0), vr = R(0);
     for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
-      auto load = [&](int n, int i, int j, int kk, bool owned) -> R {
+      // raw inputs of a window node: 0 dinv, 1 r, 2 own partial of w, 3 p, 4 s,
+      // 5..11 the neighbours' partials of w (only on tile faces), 12 x (owner)
+      auto fetch = [&](int n, int i, int j, int kk, bool owned, R* raw) {
+        if (is_dir(g, a.dir, i, j, kk)) return;
+        cp_async<sizeof(R)>(raw, c.dinv + n);
+        cp_async<sizeof(R)>(raw + NT, r_cur + n);
+        if (k < 0) return;
+        cp_async<sizeof(R)>(raw + 2 * NT, q_cur + n);
+        if (owned) cp_async<sizeof(R)>(raw + 12 * NT, c.x + n);
+        if (!first) {
+          cp_async<sizeof(R)>(raw + 3 * NT, p_cur + n);
+          cp_async<sizeof(R)>(raw + 4 * NT, s_cur + n);
+        }
+        const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
+        const bool lz = kk > 0 && kk < g.nz && (kk % t.ez) == 0;
+        const int lf = low_faces(g, t, i, ly, lz);
+        if (lf) {
+          if (lf & 1) cp_async<sizeof(R)>(raw + 5 * NT, X_cur + 0 * nn + n);
+          if (lf & 2) cp_async<sizeof(R)>(raw + 6 * NT, X_cur + 1 * nn + n);
+          if ((lf & 3) == 3) cp_async<sizeof(R)>(raw + 7 * NT, X_cur + 2 * nn + n);
+          if (lf & 4) cp_async<sizeof(R)>(raw + 8 * NT, X_cur + 3 * nn + n);
+          if ((lf & 5) == 5) cp_async<sizeof(R)>(raw + 9 * NT, X_cur + 4 * nn + n);
+          if ((lf & 6) == 6) cp_async<sizeof(R)>(raw + 10 * NT, X_cur + 5 * nn + n);
+          if (lf == 7) cp_async<sizeof(R)>(raw + 11 * NT, X_cur + 6 * nn + n);
+        }
+      };
+      auto finish = [&](int n, int i, int j, int kk, bool owned, const R* raw) -> R {
         if (is_dir(g, a.dir, i, j, kk)) return R(0);
-        const R dv = __ldcg(c.dinv + n);
-        const R rk = __ldcg(r_cur + n);
+        const R dv = raw[0];
+        const R rk = raw[NT];
         if (k < 0) {
           const R u = dv * rk;
           if (owned) {
@@ -585,12 +673,22 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const
         }
         const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
         const bool lz = kk > 0 && kk < g.nz && (kk % t.ez) == 0;
-        const R w = gather_partials(q_cur, X_cur, nn, n, low_faces(g, t, i, ly, lz));
+        const int lf = low_faces(g, t, i, ly, lz);
+        R w = raw[2 * NT];  // neighbours' partials added in the order gather_partials uses
+        if (lf) {
+          if (lf & 1) w += raw[5 * NT];
+          if (lf & 2) w += raw[6 * NT];
+          if ((lf & 3) == 3) w += raw[7 * NT];
+          if (lf & 4) w += raw[8 * NT];
+          if ((lf & 5) == 5) w += raw[9 * NT];
+          if ((lf & 6) == 6) w += raw[10 * NT];
+          if (lf == 7) w += raw[11 * NT];
+        }
         const R u = dv * rk;
         R pv = u, sv = w;
         if (!first) {
-          pv = fma(beta, __ldcg(p_cur + n), u);
-          sv = fma(beta, __ldcg(s_cur + n), w);
+          pv = fma(beta, raw[3 * NT], u);
+          sv = fma(beta, raw[4 * NT], w);
         }
         const R rn = fma(-alpha, sv, rk);
         const R un = dv * rn;
@@ -598,7 +696,7 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const
           p_nxt[n] = pv;
           s_nxt[n] = sv;
           r_nxt[n] = rn;
-          c.x[n] = fma(alpha, pv, __ldcg(c.x + n));
+          c.x[n] = fma(alpha, pv, raw[12 * NT]);
           sg = fma(rn, un, sg);
           vr = fma(rn, rn, vr);
         }
@@ -608,7 +706,7 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const
         store_partial(q_out, X_out, nn, n, slot, y, false);
         vd = fma(xin, y, vd);
       };
-      apply_tile<R>(g, t, tile, sm, load, lam8, emit);
+      apply_tile<R, LAM_STAGED, NS>(g, t, tile, sm, stage, fetch, finish, lam_fetch, lam8, emit);
     }
     tr.mark(TR_CG_APPLY);
     {
@@ -619,6 +717,7 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const
     tr.mark(TR_CG_PASS);
     R tot[3];
     grid_total<3>(red + RS_PQ * a.red_stride, a.red_stride, tot, vg);
+    tr.value(TR_RR, (double)tot[2]);
     if (k >= 0) {
       ++it;
       if (tot[2] <= thresh) {
@@ -636,7 +735,10 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, const
       s_scal[2] = (den > R(0) && gn > R(0)) ? R(1) : R(0);
     }
     __syncthreads();
-    if (s_scal[2] == R(0)) break;  // breakdown (no further progress possible): stop
+    if (s_scal[2] == R(0)) {  // breakdown (no further progress possible): stop
+      tr.value(TR_BREAK, (double)tot[1]);
+      break;
+    }
     gamma = tot[0];
     alpha = s_scal[0];
     beta = s_scal[1];
@@ -665,8 +767,11 @@ __device__ inline double elem_mean(const double* T, const Grid3& g, int ie, int 
 __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   __shared__ __align__(16) unsigned char smem_raw[sizeof(ApplySmem<double>)];
   __shared__ double s_Mhat[64], s_Khat[64];
+  extern __shared__ __align__(16) unsigned char stage_raw[];  // STAGE_BYTES of staged inputs
   ApplySmem<double>& sm64 = *reinterpret_cast<ApplySmem<double>*>(smem_raw);
   ApplySmem<float>& sm32 = *reinterpret_cast<ApplySmem<float>*>(smem_raw);
+  double* stage64 = reinterpret_cast<double*>(stage_raw);
+  float* stage32 = reinterpret_cast<float*>(stage_raw);
   if (ld_volatile_i32(a.bar.status) != 0) return;  // an earlier solve failed: leave state untouched
   Tracer tr{a.trace, vg.bid};
   tr.mark(TR_START);
@@ -712,9 +817,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
 #pragma unroll
     for (int m = 1; m < 8; ++m) a.lam[m * ne + e] = se * a.Mc[m] + k * a.Kc[m];
     if (refined) {
-      const float sf = (float)se, kf = (float)k;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) a.lam32[m * ne + e] = fmaf(sf, (float)a.Mc[m], kf * (float)a.Kc[m]);
+      a.sk32[e] = (float)se;
+      a.sk32[ne + e] = (float)k;
     }
   });
   // increments: 0 on free nodes, g - T^k on Dirichlet nodes (disjoint writes)
@@ -761,23 +865,25 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   });
   {
     // partials of A u_D (u holds the Dirichlet increments, 0 elsewhere) + K T^k
-    auto lam_full = [&](int e, double (&l8)[8]) {
+    auto lam_full = [&](int e, const double*, double (&l8)[8]) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) l8[m] = __ldcg(a.lam + m * ne + e);
     };
-    auto lam_k = [&](int e, double (&l8)[8]) {
+    auto lam_k = [&](int e, const double*, double (&l8)[8]) {
       const double k = __ldcg(a.k_e + e);
       l8[0] = 0.0;
 #pragma unroll
       for (int m = 1; m < 8; ++m) l8[m] = k * a.Kc[m];
     };
-    auto load_u = [&](int n, int, int, int, bool) -> double { return __ldcg(a.u + n); };
-    auto load_T = [&](int n, int, int, int, bool) -> double { return __ldcg(a.T_in + n); };
     auto emit1 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
     auto emit2 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, true); };
+    const FinishArray<double, double> fin;
+    auto no_lam_fetch = [](int, double*) {};
     for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
-      apply_tile<double>(g, t, tile, sm64, load_u, lam_full, emit1);
-      apply_tile<double>(g, t, tile, sm64, load_T, lam_k, emit2);
+      apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.u}, fin, no_lam_fetch,
+                                      lam_full, emit1);
+      apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.T_in}, fin,
+                                      no_lam_fetch, lam_k, emit2);
     }
   }
   if (!grid_sync(a.bar, vg)) return;
@@ -808,17 +914,29 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   bool conv = !(bb > 0.0) || (a.tol >= 1.0);
   if (!conv && !refined) {
     CGBufs<double> c{a.u, {a.r, a.r2}, {a.p0, a.p1}, {a.s0, a.s1}, {a.q, a.q2}, {a.X, a.X2}, a.dinv, a.lam};
-    int res = pcg1<double>(a, vg, sm64, c, thresh, a.max_iter, a.red, &it, tr);
+    auto lam64 = [&](int e, const double*, double (&l8)[8]) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) l8[m] = __ldcg(a.lam + m * ne + e);
+    };
+    auto no_fetch64 = [](int, double*) {};
+    int res = pcg1<double, false, NRAW>(a, vg, sm64, stage64, c, no_fetch64, lam64, thresh, a.max_iter, a.red, &it,
+                                        tr);
     if (res < 0) return;
     conv = res == 1;
   }
   // refined: FP32 CG for the correction d of the FP64 residual, FP64 update of
-  // u and of the residual r -= A d, until ||r|| <= tol ||r_0||
+  // u and of the residual r -= A d, until ||r|| <= tol ||r_0||.  The inner
+  // problem is scaled to unit residual norm (r / sigma with sigma = ||r||), so
+  // FP32 neither underflows on nearly converged or barely loaded solves nor
+  // overflows on hot ones; the correction is sigma d.
+  double rr64 = bb;
   while (!conv && refined && outer < a.max_outer) {
+    const double sigma = sqrt(rr64);
+    const double isig = 1.0 / sigma;
     {
       float v[2] = {0.0f, 0.0f};
       for_nodes(g, t, vg, [&](int n, int, int, int, bool, bool) {
-        float rf = (float)__ldcg(a.r + n);
+        float rf = (float)(__ldcg(a.r + n) * isig);
         a.r32[n] = rf;
         a.d32[n] = 0.0f;
         v[0] = fmaf(rf * rf, __ldcg(a.dinv32 + n), v[0]);
@@ -832,30 +950,48 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     grid_total<2>(a.red32 + RS_RZ0 * a.red_stride, a.red_stride, t32, vg);
     int inner = 0;
     CGBufs<float> c{a.d32, {a.r32, a.r32b}, {a.p0f, a.p1f}, {a.s0f, a.s1f}, {a.q32, a.q32b}, {a.X32, a.X32b},
-                    a.dinv32, a.lam32};
+                    a.dinv32, nullptr};
+    float mcf[8], kcf[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      mcf[m] = (float)a.Mc[m];
+      kcf[m] = (float)a.Kc[m];
+    }
+    // element data staged one layer ahead: slots NRAW (s_e) and NRAW + 1 (k_e)
+    auto fetch32 = [&](int e, float* slots) {
+      cp_async<4>(slots, a.sk32 + e);
+      cp_async<4>(slots + NT, a.sk32 + ne + e);
+    };
+    auto lam32 = [&](int e, const float* slots, float (&l8)[8]) {
+      const float se = slots[0], ke = slots[NT];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) l8[m] = fmaf(se, mcf[m], ke * kcf[m]);
+    };
     const float ti = (float)a.tol_inner;
-    int res = pcg1<float>(a, vg, sm32, c, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+    int res = pcg1<float, true, NRAW + 2>(a, vg, sm32, stage32, c, fetch32, lam32, ti * ti * t32[1], a.max_iter,
+                                          a.red32, &inner, tr);
     if (res < 0) return;
     it += inner;
     ++outer;
     // FP64 apply of the correction (exact in FP64: d is an FP32 vector)
-    auto lam_full = [&](int e, double (&l8)[8]) {
+    auto lam_full = [&](int e, const double*, double (&l8)[8]) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) l8[m] = __ldcg(a.lam + m * ne + e);
     };
-    auto load_d = [&](int n, int, int, int, bool) -> double { return (double)__ldcg(a.d32 + n); };
+    auto no_lam_fetch = [](int, double*) {};
     auto emit = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
     for (int tile = vg.bid; tile < ntiles; tile += vg.nblk)
-      apply_tile<double>(g, t, tile, sm64, load_d, lam_full, emit);
+      apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, float>{a.d32},
+                                      FinishArray<double, float>{}, no_lam_fetch, lam_full, emit);
     if (!grid_sync(a.bar, vg)) return;
     tr.mark(TR_OUTER_APPLY);
     double v[1] = {0.0};
     for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool ly, bool lz) {
       if (is_dir(g, a.dir, i, j, k)) return;
       double y = gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
-      double rn = __ldcg(a.r + n) - y;
+      double rn = fma(-sigma, y, __ldcg(a.r + n));  // partials are of A d; the correction is sigma d
       a.r[n] = rn;
-      a.u[n] = __ldcg(a.u + n) + (double)__ldcg(a.d32 + n);
+      a.u[n] = fma(sigma, (double)__ldcg(a.d32 + n), __ldcg(a.u + n));
       v[0] += rn * rn;
     });
     block_reduce_store<1>(v, a.red + RS_RR * a.red_stride, a.red_stride, vg);
@@ -863,6 +999,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     double trr[1];
     grid_total<1>(a.red + RS_RR * a.red_stride, a.red_stride, trr, vg);
     tr.mark(TR_OUTER_END);
+    rr64 = trr[0];
     conv = trr[0] <= thresh;
   }
   const int lvl = a.level;

@@ -246,7 +246,8 @@ def tl_box_step_noalloc(desc, T_in_ptr, T_out_ptr, state_ptr, stream=None):
 
 
 TRACE_MARKS = {0: "start", 1: "phase0", 2: "rhs", 3: "resid", 4: "cg_pass", 5: "outer_init",
-               6: "outer_apply", 7: "outer_end", 8: "update", 9: "end", 10: "cg_apply"}
+               6: "outer_apply", 7: "outer_end", 8: "update", 9: "end", 10: "cg_apply",
+               11: "rr_value", 12: "breakdown_value"}
 
 
 def tl_trace_last_solve(h, level, cap=1024):
