@@ -27,7 +27,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2110_12932_gb300 import workloads  # noqa: E402
+from paper_2110_12932_gb300 import ranks, workloads  # noqa: E402
 
 WORKLOAD = "multitrack_10mm"
 METRIC = "fine DOF-substeps/s"
@@ -112,33 +112,12 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus):
-    import torch
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    if ws > 1:
-        import torch.distributed as dist
-        rank = int(os.environ["RANK"])
-        local = int(os.environ.get("LOCAL_RANK", rank))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        return rank, ws, local
-    torch.cuda.set_device(0)
-    return 0, 1, 0
+    return ranks.init("nccl")
 
 
-def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+barrier = ranks.barrier
+max_over_ranks = ranks.max_over_ranks
+sum_over_ranks = ranks.sum_over_ranks
 
 
 def fine_nodes(cfg):
@@ -291,7 +270,7 @@ def run_ours(args):
     clk = clocks.stop()
     barrier(ws)
     dev_ms = max_over_ranks(dev_ms, ws)
-    work = ws * K * m * nfn
+    work = sum_over_ranks(K * m * nfn, ws)
     value = work / (dev_ms / 1e3)
     fine_iters = st["cg_iters_fine"] / max(1, st["solves_fine"])
     launch_s = statistics.mean(fine_ms) / 1e3
@@ -318,7 +297,7 @@ def run_ours(args):
         "fine_launch_ms": statistics.mean(fine_ms_r),
         "inner_iters_per_solve": st_r["cg_iters_fine"] / max(1, st_r["solves_fine"]),
         "outer_iters_per_solve": st_r["outer_iters_fine"] / max(1, st_r["solves_fine"]),
-        "gpu_launches": st_r["launches"] * ws,
+        "gpu_launches": int(sum_over_ranks(st_r["launches"], ws)),
     }
 
     # ---- end to end through the public API: create, K steps, host read-back each step
@@ -337,6 +316,7 @@ def run_ours(args):
            "note": "tl_create_problem + per step tl_macro_steps(1) + tl_get_temperature(fine) into a host buffer; "
                    "step inputs (laser positions, weights) travel as launch parameters"}
 
+    launches = int(sum_over_ranks(st["launches"], ws))
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
@@ -349,15 +329,13 @@ def run_ours(args):
                            "m": m, "r": r, "tol": cfg["tol"], "precision": "fp64",
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "flushed (256 MB write) between timed macro steps, outside the events"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"] * ws,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "wall_s": wall,
                 "cg_iters": {"fine_per_solve": fine_iters,
                              "coarse_per_solve": st["cg_iters_coarse"] / max(1, st["solves_coarse"])},
                 "fp32_refined": refined}
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    ranks.finish(ws)
     return 0
 
 
@@ -378,7 +356,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     # jobs are dealt round-robin to the ranks (no exchange between them)
-    jobs = [j for k, j in enumerate(workloads.batch_jobs(args.jobs)) if k % ws == rank]
+    jobs = ranks.deal(workloads.batch_jobs(args.jobs), rank, ws)
     for j in jobs:
         j.update(precision=1, tol=1e-10, tol_inner=1e-5)
     work = sum(fine_nodes(j) * j["m"] * j["macro_steps"] for j in jobs)
@@ -428,7 +406,8 @@ def run_batch(args):
     batch.close()
     for p in probs:
         p.close()
-    total_work = work * ws  # rank shares are equal in expectation; report this rank's count scaled
+    total_work = sum_over_ranks(work, ws)
+    launches = int(sum_over_ranks(info["launches"], ws))
     # plain FP64 one at a time: time each job's first macro steps alone
     sample_steps = 3
     alone_s = 0.0
@@ -455,10 +434,10 @@ def run_batch(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": f"batch_jobs({args.jobs}, seed 20211025)", "jobs": len(jobs),
-                           "fine_dof_substeps": work, "precision": "fp32_refined", "tol": 1e-10,
+                           "fine_dof_substeps": total_work, "precision": "fp32_refined", "tol": 1e-10,
                            "launches_per_round": args.launches_per_round, "graph_mode": info["graph_mode"],
                            "step": "one batched cooperative launch (each job's next solve)"},
-                "clocks": clk, "wall_s": wall,
+                "gpu_launches": launches, "clocks": clk, "wall_s": wall,
                 "all_ok": all(s == 0 for s in status),
                 "rounds_by_active_jobs": {k: {"rounds": c, "ms": ms} for k, (c, ms) in by_active.items()},
                 "cg_iters_fine_per_solve": sum(s["cg_iters_fine"] for s in stats) / max(1, sum(s["solves_fine"] for s in stats)),
@@ -468,9 +447,7 @@ def run_batch(args):
                               "extrapolated linearly to each job's scan"},
                 "speedup_vs_plain_fp64": (total_work / dev_s) / (alone_work / alone_s)}
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    ranks.finish(ws)
     return 0
 
 
@@ -506,7 +483,7 @@ def run_serve(args):
     tl.load()
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    arrivals = [a for k, a in enumerate(workloads.serving_arrivals(args.rate, args.duration)) if k % ws == rank]
+    arrivals = ranks.deal(workloads.serving_arrivals(args.rate, args.duration), rank, ws)
     work = sum(fine_nodes(c) * c["m"] * c["macro_steps"] for _, c in arrivals)
     srv = serve.Server(mem_cap_bytes=args.mem_cap_gb * 1e9, max_jobs=256,
                        launches_per_round=args.launches_per_round, stream=sp)
@@ -531,9 +508,9 @@ def run_serve(args):
             cache[key] = fp64_service_estimate(tl, torch, c, sp, stream)
         service.append(cache[key])
     fifo = serve.fifo_one_at_a_time(arrivals, service)
-    value = rep["fine_dof_substeps"] / rep["busy_s"]
+    value = ranks.aggregate_rate(rep["fine_dof_substeps"], rep["busy_s"], ws)
     if rank == 0:
-        line = {"metric": METRIC, "value": value * ws, "unit": "DOF-substeps/s", "n_gpus": ws,
+        line = {"metric": METRIC, "value": value, "unit": "DOF-substeps/s", "n_gpus": ws,
                 "steps": rep["rounds"], "warmup": 1, "ms_per_step": 1e3 * rep["busy_s"] / max(1, rep["rounds"]),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
@@ -551,9 +528,7 @@ def run_serve(args):
                     "sample": "service time per job shape from its first 2 macro steps alone (FP64, tol 1e-12), "
                               "extrapolated; first come first served"}}
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    ranks.finish(ws)
     return 0
 
 
