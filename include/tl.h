@@ -96,8 +96,15 @@ typedef struct {
   double tol;             /* relative residual of each solve (FP64 measure)    */
   double tol_inner;       /* relative residual of each FP32 inner solve        */
   int max_iter;           /* CG iteration cap per solve (inner cap when refined) */
+  /* refined path, tiling of the FP32 inner CG: 0 = chosen by mesh size,
+   * 1 = element tiles of up to 16 x 8 x ez with the vector update fused into
+   * the apply (one grid barrier per iteration; small meshes), 2 = wide tiles
+   * of up to 64 x 4 x ez with a separate streaming update (two barriers per
+   * iteration; large meshes).  Ignored by TL_FP64. */
+  int inner_tiles;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
-  /* optional device allocator: both NULL -> cudaMalloc / cudaFree */
+  /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks
+   * must be 16-byte aligned (else tl_create_problem returns TL_EINVAL) */
   void* (*alloc)(size_t bytes, void* stream, void* ctx);
   void (*free)(void* ptr, void* stream, void* ctx);
   void* alloc_ctx;
@@ -187,7 +194,9 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
  * 10 block 0 finished its share of a CG pass's apply (before the reduction);
  * value markers, whose second word holds the IEEE bits of a double instead of
  * a time: 11 <r,r> after a CG pass, 12 the recurrence term that stopped a CG
- * on a non-positive value.
+ * on a non-positive value; 13 the vector-update phase of a CG iteration done
+ * (grid barrier passed); 14 / 15 block 0 starts / finished its share of that
+ * update phase.
  * Synchronises.  Errors: TL_EINVAL, TL_ECUDA. */
 tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap,
                               size_t* n_out);

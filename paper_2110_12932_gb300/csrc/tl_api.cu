@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -22,6 +24,8 @@ struct Level {
   Grid3 g{};
   Tiling t{};
   Tiling tb{};   // tiling used in batched launches (a slice of the grid)
+  Tiling tw{};   // refined path on large meshes: wide tiles of the FP32 inner CG
+  int wide = 0;
   int grid = 0;  // cooperative grid size
   double* T = nullptr;    // current temperature
   double* T2 = nullptr;   // coarse: predictor T~+; fine: move double buffer
@@ -88,6 +92,16 @@ struct tl_problem {
 
 namespace {
 
+// The solve kernel for a precision mode (0 plain FP64, 1 refined, 2 either).
+const void* solve_kernel_for(int pmode) {
+  return pmode == 0 ? (const void*)solve_kernel<0> : (const void*)solve_kernel<1>;
+}
+const void* batch_kernel_for(int pmode) {
+  return pmode == 0 ? (const void*)solve_batch_kernel<0>
+                    : (pmode == 1 ? (const void*)solve_batch_kernel<1> : (const void*)solve_batch_kernel<2>);
+}
+int pmode_of(const tl_config& c) { return c.precision == TL_FP32_REFINED ? 1 : 0; }
+
 tl_status dev_alloc(tl_problem* p, void** out, size_t bytes) {
   *out = nullptr;
   if (bytes == 0) bytes = 16;
@@ -95,6 +109,10 @@ tl_status dev_alloc(tl_problem* p, void** out, size_t bytes) {
   if (p->cfg.alloc) {
     ptr = p->cfg.alloc(bytes, (void*)p->stream, p->cfg.alloc_ctx);
     if (!ptr) return TL_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) {  // the kernels use 16-byte vector accesses
+      if (p->cfg.free) p->cfg.free(ptr, (void*)p->stream, p->cfg.alloc_ctx);
+      return TL_EINVAL;
+    }
   } else {
     cudaError_t e = cudaMalloc(&ptr, bytes);
     if (e != cudaSuccess) {
@@ -183,6 +201,32 @@ void choose_tiling(Level& L, int nsm, int per_sm) {
       }
   L.t = bt;
 }
+
+// Wide tiles (AX x AY x ez elements) of the FP32 inner CG on large meshes:
+// every tile costs its ez layers plus a pipeline fill of about three layers,
+// and the step takes as long as the block with the most tiles.
+Tiling wide_tiling(const Grid3& g, int nblk) {
+  const int ntx = (g.nx + AX - 1) / AX, nty = (g.ny + AY - 1) / AY;
+  const long long C = (long long)ntx * nty;
+  double best = 1e300;
+  Tiling bt{AX, AY, g.nz, ntx, nty, 1};
+  for (int ez = 1; ez <= g.nz; ++ez) {
+    const int ntz = (g.nz + ez - 1) / ez;
+    const long long T = C * ntz;
+    const long long per_block = (T + nblk - 1) / nblk;
+    const double cost = (double)per_block * (ez + 3.0);
+    if (cost < best * (1 - 1e-9)) {
+      best = cost;
+      bt = Tiling{AX, AY, ez, ntx, nty, ntz};
+    }
+  }
+  return bt;
+}
+
+// With inner_tiles = 0 the refined path switches its inner CG to wide tiles
+// from this many elements (measured crossover: the fused element-tile CG is
+// faster at 1.3e5 elements, the wide two-phase CG at 1.0e6).
+constexpr long long WIDE_MIN_ELEMS = 1LL << 19;
 
 tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
   const size_t nn = (size_t)L.g.nnx * L.g.nny * L.g.nnz;
@@ -324,6 +368,8 @@ LoadSpec box_load(const tl_problem* p, int n) {
 void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.g = L.g;
   a.t = L.t;
+  a.wide = L.wide;
+  a.tw = L.tw;
   a.u = L.u;
   a.r = L.r;
   a.r2 = L.r2;
@@ -364,6 +410,8 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.max_iter = c.max_iter;
   std::memcpy(a.Mc, L.Mc, sizeof a.Mc);
   std::memcpy(a.Kc, L.Kc, sizeof a.Kc);
+  to_pair_form(a.Mc);
+  to_pair_form(a.Kc);
   a.Md = L.Md;
   a.Kd = L.Kd;
   a.vol8 = L.vol8;
@@ -379,7 +427,7 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
 
 tl_status launch_solve(tl_problem* p, const Level& L, SolveArgs& a) {
   void* args[] = {(void*)&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(L.grid), dim3(NT), args,
+  cudaError_t e = cudaLaunchCooperativeKernel(solve_kernel_for(pmode_of(p->cfg)), dim3(L.grid), dim3(NT), args,
                                               STAGE_BYTES, p->stream);
   p->launches++;
   return cuda_status(e);
@@ -503,6 +551,7 @@ tl_status validate(const tl_config* c) {
   if (!(c->tol > 0) || c->max_iter < 1) return TL_EINVAL;
   if (c->precision != TL_FP64 && c->precision != TL_FP32_REFINED) return TL_EINVAL;
   if (c->precision == TL_FP32_REFINED && !(c->tol_inner > 0 && c->tol_inner < 1)) return TL_EINVAL;
+  if (c->inner_tiles < 0 || c->inner_tiles > 2) return TL_EINVAL;
   if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
   for (int j = 0; j < c->ntracks; ++j) {
     const tl_track& k = c->path[j];
@@ -603,7 +652,8 @@ struct tl_batch {
   cudaStream_t stream = nullptr;
   int R = 0;                   // cooperative launches per round
   int cap = 0;                 // jobs per launch at most (one block each at least)
-  int max_coop = 0, nsm = 0;
+  int max_coop = 0, nsm = 0;    // co-resident blocks of the slowest-to-fit kernel variant
+  int max_coop_v[3] = {0, 0, 0}; // ... of each precision mode's batch kernel
   std::vector<Job> jobs;
   std::vector<int> finished;   // ids that reached their target, not yet polled
   BatchTable* d_tab = nullptr; // R tables
@@ -653,10 +703,9 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, STAGE_BYTES);
+  const void* kern = solve_kernel_for(pmode_of(*cfg));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, STAGE_BYTES);
   if (e != cudaSuccess || per_sm < 1) {
     delete p;
     cudaGetLastError();
@@ -681,6 +730,12 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   C.grid = std::min(p->max_coop, C.t.ntx * C.t.nty * C.t.ntz);
   F.grid = std::min(p->max_coop, F.t.ntx * F.t.nty * F.t.ntz);
   p->red_stride = std::max(C.grid, F.grid);
+  for (Level* L : {&C, &F}) {
+    const long long ne = (long long)L->g.nx * L->g.ny * L->g.nz;
+    L->wide = c.precision == TL_FP32_REFINED &&
+              (c.inner_tiles == 2 || (c.inner_tiles == 0 && ne >= WIDE_MIN_ELEMS));
+    if (L->wide) L->tw = wide_tiling(L->g, L->grid);
+  }
   if ((s = alloc_level(p, C, true)) != TL_OK || (s = alloc_level(p, F, false)) != TL_OK ||
       (s = alloc_n(p, &p->bar, BAR_WORDS)) != TL_OK ||
       (s = alloc_n(p, &p->red, (size_t)RS_N * p->red_stride)) != TL_OK ||
@@ -916,17 +971,19 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
   int dev = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)solve_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             STAGE_BYTES);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_batch_kernel, NT, STAGE_BYTES);
-  if (e != cudaSuccess || per_sm < 1) {
+  b->max_coop = 1 << 30;
+  for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+    e = cudaFuncSetAttribute(batch_kernel_for(m), cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_for(m), NT, STAGE_BYTES);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    b->max_coop_v[m] = per_sm * b->nsm;
+    b->max_coop = std::min(b->max_coop, b->max_coop_v[m]);
+  }
+  if (e != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return TL_ECUDA;
   }
-  b->max_coop = per_sm * b->nsm;
   b->cap = std::min(max_jobs, b->max_coop);
   const size_t targs = (size_t)b->R * b->cap * sizeof(SolveArgs), ttab = sizeof(BatchTable);
   e = cudaMalloc(&b->d_tab, ttab);
@@ -1023,6 +1080,7 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
   std::vector<long long> w;
   std::vector<int> capb;
   int nj = 0;
+  int seen = 0;  // bit 0: a plain FP64 job, bit 1: a refined job in this round
   for (size_t id = 0; id < b->jobs.size(); ++id) {
     auto& j = b->jobs[id];
     if (!j.active) continue;
@@ -1045,13 +1103,15 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
       ++ns;
     }
     tab.nsolves[nj] = ns;
+    seen |= 1 << pmode_of(j.p->cfg);
     capb.push_back(j.p->red_stride);
     w.push_back(work);
     ++nj;
   }
   if (active_out) *active_out = nj;
   std::vector<int> nb;
-  allocate_blocks(w, capb, b->max_coop, nb);
+  const int mode = seen == 1 ? 0 : (seen == 2 ? 1 : 2);
+  allocate_blocks(w, capb, b->max_coop_v[mode], nb);
   // tile each solve for the slice it got: few large tiles in a crowded round,
   // many in a sparse one (tiling only sets how the slice walks the mesh)
   {
@@ -1063,8 +1123,12 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
       choose_tiling(tmpc, nb[q], 1);
       choose_tiling(tmpf, nb[q], 1);
       SolveArgs* args = b->h_args + (size_t)q * b->R;
-      for (int sv = 0; sv < tab.nsolves[q]; ++sv)
+      const Tiling twc = j.p->C.wide ? wide_tiling(tmpc.g, nb[q]) : Tiling{};
+      const Tiling twf = j.p->Fi.wide ? wide_tiling(tmpf.g, nb[q]) : Tiling{};
+      for (int sv = 0; sv < tab.nsolves[q]; ++sv) {
         args[sv].t = (args[sv].level == 1) ? tmpf.t : tmpc.t;
+        args[sv].tw = (args[sv].level == 1) ? twf : twc;
+      }
       ++q;
     }
   }
@@ -1081,8 +1145,8 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
   const BatchTable* tp = b->d_tab;
   const SolveArgs* ap = b->d_args;
   void* kargs[] = {(void*)&tp, (void*)&ap};
-  e = cudaLaunchCooperativeKernel((const void*)solve_batch_kernel, dim3(tab.first[nj]), dim3(NT), kargs,
-                                  STAGE_BYTES, b->stream);
+  e = cudaLaunchCooperativeKernel(batch_kernel_for(mode), dim3(tab.first[nj]), dim3(NT), kargs, STAGE_BYTES,
+                                  b->stream);
   if (e != cudaSuccess) return cuda_status(e);
   b->launches++;
   b->rounds++;

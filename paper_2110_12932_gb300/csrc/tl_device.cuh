@@ -143,9 +143,24 @@ __device__ inline bool grid_sync(const Barrier& b, const VGrid& vg, unsigned lon
 // equal totals.  On GB300 an FP64 warp instruction occupies the SM
 // sub-partition's FP64 unit for ~64 cycles, so FP32 solves reduce in FP32.
 // ---------------------------------------------------------------------------
+// One shared scratch for all reductions of a kernel (a static array in a
+// template would be allocated once per instantiation): per-warp partials of up
+// to RED_NV values, the block totals, and a few scalars (red_scalars) that the
+// CG broadcasts after a reduction.  The users never overlap in time.
+constexpr int RED_NV = 3;
+__device__ inline double* red_scratch() {
+  __shared__ double buf[RED_NV * 32 + RED_NV + 4];
+  return buf;
+}
+template <typename T>
+__device__ inline T* red_scalars() {
+  return reinterpret_cast<T*>(red_scratch() + RED_NV * 32 + RED_NV);
+}
+
 template <int NV, typename T>
 __device__ inline void block_reduce_store(T (&v)[NV], T* slots, int stride, const VGrid& vg) {
-  __shared__ T s_part[NV][32];
+  static_assert(NV <= RED_NV && sizeof(T) <= sizeof(double), "reduction scratch");
+  T (*s_part)[32] = reinterpret_cast<T (*)[32]>(red_scratch());
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -168,18 +183,48 @@ __device__ inline void block_reduce_store(T (&v)[NV], T* slots, int stride, cons
   __syncthreads();
 }
 
+// Every thread of the block loads up to four slots per value at once (one L2
+// round trip for grids of up to 4 x blockDim blocks), then the block sums them
+// in a fixed tree.
 template <int NV, typename T>
 __device__ inline void grid_total(const T* slots, int stride, T (&out)[NV], const VGrid& vg) {
-  __shared__ T s_tot[NV];
+  static_assert(NV <= RED_NV && sizeof(T) <= sizeof(double), "reduction scratch");
+  T (*s_part)[32] = reinterpret_cast<T (*)[32]>(red_scratch());
+  T* s_tot = reinterpret_cast<T*>(red_scratch() + RED_NV * 32);
+  constexpr int U = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  T x[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) x[a] = T(0);
+  for (int s0 = threadIdx.x; s0 < vg.nblk; s0 += U * blockDim.x) {
+    T v[NV][U];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int s = s0 + u * blockDim.x;
+        v[a][u] = s < vg.nblk ? __ldcg(slots + (size_t)a * stride + s) : T(0);
+      }
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int u = 0; u < U; ++u) x[a] += v[a][u];
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x[a] += __shfl_down_sync(0xffffffffu, x[a], o);
+    if (lane == 0) s_part[a][warp] = x[a];
+  }
+  __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-      T x = T(0);
-      for (int s = lane; s < vg.nblk; s += 32) x += __ldcg(slots + (size_t)a * stride + s);
+      T y = lane < nwarps ? s_part[a][lane] : T(0);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) s_tot[a] = x;
+      for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+      if (lane == 0) s_tot[a] = y;
     }
   }
   __syncthreads();

@@ -104,6 +104,8 @@ void box_constants(const Grid3& g, SolveArgs& a) {
     a.Kc[m] = 0.125 * (ka[0][mx] * mu[1][my] * mu[2][mz] + mu[0][mx] * ka[1][my] * mu[2][mz] +
                        mu[0][mx] * mu[1][my] * ka[2][mz]);
   }
+  to_pair_form(a.Mc);
+  to_pair_form(a.Kc);
   a.Md = (h[0] / 3.0) * (h[1] / 3.0) * (h[2] / 3.0);
   a.Kd = (1.0 / h[0]) * (h[1] / 3.0) * (h[2] / 3.0) + (h[0] / 3.0) * (1.0 / h[1]) * (h[2] / 3.0) +
          (h[0] / 3.0) * (h[1] / 3.0) * (1.0 / h[2]);
@@ -159,9 +161,9 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
+    e = cudaFuncSetAttribute((const void*)solve_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel, NT, STAGE_BYTES);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)solve_kernel<0>, NT, STAGE_BYTES);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return TL_ECUDA;
@@ -239,7 +241,7 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
     return TL_ECUDA;
   }
   void* args[] = {(void*)&a};
-  e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(grid), dim3(NT), args, STAGE_BYTES, st);
+  e = cudaLaunchCooperativeKernel((const void*)solve_kernel<0>, dim3(grid), dim3(NT), args, STAGE_BYTES, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   int status = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&status, words + BAR_STATUS, sizeof(int), cudaMemcpyDeviceToHost);

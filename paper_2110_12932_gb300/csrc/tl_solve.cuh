@@ -243,6 +243,16 @@ struct DevStats {
   int max_iters[2], last_iters[2];
 };
 
+// Converts eight Hadamard factors (index = x mode + 2 y mode + 4 z mode) to
+// the pair form the apply uses: (f[2m], f[2m+1]) -> (f[2m] + f[2m+1], f[2m] - f[2m+1]).
+__host__ __device__ inline void to_pair_form(double (&f)[8]) {
+  for (int m4 = 0; m4 < 4; ++m4) {
+    const double e = f[2 * m4], o = f[2 * m4 + 1];
+    f[2 * m4] = e + o;
+    f[2 * m4 + 1] = e - o;
+  }
+}
+
 struct Tiling {
   int ex, ey, ez;     // tile size in elements
   int ntx, nty, ntz;  // tile counts
@@ -308,8 +318,10 @@ struct SolveArgs {
   Material mat;
   double dt, tol, tol_inner;
   int max_iter, max_outer, precision;
+  int wide;        // refined path: inner CG on wide tiles (two-phase pcg2, tiling tw)
+  Tiling tw;
   int energy, update_state, level;
-  double Mc[8], Kc[8], Md, Kd, vol8;
+  double Mc[8], Kc[8], Md, Kd, vol8;  // Mc, Kc: eigenvalue factors in pair form (to_pair_form)
   double Mhat[64], Khat[64];
   Barrier bar;
   double* red;   // reduction slots [RS_N][red_stride]
@@ -325,7 +337,10 @@ enum TraceMark : int {
   TR_START = 0, TR_PHASE0 = 1, TR_RHS = 2, TR_RESID = 3, TR_CG_PASS = 4, TR_OUTER_INIT = 5,
   TR_OUTER_APPLY = 6, TR_OUTER_END = 7, TR_UPDATE = 8, TR_END = 9, TR_CG_APPLY = 10,
   TR_RR = 11,      // value marker: second word = <r,r> of the pass (IEEE double bits)
-  TR_BREAK = 12    // value marker: CG stopped on a non-positive recurrence term
+  TR_BREAK = 12,   // value marker: CG stopped on a non-positive recurrence term
+  TR_CG_UPDATE = 13,
+  TR_CG_U0 = 14,   // block 0 starts its share of a CG update phase
+  TR_CG_U1 = 15    // ... and finished it (before the block reduction)
 };
 constexpr int TRACE_CAP = 1024;
 
@@ -375,13 +390,16 @@ struct ApplySmem {
 // slots raw[s * NT], and finish(n, i, j, k, owned, raw) turns them into x_n
 // (called exactly once per window node, after the copies landed).  The
 // copies for layer k+2 are issued while layer k is being processed.
-// lam(e, l8) fills the eight Hadamard eigenvalues of element e.
+// lam(e, l8) fills the eight Hadamard eigenvalues of element e in pair form:
+// l8[2 m4] = lam[2 m4] + lam[2 m4 + 1], l8[2 m4 + 1] = lam[2 m4] - lam[2 m4 + 1]
+// (m4 = the y, z mode; the pair differs in the x mode).
 // Element data (the eigenvalues' inputs) are either loaded into registers at
 // the start of each layer (LAM_STAGED false: lam(e, nullptr, l8) reads
 // global memory) or staged one layer ahead in slots NRAW.. of the same ring
 // (LAM_STAGED true: lam_fetch(e, slots) issues the copies, lam(e, slots, l8)
-// builds the eigenvalues).  NS = slots per buffer and thread.
-template <typename R, bool LAM_STAGED, int NS, class Fetch, class Finish, class LamFetch, class Lam, class Emit>
+// builds the eigenvalues; slots start at LSLOT).  NS = slots per buffer and thread.
+template <typename R, bool LAM_STAGED, int NS, int LSLOT = NRAW, class Fetch, class Finish, class LamFetch, class Lam,
+          class Emit>
 __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, ApplySmem<R>& sm, R* stage,
                                   Fetch fetch, Finish finish, LamFetch lam_fetch, Lam lam, Emit emit) {
   const int tid = threadIdx.x;
@@ -410,7 +428,7 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
   cp_async_commit();
   if (has_w) fetch(wnode + (ke0 + 1) * S, wi, wj, ke0 + 1, owned_at(ke0 + 1), raw1);
   // element layer k sits in the buffer of node layer k + 1
-  if (LAM_STAGED && has_e) lam_fetch(welem + ke0 * Se, raw1 + NRAW * NT);
+  if (LAM_STAGED && has_e) lam_fetch(welem + ke0 * Se, raw1 + LSLOT * NT);
   cp_async_commit();
   cp_async_wait<1>();
   int cur = 0;
@@ -436,8 +454,8 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
       sm.a.Z[1][wlj][wli] = lo - hi;
     }
     if (LAM_STAGED && has_e) {
-      lam(welem + ke * Se, rnext + NRAW * NT, l8);
-      if (ke + 1 < ke1) lam_fetch(welem + (ke + 1) * Se, rfree + NRAW * NT);
+      lam(welem + ke * Se, rnext + LSLOT * NT, l8);
+      if (ke + 1 < ke1) lam_fetch(welem + (ke + 1) * Se, rfree + LSLOT * NT);
     }
     cp_async_commit();
     __syncthreads();
@@ -451,15 +469,15 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
       }
     }
     __syncthreads();
-    // stage 3: per element, x-direction, eigenvalue scaling, x-backward
+    // stage 3: per element, x-direction, eigenvalue scaling and x-backward in
+    // one step: with the pair form c = lam_even + lam_odd, d = lam_even - lam_odd,
+    // left = lam_even (a + b) + lam_odd (a - b) = c a + d b, right = d a + c b
     if (has_e) {
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) {
         R a = sm.Y[m4][ely][elx], b = sm.Y[m4][ely][elx + 1];
-        R s = a + b;
-        R yd = l8[2 * m4 + 1] * (a - b);
-        sm.XL[m4][ely][elx] = fma(l8[2 * m4], s, yd);
-        sm.XR[m4][ely][elx] = fma(l8[2 * m4], s, -yd);
+        sm.XL[m4][ely][elx] = fma(l8[2 * m4], a, l8[2 * m4 + 1] * b);
+        sm.XR[m4][ely][elx] = fma(l8[2 * m4 + 1], a, l8[2 * m4] * b);
       }
     }
     __syncthreads();
@@ -607,7 +625,7 @@ struct CGBufs {
 template <typename R, bool LAM_STAGED, int NS, class LamFetch, class Lam>
 __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* stage, const CGBufs<R>& c,
                     LamFetch lam_fetch, Lam lam8, R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
-  __shared__ R s_scal[3];
+  R* s_scal = red_scalars<R>();  // broadcast of the step scalars
   const Grid3 g = a.g;
   const Tiling t = a.t;
   const int nn = g.nnx * g.nny * g.nnz;
@@ -620,6 +638,8 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
   for (int k = -1; k < max_iter; ++k) {
     const int cur = k < 0 ? 0 : (k & 1), nxt = k < 0 ? 0 : (cur ^ 1);
     const bool first = k == 0;
+    // reduction rows alternate by pass (see pcg2)
+    R* rslots = red + (((k + 1) & 1) ? RS_ES : RS_PQ) * a.red_stride;
     // pass pointers chosen by selects (no dynamic indexing into the struct)
     const R* r_cur = cur ? c.r[1] : c.r[0];
     const R* p_cur = cur ? c.p[1] : c.p[0];
@@ -711,12 +731,12 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
     tr.mark(TR_CG_APPLY);
     {
       R v[3] = {sg, vd, vr};
-      block_reduce_store<3>(v, red + RS_PQ * a.red_stride, a.red_stride, vg);
+      block_reduce_store<3>(v, rslots, a.red_stride, vg);
     }
     if (!grid_sync(a.bar, vg)) return -1;
     tr.mark(TR_CG_PASS);
     R tot[3];
-    grid_total<3>(red + RS_PQ * a.red_stride, a.red_stride, tot, vg);
+    grid_total<3>(rslots, a.red_stride, tot, vg);
     tr.value(TR_RR, (double)tot[2]);
     if (k >= 0) {
       ++it;
@@ -749,6 +769,490 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
   return conv ? 1 : 0;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 apply for large patches.  Tiles of up to AX x AY x ez elements; warp w
+// of a block handles window node row w (w <= ey) and, for w < ey, element row
+// w; lane l handles window columns 2l and 2l + 1 and the two elements that
+// start there (lane 31 also column AX).  Within a row the x-direction stays in
+// registers and warp shuffles, the neighbouring node row passes through
+// shared memory, and an element layer takes two block barriers.  Inputs
+// (window values and element data) arrive by cp.async two layers ahead in a
+// four-stage per-thread ring.  Emits like apply_tile: emit(n, slot, y, x_n).
+// ---------------------------------------------------------------------------
+constexpr int AX = 64, AY = 4;
+constexpr int WSLOTS = 8;    // ring slots per stage: u(c0), u(c1), u(AX), s0, k0, s1, k1, spare
+constexpr int WSTAGES = 4;
+static_assert(NT == 32 * (AY + 1), "one warp per window row");
+static_assert(WSTAGES * WSLOTS * NT * 4 <= STAGE_BYTES, "staging ring fits the dynamic shared memory");
+
+struct WideSmem {
+  float ZS[AY + 1][AX + 2];   // z-sum and z-difference of each window column (current layer pair)
+  float ZD[AY + 1][AX + 2];
+  float R1s[AY][AX + 2];      // y-backward of element row w to node row w + 1 (z-sum / z-difference)
+  float R1d[AY][AX + 2];
+};
+
+template <class Emit>
+__device__ inline void apply_tile_wide(const Grid3& g, const Tiling& t, int tile, WideSmem& sm, float* ring,
+                                       const float* u, const float* sk, const float (&mp)[8], const float (&kp)[8],
+                                       Emit emit) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int txy = t.ntx * t.nty;
+  const int tiz = tile / txy, trem = tile - tiz * txy;
+  const int tiy = trem / t.ntx, tix = trem - tiy * t.ntx;
+  const int ie0 = tix * AX, je0 = tiy * AY, ke0 = tiz * t.ez;
+  const int ex = min(AX, g.nx - ie0), ey = min(AY, g.ny - je0), ke1 = min(ke0 + t.ez, g.nz);
+  const int S = g.nnx * g.nny, Se = g.nx * g.ny, ne = Se * g.nz;
+  const bool row_on = wy <= ey;                 // this warp has a window node row
+  const bool has_el = wy < ey;                  // ... and an element row
+  const int c0 = 2 * lane, c1 = c0 + 1;
+  const bool v0 = row_on && c0 <= ex, v1 = row_on && c1 <= ex;
+  const bool vx = row_on && lane == 31 && ex == AX;  // column AX
+  const bool ok0 = has_el && c0 < ex, ok1 = has_el && c1 < ex;
+  const int nb = ie0 + g.nnx * (je0 + (row_on ? wy : 0));
+  const int eb = ie0 + g.nx * (je0 + (has_el ? wy : 0)) + c0;
+  // exchange slots: the tile's high-y node row; column AX is on the high-x
+  // face only when another tile follows in x (a ragged last column is the
+  // plate's own boundary)
+  const int ys = (wy == ey && je0 + ey < g.ny) ? 2 : 0;
+  const int xs = (ie0 + AX < g.nx) ? 1 : 0;
+  float* my = ring + threadIdx.x;
+  auto issue = [&](int st) {  // stage st: u at node layer ke0 + st, s/k at element layer ke0 + st
+    float* r = my + (st & (WSTAGES - 1)) * WSLOTS * NT;
+    const int kn = ke0 + st;
+    if (kn <= ke1) {
+      const int b = nb + S * kn;
+      if (v0) cp_async<4>(r, u + b + c0); else r[0] = 0.0f;
+      if (v1) cp_async<4>(r + NT, u + b + c1); else r[NT] = 0.0f;
+      if (vx) cp_async<4>(r + 2 * NT, u + b + AX); else r[2 * NT] = 0.0f;
+    }
+    if (kn < ke1) {
+      const int e = eb + Se * kn;
+      if (ok0) {
+        cp_async<4>(r + 3 * NT, sk + e);
+        cp_async<4>(r + 4 * NT, sk + ne + e);
+      } else {
+        r[3 * NT] = 0.0f;
+        r[4 * NT] = 0.0f;
+      }
+      if (ok1) {
+        cp_async<4>(r + 5 * NT, sk + e + 1);
+        cp_async<4>(r + 6 * NT, sk + ne + e + 1);
+      } else {
+        r[5 * NT] = 0.0f;
+        r[6 * NT] = 0.0f;
+      }
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+  issue(2);
+  cp_async_wait<2>();
+  float uL[3];
+  {
+    const float* r = my;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) uL[c] = r[c * NT];
+  }
+  float carry[3] = {0.0f, 0.0f, 0.0f};
+  for (int ke = ke0; ke < ke1; ++ke) {
+    const int j = ke - ke0;
+    issue(j + 3);
+    cp_async_wait<2>();  // stages j and j + 1 have landed
+    const float* rc = my + (j & (WSTAGES - 1)) * WSLOTS * NT;
+    const float* rn = my + ((j + 1) & (WSTAGES - 1)) * WSLOTS * NT;
+    float uH[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) uH[c] = rn[c * NT];
+    const float s0 = rc[3 * NT], k0 = rc[4 * NT], s1 = rc[5 * NT], k1 = rc[6 * NT];
+    // z-direction per own column
+    float zs[3], zd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      zs[c] = uL[c] + uH[c];
+      zd[c] = uL[c] - uH[c];
+    }
+    if (row_on) {
+      *reinterpret_cast<float2*>(&sm.ZS[wy][c0]) = make_float2(zs[0], zs[1]);
+      *reinterpret_cast<float2*>(&sm.ZD[wy][c0]) = make_float2(zd[0], zd[1]);
+      if (lane == 31) {
+        sm.ZS[wy][AX] = zs[2];
+        sm.ZD[wy][AX] = zd[2];
+      }
+    }
+    __syncthreads();
+    // elements of row wy: y-forward, x-direction with scaling, y-backward
+    float r0s[3] = {0.0f, 0.0f, 0.0f}, r0d[3] = {0.0f, 0.0f, 0.0f};
+    if (has_el) {
+      const float2 ns = *reinterpret_cast<const float2*>(&sm.ZS[wy + 1][c0]);
+      const float2 nd = *reinterpret_cast<const float2*>(&sm.ZD[wy + 1][c0]);
+      float s2 = __shfl_down_sync(FULL, zs[0], 1), d2 = __shfl_down_sync(FULL, zd[0], 1);
+      float ns2 = __shfl_down_sync(FULL, ns.x, 1), nd2 = __shfl_down_sync(FULL, nd.x, 1);
+      if (lane == 31) {
+        s2 = zs[2];
+        d2 = zd[2];
+        ns2 = sm.ZS[wy + 1][AX];
+        nd2 = sm.ZD[wy + 1][AX];
+      }
+      const float S0[3] = {zs[0], zs[1], s2}, D0[3] = {zd[0], zd[1], d2};
+      const float S1[3] = {ns.x, ns.y, ns2}, D1[3] = {nd.x, nd.y, nd2};
+      float Y[4][3];  // (y, z) mode m4 = my + 2 mz, per column
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Y[0][c] = S0[c] + S1[c];
+        Y[1][c] = S0[c] - S1[c];
+        Y[2][c] = D0[c] + D1[c];
+        Y[3][c] = D0[c] - D1[c];
+      }
+      float B[4][3];
+#pragma unroll
+      for (int m4 = 0; m4 < 4; ++m4) {
+        const float la = fmaf(s0, mp[2 * m4], k0 * kp[2 * m4]), lb = fmaf(s0, mp[2 * m4 + 1], k0 * kp[2 * m4 + 1]);
+        const float ma = fmaf(s1, mp[2 * m4], k1 * kp[2 * m4]), mb = fmaf(s1, mp[2 * m4 + 1], k1 * kp[2 * m4 + 1]);
+        const float a0 = Y[m4][0], a1 = Y[m4][1], a2 = Y[m4][2];
+        B[m4][0] = fmaf(la, a0, lb * a1);
+        B[m4][1] = fmaf(lb, a0, la * a1) + fmaf(ma, a1, mb * a2);
+        B[m4][2] = fmaf(mb, a1, ma * a2);
+      }
+      float r1s[3], r1d[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r0s[c] = B[0][c] + B[1][c];
+        r1s[c] = B[0][c] - B[1][c];
+        r0d[c] = B[2][c] + B[3][c];
+        r1d[c] = B[2][c] - B[3][c];
+      }
+      // column 2l + 2 is the next lane's first column
+      const float t0 = __shfl_up_sync(FULL, r0s[2], 1), t1 = __shfl_up_sync(FULL, r0d[2], 1);
+      const float t2 = __shfl_up_sync(FULL, r1s[2], 1), t3 = __shfl_up_sync(FULL, r1d[2], 1);
+      if (lane > 0) {
+        r0s[0] += t0;
+        r0d[0] += t1;
+        r1s[0] += t2;
+        r1d[0] += t3;
+      }
+      *reinterpret_cast<float2*>(&sm.R1s[wy][c0]) = make_float2(r1s[0], r1s[1]);
+      *reinterpret_cast<float2*>(&sm.R1d[wy][c0]) = make_float2(r1d[0], r1d[1]);
+      if (lane == 31) {
+        sm.R1s[wy][AX] = r1s[2];
+        sm.R1d[wy][AX] = r1d[2];
+      }
+    }
+    __syncthreads();
+    // node row wy: own element row plus the row below, then z-backward
+    if (row_on) {
+      float cs[3] = {r0s[0], r0s[1], r0s[2]}, cd[3] = {r0d[0], r0d[1], r0d[2]};
+      if (wy > 0) {
+        const float2 ps = *reinterpret_cast<const float2*>(&sm.R1s[wy - 1][c0]);
+        const float2 pd = *reinterpret_cast<const float2*>(&sm.R1d[wy - 1][c0]);
+        cs[0] += ps.x;
+        cs[1] += ps.y;
+        cd[0] += pd.x;
+        cd[1] += pd.y;
+        if (lane == 31) {
+          cs[2] += sm.R1s[wy - 1][AX];
+          cd[2] += sm.R1d[wy - 1][AX];
+        }
+      }
+      float out[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        out[c] = carry[c] + (cs[c] + cd[c]);
+        carry[c] = cs[c] - cd[c];
+      }
+      const int b = nb + S * ke;
+      if (v0) emit(b + c0, ys, out[0], uL[0]);
+      if (v1) emit(b + c1, ys, out[1], uL[1]);
+      if (vx) emit(b + AX, ys | xs, out[2], uL[2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) uL[c] = uH[c];
+  }
+  // top node layer of the tile: only the contributions of element layer ke1 - 1
+  if (row_on) {
+    const int zs4 = ke1 < g.nz ? 4 : 0;
+    const int b = nb + S * ke1;
+    if (v0) emit(b + c0, ys | zs4, carry[0], uL[0]);
+    if (v1) emit(b + c1, ys | zs4, carry[1], uL[1]);
+    if (vx) emit(b + AX, ys | xs | zs4, carry[2], uL[2]);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+struct WideCoef {
+  float mp[8], kp[8];  // eigenvalue factors (pair form) of the mass and stiffness parts
+};
+
+// One wide tile of w = A z for the two-phase CG: stores the partials (own and
+// exchange) and returns the tile's sum of z_n times its partials.  Not
+// inlined: the tile loop gets the kernel's whole register budget.
+static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Tiling t, int tile, WideSmem* sm, float* ring,
+                                                  const float* z, const float* sk, const WideCoef cf, float* q,
+                                                  float* X) {
+  const int nn = g.nnx * g.nny * g.nnz;
+  float vd = 0.0f;
+  auto emit = [&](int n, int slot, float y, float xin) {
+    store_partial(q, X, nn, n, slot, y, false);
+    vd = fmaf(xin, y, vd);
+  };
+  apply_tile_wide(g, t, tile, *sm, ring, z, sk, cf.mp, cf.kp, emit);
+  return vd;
+}
+
+// Vectors of the two-phase CG (pcg2).  Only owners touch a node in the update
+// phase and the apply reads only u, so nothing is double-buffered.
+template <typename R>
+struct CGVecs {
+  R* x;           // solution, updated in place
+  R* r;           // residual
+  R* p;           // search direction
+  R* s;           // s = A p, kept by recurrence
+  R* z;           // z = D^-1 r, the apply's input (0 on Dirichlet nodes)
+  R* q;           // own partial of w = A u
+  R* X;           // NXB exchange arrays of w's partials
+  const R* dinv;  // Jacobi inverse diagonal, 0 on Dirichlet nodes
+};
+
+// floor(n / d) for 0 <= n < 2^31 and a runtime divisor d >= 1, as the high
+// 64 bits of n * M with M = floor(2^64 / d) + 1 (M = 2^64 / d when d is a
+// power of two): the error n (d - 2^64 mod d) / (d 2^64) < 1/d cannot carry
+// the quotient past an integer.  div_magic(d) computes M; d = 1 returns n.
+__device__ inline unsigned long long div_magic(int d) {
+  return d == 1 ? 0ull : ~0ull / (unsigned long long)d + 1ull;
+}
+__device__ inline int div_by(int n, int d, unsigned long long M) {
+  return d == 1 ? n : (int)__umul64hi((unsigned long long)n, M);
+}
+
+template <typename R> struct Vec16;
+template <> struct Vec16<float> { using T = float4; };
+template <> struct Vec16<double> { using T = double2; };
+
+template <typename R>
+struct Sums2 { R a, b; };
+
+// The update phase of the two-phase CG over all nodes, flat: each lane takes
+// 16 bytes of every array at once (VEC consecutive nodes, vector loads and
+// stores), so every array streams at full line width whatever the row
+// length.  The lane's first node gets its (i, j, k) from two exact
+// multiply-high divisions, the others by increments.  A node's low tile faces
+// decide which exchange partials its owner adds; the y-face partial (a
+// quarter of all nodes on wide tiles) is loaded with the main inputs, the
+// rarer x, z and edge partials afterwards.  k < 0: z = D^-1 r only.
+// Dirichlet nodes (dinv = 0) keep their r, p, s, x and get z = 0.  Returns the
+// thread's sums of <r,z> and <r,r>.  Not inlined: it gets the kernel's whole
+// register budget.
+template <typename R>
+static __device__ __noinline__ Sums2<R> cg_update(const Grid3 g, const Tiling t, const CGVecs<R> c, R alpha, R beta,
+                                                  int k, int gtid, int gstride) {
+  using V = typename Vec16<R>::T;
+  constexpr int VEC = 16 / sizeof(R);
+  const int nn = g.nnx * g.nny * g.nnz;
+  const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny), mz = div_magic(t.ez);
+  const bool init = k < 0, first = k == 0;
+  const int ngroups = (nn + VEC - 1) / VEC;
+  R vgam = R(0), vrr = R(0);
+  auto load = [&](const R* a, int n0, int cnt, R (&o)[VEC]) {
+    if (cnt == VEC) {
+      const V v = __ldcg(reinterpret_cast<const V*>(a + n0));
+      const R* e = reinterpret_cast<const R*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = e[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = m < cnt ? __ldcg(a + n0 + m) : R(0);
+    }
+  };
+  auto store = [&](R* a, int n0, int cnt, const R (&o)[VEC]) {
+    if (cnt == VEC) {
+      V v;
+      R* e = reinterpret_cast<R*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) e[m] = o[m];
+      *reinterpret_cast<V*>(a + n0) = v;
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m)
+        if (m < cnt) a[n0 + m] = o[m];
+    }
+  };
+  for (int q = gtid; q < ngroups; q += gstride) {
+    const int n0 = q * VEC;
+    const int cnt = min(VEC, nn - n0);
+    R dv[VEC], rk[VEC];
+    load(c.dinv, n0, cnt, dv);
+    load(c.r, n0, cnt, rk);
+    if (init) {
+      R zn[VEC];
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) {
+        zn[m] = dv[m] * rk[m];
+        if (dv[m] != R(0)) {
+          vgam = fma(rk[m], zn[m], vgam);
+          vrr = fma(rk[m], rk[m], vrr);
+        }
+      }
+      store(c.z, n0, cnt, zn);
+      continue;
+    }
+    // low tile faces of the group's nodes
+    int lf[VEC];
+    {
+      const int row = div_by(n0, g.nnx, mx);
+      int i = n0 - row * g.nnx;
+      int kz = div_by(row, g.nny, my);
+      int j = row - kz * g.nny;
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) {
+        const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
+        const bool lz = kz > 0 && kz < g.nz && kz - div_by(kz, t.ez, mz) * t.ez == 0;
+        lf[m] = m < cnt ? low_faces(g, t, i, ly, lz) : 0;
+        if (++i == g.nnx) {
+          i = 0;
+          if (++j == g.nny) {
+            j = 0;
+            ++kz;
+          }
+        }
+      }
+    }
+    R w[VEC], xk[VEC], pk[VEC], sk[VEC], wy[VEC];
+    load(c.q, n0, cnt, w);
+    load(c.x, n0, cnt, xk);
+    if (!first) {
+      load(c.p, n0, cnt, pk);
+      load(c.s, n0, cnt, sk);
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) pk[m] = sk[m] = R(0);
+    }
+#pragma unroll
+    for (int m = 0; m < VEC; ++m) wy[m] = (lf[m] & 2) ? __ldcg(c.X + 1 * nn + n0 + m) : R(0);
+    R pn[VEC], sn[VEC], rn[VEC], xn[VEC], zn[VEC];
+#pragma unroll
+    for (int m = 0; m < VEC; ++m) {
+      pn[m] = pk[m];
+      sn[m] = sk[m];
+      rn[m] = rk[m];
+      xn[m] = xk[m];
+      zn[m] = R(0);
+      if (m >= cnt || dv[m] == R(0)) continue;
+      const int n = n0 + m;
+      const int f = lf[m];
+      R wv = w[m];
+      if (f) {  // neighbours' partials, in the order gather_partials uses
+        if (f & 1) wv += __ldcg(c.X + 0 * nn + n);
+        if (f & 2) wv += wy[m];
+        if ((f & 3) == 3) wv += __ldcg(c.X + 2 * nn + n);
+        if (f & 4) wv += __ldcg(c.X + 3 * nn + n);
+        if ((f & 5) == 5) wv += __ldcg(c.X + 4 * nn + n);
+        if ((f & 6) == 6) wv += __ldcg(c.X + 5 * nn + n);
+        if (f == 7) wv += __ldcg(c.X + 6 * nn + n);
+      }
+      const R z0 = dv[m] * rk[m];
+      pn[m] = first ? z0 : fma(beta, pk[m], z0);
+      sn[m] = first ? wv : fma(beta, sk[m], wv);
+      rn[m] = fma(-alpha, sn[m], rk[m]);
+      zn[m] = dv[m] * rn[m];
+      xn[m] = fma(alpha, pn[m], xk[m]);
+      vgam = fma(rn[m], zn[m], vgam);
+      vrr = fma(rn[m], rn[m], vrr);
+    }
+    store(c.p, n0, cnt, pn);
+    store(c.s, n0, cnt, sn);
+    store(c.r, n0, cnt, rn);
+    store(c.x, n0, cnt, xn);
+    store(c.z, n0, cnt, zn);
+  }
+  return Sums2<R>{vgam, vrr};
+}
+
+// The same single-reduction recurrences as pcg1, in two phases per iteration:
+//   U  (owners, one pass over the nodes): w = own + neighbours' partials of
+//      A u;  p = u + beta p;  s = w + beta s;  x += alpha p;  r -= alpha s;
+//      u = D^-1 r;  block sums of <r,u> and <r,r>;
+//   A  (tiles): partials of w = A u on each tile's window; block sums of
+//      <w,u> (linear in the partials);
+// with a grid barrier after each phase and one reduction of the three sums.
+// The update streams six inputs and five outputs per node without window
+// re-reads, and the apply stages a single input per window node.  Dirichlet
+// nodes (dinv = 0) keep r = 0 and u = 0.  Starts from the residual in c.r
+// and x = c.x; stops when <r,r> <= thresh or after max_iter iterations.
+// Returns 1 converged, 0 capped, -1 barrier failure; *iters gets the count.
+// apply_z(tile) applies the operator to c.z on one tile of the tiling t (whose
+// faces also decide which exchange partials an owner gathers), stores the
+// partials in c.q / c.X and returns the tile's share of <w, z>.
+template <typename R, class ApplyZ>
+__device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const CGVecs<R>& c, ApplyZ apply_z,
+                    R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
+  R* s_scal = red_scalars<R>();  // broadcast of the step scalars
+  const Grid3 g = a.g;
+  const int nn = g.nnx * g.nny * g.nnz;
+  const int ntiles = t.ntx * t.nty * t.ntz;
+  R alpha = R(0), beta = R(0), gamma = R(0);
+  int it = 0;
+  bool conv = false;
+  for (int k = -1; k < max_iter; ++k) {
+    // reduction rows alternate by iteration: a block that runs ahead into the
+    // next iteration never overwrites sums another block is still reading
+    R* rslots = red + (((k + 1) & 1) ? RS_ES : RS_PQ) * a.red_stride;
+    // ---- U: owner update of every node
+    tr.mark(TR_CG_U0);
+    const Sums2<R> us = cg_update<R>(g, t, c, alpha, beta, k, vg.bid * blockDim.x + threadIdx.x,
+                                     vg.nblk * blockDim.x);
+    tr.mark(TR_CG_U1);
+    const R vgam = us.a, vrr = us.b;
+    {
+      R v[2] = {vgam, vrr};
+      block_reduce_store<2>(v, rslots + a.red_stride, a.red_stride, vg);
+    }
+    if (!grid_sync(a.bar, vg)) return -1;
+    tr.mark(TR_CG_UPDATE);
+    // ---- A: partials of w = A u, block sums of <w, u>
+    R vd = R(0);
+    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) vd += apply_z(tile);
+    tr.mark(TR_CG_APPLY);
+    {
+      R v[1] = {vd};
+      block_reduce_store<1>(v, rslots, a.red_stride, vg);
+    }
+    if (!grid_sync(a.bar, vg)) return -1;
+    tr.mark(TR_CG_PASS);
+    R tot[3];  // <w,u>, <r,u>, <r,r>
+    grid_total<3>(rslots, a.red_stride, tot, vg);
+    tr.value(TR_RR, (double)tot[2]);
+    if (k >= 0) {
+      ++it;
+      if (tot[2] <= thresh) {
+        conv = true;
+        break;
+      }
+    }
+    if (threadIdx.x == 0) {
+      const R gn = tot[1], dn = tot[0];
+      R b = k < 0 ? R(0) : gn / gamma;
+      R den = k < 0 ? dn : dn - b * gn / alpha;
+      s_scal[0] = gn / den;
+      s_scal[1] = b;
+      s_scal[2] = (den > R(0) && gn > R(0)) ? R(1) : R(0);
+    }
+    __syncthreads();
+    if (s_scal[2] == R(0)) {
+      tr.value(TR_BREAK, (double)tot[0]);
+      break;
+    }
+    gamma = tot[1];
+    alpha = s_scal[0];
+    beta = s_scal[1];
+    __syncthreads();
+  }
+  *iters = it;
+  return conv ? 1 : 0;
+}
+
 __device__ inline double elem_mean(const double* T, const Grid3& g, int ie, int je, int ke) {
   const int S = g.nnx * g.nny;
   const int n0 = ie + g.nnx * je + S * ke;
@@ -764,9 +1268,13 @@ __device__ inline double elem_mean(const double* T, const Grid3& g, int ie, int 
 }
 
 // One backward-Euler solve on the block range vg (all of it or one job's slice).
+// PMODE: 0 plain FP64 solves only, 1 refined solves only, 2 either (chosen by
+// a.precision at run time).  Each kernel instantiates only the paths it runs,
+// so the FP64 and FP32 loops do not share one register budget.
+template <int PMODE>
 __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   __shared__ __align__(16) unsigned char smem_raw[sizeof(ApplySmem<double>)];
-  __shared__ double s_Mhat[64], s_Khat[64];
+  static_assert(sizeof(WideSmem) <= sizeof(ApplySmem<double>), "wide-tile buffers share the apply's shared memory");
   extern __shared__ __align__(16) unsigned char stage_raw[];  // STAGE_BYTES of staged inputs
   ApplySmem<double>& sm64 = *reinterpret_cast<ApplySmem<double>*>(smem_raw);
   ApplySmem<float>& sm32 = *reinterpret_cast<ApplySmem<float>*>(smem_raw);
@@ -781,13 +1289,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   const int ne = g.nx * g.ny * g.nz;
   const int S = g.nnx * g.nny;
   const int ntiles = t.ntx * t.nty * t.ntz;
-  const bool refined = a.precision == PREC_FP32_REFINED;
+  const bool refined = PMODE == 2 ? a.precision == PREC_FP32_REFINED : PMODE == 1;
   const int gtid = vg.bid * blockDim.x + threadIdx.x;
   const int gstride = vg.nblk * blockDim.x;
-  if (threadIdx.x < 64) {
-    s_Mhat[threadIdx.x] = a.Mhat[threadIdx.x];
-    s_Khat[threadIdx.x] = a.Khat[threadIdx.x];
-  }
 
   // ---- phase 0: coefficients and eigenvalues, Dirichlet increments, load ---
   if (a.mv.active) {  // fused patch motion; independent of this (coarse) solve's data
@@ -813,9 +1317,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     const double se = rc * (1.0 / a.dt);
     a.s_e[e] = se;
     a.k_e[e] = k;
-    a.lam[e] = se * a.Mc[0];
 #pragma unroll
-    for (int m = 1; m < 8; ++m) a.lam[m * ne + e] = se * a.Mc[m] + k * a.Kc[m];
+    for (int m = 0; m < 8; ++m) a.lam[m * ne + e] = se * a.Mc[m] + k * a.Kc[m];
     if (refined) {
       a.sk32[e] = (float)se;
       a.sk32[ne + e] = (float)k;
@@ -871,9 +1374,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     };
     auto lam_k = [&](int e, const double*, double (&l8)[8]) {
       const double k = __ldcg(a.k_e + e);
-      l8[0] = 0.0;
 #pragma unroll
-      for (int m = 1; m < 8; ++m) l8[m] = k * a.Kc[m];
+      for (int m = 0; m < 8; ++m) l8[m] = k * a.Kc[m];
     };
     auto emit1 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
     auto emit2 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, true); };
@@ -919,8 +1421,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       for (int m = 0; m < 8; ++m) l8[m] = __ldcg(a.lam + m * ne + e);
     };
     auto no_fetch64 = [](int, double*) {};
-    int res = pcg1<double, false, NRAW>(a, vg, sm64, stage64, c, no_fetch64, lam64, thresh, a.max_iter, a.red, &it,
-                                        tr);
+    const int res = pcg1<double, false, NRAW>(a, vg, sm64, stage64, c, no_fetch64, lam64, thresh, a.max_iter,
+                                              a.red, &it, tr);
     if (res < 0) return;
     conv = res == 1;
   }
@@ -957,7 +1459,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       mcf[m] = (float)a.Mc[m];
       kcf[m] = (float)a.Kc[m];
     }
-    // element data staged one layer ahead: slots NRAW (s_e) and NRAW + 1 (k_e)
+    // element data staged one layer ahead: two consecutive slots (s_e, k_e)
     auto fetch32 = [&](int e, float* slots) {
       cp_async<4>(slots, a.sk32 + e);
       cp_async<4>(slots + NT, a.sk32 + ne + e);
@@ -968,8 +1470,24 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       for (int m = 0; m < 8; ++m) l8[m] = fmaf(se, mcf[m], ke * kcf[m]);
     };
     const float ti = (float)a.tol_inner;
-    int res = pcg1<float, true, NRAW + 2>(a, vg, sm32, stage32, c, fetch32, lam32, ti * ti * t32[1], a.max_iter,
-                                          a.red32, &inner, tr);
+    int res;
+    if (a.wide) {
+      CGVecs<float> c2{a.d32, a.r32, a.p0f, a.s0f, a.r32b, a.q32, a.X32, a.dinv32};
+      WideSmem* smw = reinterpret_cast<WideSmem*>(smem_raw);
+      WideCoef cf;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        cf.mp[m] = mcf[m];
+        cf.kp[m] = kcf[m];
+      }
+      auto apply_z = [&](int tile) {
+        return apply_wide_partials(g, a.tw, tile, smw, stage32, c2.z, a.sk32, cf, c2.q, c2.X);
+      };
+      res = pcg2<float>(a, vg, a.tw, c2, apply_z, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+    } else {
+      res = pcg1<float, true, NRAW + 2>(a, vg, sm32, stage32, c, fetch32, lam32, ti * ti * t32[1], a.max_iter,
+                                        a.red32, &inner, tr);
+    }
     if (res < 0) return;
     it += inner;
     ++outer;
@@ -1058,7 +1576,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
 #pragma unroll
               for (int b = 0; b < 8; ++b) {
                 int nb = (ie + (b & 1)) + g.nnx * (je + ((b >> 1) & 1)) + S * (ke + (b >> 2));
-                acc += se * s_Mhat[la * 8 + b] * __ldcg(a.u + nb) + kk * s_Khat[la * 8 + b] * __ldcg(a.T_out + nb);
+                acc += se * a.Mhat[la * 8 + b] * __ldcg(a.u + nb) + kk * a.Khat[la * 8 + b] * __ldcg(a.T_out + nb);
               }
               R_n += acc;
             }
@@ -1091,8 +1609,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
 
 // Internal linkage: every translation unit that launches the solve compiles its
 // own copy (the two-level path and the allocation-free single step).
+template <int PMODE>
 static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_kernel(const SolveArgs a) {
-  solve_body(a, VGrid{(int)blockIdx.x, (int)gridDim.x});
+  solve_body<PMODE>(a, VGrid{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // A batch of independent jobs in one cooperative launch: job j runs on the
@@ -1108,6 +1627,7 @@ struct BatchTable {
   int nsolves[BATCH_MAX];
 };
 
+template <int PMODE>
 static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_batch_kernel(const BatchTable* __restrict__ tab,
                                                                   const SolveArgs* __restrict__ jobs) {
   __shared__ SolveArgs s_args;
@@ -1133,7 +1653,7 @@ static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_batch_kernel(cons
     __syncthreads();  // the previous solve is done with s_args
     for (int w = threadIdx.x; w < (int)(sizeof(SolveArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
     __syncthreads();
-    solve_body(s_args, vg);
+    solve_body<PMODE>(s_args, vg);
     if (sv + 1 < ns) {
       if (!grid_sync(s_args.bar, vg)) return;  // the next solve reads this one's results
       if (ld_volatile_i32(s_args.bar.status) != 0) return;

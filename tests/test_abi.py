@@ -78,7 +78,7 @@ def _einval(lib, **over):
     dict(k0=-1.0), dict(rho=0.0), dict(radius=0.0), dict(tol=0.0), dict(max_iter=0),
     dict(tracks=[(0.0, 0.0, 1e-3, 1e-3, 0.8)]),          # diagonal track with the box source
     dict(tracks=[(0.0, 0.0, 1e-3, 0.0, 0.0)]),           # zero speed
-    dict(coarse_source=2), dict(precision=7),
+    dict(coarse_source=2), dict(precision=7), dict(inner_tiles=3), dict(inner_tiles=-1),
 ])
 def test_invalid_config_is_rejected_on_host(lib, over):
     assert _einval(lib, **over) == tl.TL_EINVAL

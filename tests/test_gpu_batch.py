@@ -31,10 +31,15 @@ def _mixed_jobs():
     return [a, b, c, d]
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-6)])
-def test_batch_equals_alone(precision, tol):
-    cfgs = [dict(c, precision=precision, tol=1e-12 if precision == 0 else 1e-10, tol_inner=1e-5)
-            for c in _mixed_jobs()]
+# precision None: jobs alternate between the FP64 and the refined path (the
+# batch then runs the kernel that holds both); inner_tiles 2 forces the wide
+# two-phase inner CG on these small patches.
+@pytest.mark.parametrize("precision,tol,inner_tiles", [(0, 1e-9, 0), (1, 1e-6, 1), (1, 1e-6, 2), (None, 1e-6, 0)])
+def test_batch_equals_alone(precision, tol, inner_tiles):
+    cfgs = []
+    for k, c in enumerate(_mixed_jobs()):
+        pr = (k % 2) if precision is None else precision
+        cfgs.append(dict(c, precision=pr, tol=1e-12 if pr == 0 else 1e-10, tol_inner=1e-5, inner_tiles=inner_tiles))
     steps = [12, 9, 7, 15]
     alone = []
     for c, n in zip(cfgs, steps):

@@ -190,8 +190,10 @@ def test_deterministic_reruns():
 REFINED_TOL = 1e-6
 
 
-def test_refined_single_track_tiny_against_oracle():
-    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5)
+@pytest.mark.parametrize("inner_tiles", [1, 2])
+def test_refined_single_track_tiny_against_oracle(inner_tiles):
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5,
+                             inner_tiles=inner_tiles)
     prob = tl.Problem(cfg)
     ref = TL.TwoLevel(cfg, energy=False)
     for _ in range(5):
@@ -221,8 +223,10 @@ def test_refined_matches_fp64_gpu_path_multitrack():
     p32.close()
 
 
-def test_refined_energy_identity():
-    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5)
+@pytest.mark.parametrize("inner_tiles", [1, 2])
+def test_refined_energy_identity(inner_tiles):
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5,
+                             inner_tiles=inner_tiles)
     prob = tl.Problem(cfg)
     prob.macro_steps(10)
     st = prob.stats()
@@ -230,3 +234,55 @@ def test_refined_energy_identity():
         s, l, f = (st[f"energy_{lvl}_{k}"] for k in ("stored", "laser", "flux"))
         assert abs(s - l - f) <= 1e-7 * max(abs(s), abs(l)), lvl
     prob.close()
+
+
+def test_refined_wide_tiles_ragged_against_oracle():
+    """Wide inner tiles (64 x 4 elements) on a 72 x 18 x 12 fine patch: a
+    ragged second tile in x (8 elements), a ragged last row of tiles in y (2),
+    several tiles in z."""
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5,
+                             inner_tiles=2, pNXc=12, pNYc=3, pNZc=2, r=6, m=2, macro_steps=3)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    prob.macro_steps(3)
+    ref.run(3)
+    Tf, org = prob.temperature(tl.TL_FINE)
+    Tc, _ = prob.temperature(tl.TL_COARSE)
+    assert tuple(org) == tuple(ref.origin)
+    assert rel(Tf, ref.Tf) <= REFINED_TOL and rel(Tc, ref.Tc) <= REFINED_TOL
+    assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+    prob.close()
+
+
+def test_refined_wide_equals_element_tiles_multitrack():
+    """Both inner tilings converge to the same solution (outer tolerance 1e-10)."""
+    base = workloads.workload("multitrack_10mm", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5)
+    out = []
+    for tiles in (1, 2):
+        p = tl.Problem(dict(base, inner_tiles=tiles))
+        p.macro_steps(4)
+        out.append((p.temperature(tl.TL_FINE)[0], p.state(tl.TL_FINE)))
+        p.close()
+    assert rel(out[1][0], out[0][0]) <= 1e-8
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_refined_20mm_full_size_against_fp64_gpu_path():
+    """The 20 x 10 x 4 mm plate at full size (129 x 129 x 65 fine nodes, wide
+    inner tiles): the precision form against the FP64 path after 3 macro steps
+    (the oracle would need tens of minutes per step at this size), plus the
+    energy identity of the refined solves."""
+    base = workloads.workload("multitrack_20mm")
+    out = []
+    for prec, tol in ((tl.TL_FP64, 1e-12), (tl.TL_FP32_REFINED, 1e-10)):
+        p = tl.Problem(dict(base, precision=prec, tol=tol))
+        p.macro_steps(3)  # raises on a failed solve
+        assert p.sync() == tl.TL_OK
+        out.append((p.temperature(tl.TL_FINE)[0], p.temperature(tl.TL_COARSE)[0], p.state(tl.TL_FINE), p.stats()))
+        p.close()
+    (a, ac, sa, _), (b, bc, sb, st) = out
+    assert rel(b, a) <= REFINED_TOL and rel(bc, ac) <= REFINED_TOL
+    assert np.array_equal(sa == tl.MELTED, sb == tl.MELTED)
+    for lvl in ("fine", "coarse"):
+        s_, l_, f_ = (st[f"energy_{lvl}_{k}"] for k in ("stored", "laser", "flux"))
+        assert abs(s_ - l_ - f_) <= 1e-7 * max(abs(s_), abs(l_)), lvl
