@@ -532,18 +532,26 @@ def run_serve(args):
     return 0
 
 
-# Algorithmic bytes per node of one single-reduction CG pass (window update
-# fused into the matrix-free apply): reads dinv, r, w-partial, p, s, x and
-# writes p, s, r, x, w-partial (11 nodal values) plus the element data the
-# apply reads (FP32: s_e, k_e; FP64: eight eigenvalues), elements ~ nodes.
+# Algorithmic bytes per node of one CG iteration.
+#  fused (element tiles; FP64 path and small refined meshes): the window
+#   update fused into the matrix-free apply reads dinv, r, w-partial, p, s, x
+#   and writes p, s, r, x, w-partial (11 nodal values) plus the element data
+#   the apply reads (FP32: s_e, k_e; FP64: eight eigenvalues), elements ~ nodes;
+#  wide (two-phase, large refined meshes): the update phase reads dinv, r, q,
+#   x, p, s and writes p, s, r, x, z (11 FP32 values); the apply phase reads z
+#   and s_e, k_e and writes q (4 values).
 PASS_BYTES = {"fp32": 11 * 4 + 2 * 4, "fp64": 11 * 8 + 8 * 8}
+WIDE_UPDATE_BYTES = 11 * 4
+WIDE_APPLY_BYTES = 4 * 4
 PASS_FLOPS_FP64 = FLOPS_APPLY_PER_ELEM + FLOPS_VEC_PER_NODE
+HBM_GBS = 6688.8  # measured copy bandwidth of this GB300 (read + write bytes)
 
 
 def run_roofline(args):
     """A 256 x 256 x 128-element fine patch (8.5M nodes; 32 x 32 x 16 coarse
     elements refined 8x, plate 40 x 40 x 20 coarse): one micro step in each
-    precision, per-pass times from the device phase tracer."""
+    precision, per-phase times from the device phase tracer (block 0's view:
+    a phase ends when the grid barrier after it is passed)."""
     import torch
 
     from paper_2110_12932_gb300 import build as tlbuild
@@ -556,6 +564,7 @@ def run_roofline(args):
                               tracks=[(1e-3, 2.5e-3, 4e-3, 2.5e-3, 0.8)])
     nn = fine_nodes(base)
     out = {}
+    names = {v: k for k, v in tl.TRACE_MARKS.items()}
     for prec in ("fp32", "fp64"):
         cfg = dict(base, precision=1 if prec == "fp32" else 0, tol=1e-10 if prec == "fp32" else 1e-12)
         p = tl.Problem(cfg)
@@ -563,23 +572,42 @@ def run_roofline(args):
         p.predict()
         p.fine_substeps(1)
         torch.cuda.synchronize()
-        ev = p.trace(tl.TL_FINE)
+        ev = [e for e in p.trace(tl.TL_FINE) if e[0] not in (names["rr_value"], names["breakdown_value"])]
         p.close()
-        passes = [(b - a) / 1e9 for (m0, a), (m1, b) in zip(ev, ev[1:]) if m1 == 4]  # CG pass ends
-        # a pass spans apply + reduction + barrier: time from one pass end to the next
-        ends = [b for (m, b) in ev if m == 4]
-        dts = [(y - x) / 1e9 for x, y in zip(ends, ends[1:])]
-        t = statistics.median(dts) if dts else float("nan")
-        byt = PASS_BYTES[prec] * nn
-        o = {"pass_us": 1e6 * t, "passes": len(ends), "bytes_per_pass": byt, "GBps": byt / t / 1e9,
-             "frac_of_measured_hbm": byt / t / 1e9 / 6688.8}
-        if prec == "fp64":
-            fl = PASS_FLOPS_FP64 * nn
-            o.update({"TFLOPs": fl / t / 1e12, "frac_of_fp64_peak": fl / t / 1e12 / 1.25856})
+        ends = [b for (m, b) in ev if m == names["cg_pass"]]
+        t = statistics.median([(y - x) / 1e9 for x, y in zip(ends, ends[1:])]) if len(ends) > 1 else float("nan")
+        seg = {}
+        for (m0, a), (m1, b) in zip(ev, ev[1:]):
+            seg.setdefault((m0, m1), []).append((b - a) / 1e9)
+        o = {"pass_us": 1e6 * t, "passes": len(ends)}
+        upd = seg.get((names["cg_pass"], names["cg_u_start"]))
+        if upd:  # two-phase (wide) iterations: update phase, apply phase
+            tu = statistics.median(seg[(names["cg_pass"], names["cg_u_start"])]) + \
+                statistics.median(seg[(names["cg_u_start"], names["cg_u_end"])]) + \
+                statistics.median(seg[(names["cg_u_end"], names["cg_update"])])
+            ta = statistics.median(seg[(names["cg_update"], names["cg_apply"])]) + \
+                statistics.median(seg[(names["cg_apply"], names["cg_pass"])])
+            bu, ba = WIDE_UPDATE_BYTES * nn, WIDE_APPLY_BYTES * nn
+            o.update({"scheme": "two-phase, wide tiles",
+                      "update_phase": {"us": 1e6 * tu, "bytes": bu, "GBps": bu / tu / 1e9,
+                                       "frac_of_measured_hbm": bu / tu / 1e9 / HBM_GBS},
+                      "apply_phase": {"us": 1e6 * ta, "bytes": ba, "GBps": ba / ta / 1e9,
+                                      "frac_of_measured_hbm": ba / ta / 1e9 / HBM_GBS},
+                      "bytes_per_pass": bu + ba, "GBps": (bu + ba) / t / 1e9,
+                      "frac_of_measured_hbm": (bu + ba) / t / 1e9 / HBM_GBS})
+        else:
+            byt = PASS_BYTES[prec] * nn
+            o.update({"scheme": "fused, element tiles", "bytes_per_pass": byt, "GBps": byt / t / 1e9,
+                      "frac_of_measured_hbm": byt / t / 1e9 / HBM_GBS})
+            if prec == "fp64":
+                fl = PASS_FLOPS_FP64 * nn
+                o.update({"TFLOPs": fl / t / 1e12, "frac_of_fp64_peak": fl / t / 1e12 / 1.25856})
         out[prec] = o
-    line = {"metric": "CG pass throughput (matrix-free apply + fused update)", "mode": "roofline",
+    line = {"metric": "CG pass throughput (matrix-free apply + vector update)", "mode": "roofline",
             "config": {"fine_nodes": nn, "fine_elements": 256 * 256 * 128,
-                       "bytes_per_node": PASS_BYTES, "fp64_flops_per_node": PASS_FLOPS_FP64},
+                       "bytes_per_node": {"fused": PASS_BYTES, "wide_update": WIDE_UPDATE_BYTES,
+                                          "wide_apply": WIDE_APPLY_BYTES},
+                       "fp64_flops_per_node": PASS_FLOPS_FP64, "hbm_peak_GBps": HBM_GBS},
             "results": out}
     print(json.dumps(line), flush=True)
     return 0

@@ -774,10 +774,11 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
 // of a block handles window node row w (w <= ey) and, for w < ey, element row
 // w; lane l handles window columns 2l and 2l + 1 and the two elements that
 // start there (lane 31 also column AX).  Within a row the x-direction stays in
-// registers and warp shuffles, the neighbouring node row passes through
-// shared memory, and an element layer takes two block barriers.  Inputs
-// (window values and element data) arrive by cp.async two layers ahead in a
-// four-stage per-thread ring.  Emits like apply_tile: emit(n, slot, y, x_n).
+// registers, warp shuffles and shared memory, the neighbouring node row
+// passes through shared memory, and an element layer takes two block
+// barriers.  Inputs (window values and element data) arrive by cp.async two
+// layers ahead in a four-stage per-thread ring.  Partials of window nodes on
+// the tile's high faces go to the exchange arrays, as with apply_tile.
 // ---------------------------------------------------------------------------
 constexpr int AX = 64, AY = 4;
 constexpr int WSLOTS = 8;    // ring slots per stage: u(c0), u(c1), u(AX), s0, k0, s1, k1, spare
@@ -792,18 +793,32 @@ struct WideSmem {
   float R1d[AY][AX + 2];
 };
 
-template <class Emit>
-__device__ inline void apply_tile_wide(const Grid3& g, const Tiling& t, int tile, WideSmem& sm, float* ring,
-                                       const float* u, const float* sk, const float (&mp)[8], const float (&kp)[8],
-                                       Emit emit) {
+struct WideCoef {
+  float mp[8], kp[8];  // eigenvalue factors (pair form) of the mass and stiffness parts
+};
+
+// One wide tile of w = A z for the two-phase CG: stores the partials (own and
+// exchange) in q / X and returns the tile's sum of z_n times its partials.
+// Not inlined: the tile loop gets the kernel's whole register budget.
+// Per element layer a thread does: one cp.async group for the layer two
+// ahead (inputs of invalid columns and elements are zeroed once per tile),
+// the z-direction of its columns, a block barrier, the y- and x-direction of
+// its two elements with the eigenvalue scaling (the next column's values
+// come from shared memory, so lane 31 needs no special case), the backward
+// x- and y-direction (the next lane's column by shuffle, the next row by
+// shared memory), a block barrier, the z-backward and the stores.
+static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Tiling t, int tile, WideSmem* smp,
+                                                         float* ring, const float* z, const float* sk,
+                                                         const WideCoef cf, float* q, float* X) {
   constexpr unsigned FULL = 0xffffffffu;
+  WideSmem& sm = *smp;
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int txy = t.ntx * t.nty;
   const int tiz = tile / txy, trem = tile - tiz * txy;
   const int tiy = trem / t.ntx, tix = trem - tiy * t.ntx;
   const int ie0 = tix * AX, je0 = tiy * AY, ke0 = tiz * t.ez;
   const int ex = min(AX, g.nx - ie0), ey = min(AY, g.ny - je0), ke1 = min(ke0 + t.ez, g.nz);
-  const int S = g.nnx * g.nny, Se = g.nx * g.ny, ne = Se * g.nz;
+  const int S = g.nnx * g.nny, Se = g.nx * g.ny, ne = Se * g.nz, nn = S * g.nnz;
   const bool row_on = wy <= ey;                 // this warp has a window node row
   const bool has_el = wy < ey;                  // ... and an element row
   const int c0 = 2 * lane, c1 = c0 + 1;
@@ -811,37 +826,43 @@ __device__ inline void apply_tile_wide(const Grid3& g, const Tiling& t, int tile
   const bool vx = row_on && lane == 31 && ex == AX;  // column AX
   const bool ok0 = has_el && c0 < ex, ok1 = has_el && c1 < ex;
   const int nb = ie0 + g.nnx * (je0 + (row_on ? wy : 0));
-  const int eb = ie0 + g.nx * (je0 + (has_el ? wy : 0)) + c0;
+  const float* up = z + nb;                                            // node (ie0, row, 0)
+  const float* ep = sk + ie0 + g.nx * (je0 + (has_el ? wy : 0)) + c0;  // element (ie0 + c0, row, 0)
   // exchange slots: the tile's high-y node row; column AX is on the high-x
   // face only when another tile follows in x (a ragged last column is the
-  // plate's own boundary)
+  // plate's own boundary); the top node layer adds the high-z bit
   const int ys = (wy == ey && je0 + ey < g.ny) ? 2 : 0;
-  const int xs = (ie0 + AX < g.nx) ? 1 : 0;
+  const int sx = ys | ((ie0 + AX < g.nx) ? 1 : 0);
+  float* o01 = (ys ? X + (size_t)(ys - 1) * nn : q) + nb;
+  float* ox = (sx ? X + (size_t)(sx - 1) * nn : q) + nb + AX;
   float* my = ring + threadIdx.x;
-  auto issue = [&](int st) {  // stage st: u at node layer ke0 + st, s/k at element layer ke0 + st
+#pragma unroll
+  for (int st = 0; st < WSTAGES; ++st) {
+    float* r = my + st * WSLOTS * NT;
+    if (!v0) r[0] = 0.0f;
+    if (!v1) r[NT] = 0.0f;
+    if (!vx) r[2 * NT] = 0.0f;
+    if (!ok0) r[3 * NT] = r[4 * NT] = 0.0f;
+    if (!ok1) r[5 * NT] = r[6 * NT] = 0.0f;
+  }
+  auto issue = [&](int st) {  // stage st: z at node layer ke0 + st, s/k at element layer ke0 + st
     float* r = my + (st & (WSTAGES - 1)) * WSLOTS * NT;
     const int kn = ke0 + st;
     if (kn <= ke1) {
-      const int b = nb + S * kn;
-      if (v0) cp_async<4>(r, u + b + c0); else r[0] = 0.0f;
-      if (v1) cp_async<4>(r + NT, u + b + c1); else r[NT] = 0.0f;
-      if (vx) cp_async<4>(r + 2 * NT, u + b + AX); else r[2 * NT] = 0.0f;
+      const float* ub = up + (size_t)S * kn;
+      if (v0) cp_async<4>(r, ub + c0);
+      if (v1) cp_async<4>(r + NT, ub + c1);
+      if (vx) cp_async<4>(r + 2 * NT, ub + AX);
     }
     if (kn < ke1) {
-      const int e = eb + Se * kn;
+      const float* eb = ep + (size_t)Se * kn;
       if (ok0) {
-        cp_async<4>(r + 3 * NT, sk + e);
-        cp_async<4>(r + 4 * NT, sk + ne + e);
-      } else {
-        r[3 * NT] = 0.0f;
-        r[4 * NT] = 0.0f;
+        cp_async<4>(r + 3 * NT, eb);
+        cp_async<4>(r + 4 * NT, eb + ne);
       }
       if (ok1) {
-        cp_async<4>(r + 5 * NT, sk + e + 1);
-        cp_async<4>(r + 6 * NT, sk + ne + e + 1);
-      } else {
-        r[5 * NT] = 0.0f;
-        r[6 * NT] = 0.0f;
+        cp_async<4>(r + 5 * NT, eb + 1);
+        cp_async<4>(r + 6 * NT, eb + ne + 1);
       }
     }
     cp_async_commit();
@@ -850,53 +871,37 @@ __device__ inline void apply_tile_wide(const Grid3& g, const Tiling& t, int tile
   issue(1);
   issue(2);
   cp_async_wait<2>();
-  float uL[3];
-  {
-    const float* r = my;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) uL[c] = r[c * NT];
-  }
-  float carry[3] = {0.0f, 0.0f, 0.0f};
+  float uL0 = my[0], uL1 = my[NT], uL2 = my[2 * NT];
+  float carry0 = 0.0f, carry1 = 0.0f, carry2 = 0.0f;
+  float vd = 0.0f;
   for (int ke = ke0; ke < ke1; ++ke) {
     const int j = ke - ke0;
     issue(j + 3);
     cp_async_wait<2>();  // stages j and j + 1 have landed
     const float* rc = my + (j & (WSTAGES - 1)) * WSLOTS * NT;
     const float* rn = my + ((j + 1) & (WSTAGES - 1)) * WSLOTS * NT;
-    float uH[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) uH[c] = rn[c * NT];
+    const float uH0 = rn[0], uH1 = rn[NT], uH2 = rn[2 * NT];
     const float s0 = rc[3 * NT], k0 = rc[4 * NT], s1 = rc[5 * NT], k1 = rc[6 * NT];
     // z-direction per own column
-    float zs[3], zd[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      zs[c] = uL[c] + uH[c];
-      zd[c] = uL[c] - uH[c];
-    }
+    const float zs0 = uL0 + uH0, zs1 = uL1 + uH1, zs2 = uL2 + uH2;
+    const float zd0 = uL0 - uH0, zd1 = uL1 - uH1, zd2 = uL2 - uH2;
     if (row_on) {
-      *reinterpret_cast<float2*>(&sm.ZS[wy][c0]) = make_float2(zs[0], zs[1]);
-      *reinterpret_cast<float2*>(&sm.ZD[wy][c0]) = make_float2(zd[0], zd[1]);
+      *reinterpret_cast<float2*>(&sm.ZS[wy][c0]) = make_float2(zs0, zs1);
+      *reinterpret_cast<float2*>(&sm.ZD[wy][c0]) = make_float2(zd0, zd1);
       if (lane == 31) {
-        sm.ZS[wy][AX] = zs[2];
-        sm.ZD[wy][AX] = zd[2];
+        sm.ZS[wy][AX] = zs2;
+        sm.ZD[wy][AX] = zd2;
       }
     }
     __syncthreads();
     // elements of row wy: y-forward, x-direction with scaling, y-backward
-    float r0s[3] = {0.0f, 0.0f, 0.0f}, r0d[3] = {0.0f, 0.0f, 0.0f};
+    float r0s0 = 0.0f, r0s1 = 0.0f, r0s2 = 0.0f, r0d0 = 0.0f, r0d1 = 0.0f, r0d2 = 0.0f;
     if (has_el) {
       const float2 ns = *reinterpret_cast<const float2*>(&sm.ZS[wy + 1][c0]);
       const float2 nd = *reinterpret_cast<const float2*>(&sm.ZD[wy + 1][c0]);
-      float s2 = __shfl_down_sync(FULL, zs[0], 1), d2 = __shfl_down_sync(FULL, zd[0], 1);
-      float ns2 = __shfl_down_sync(FULL, ns.x, 1), nd2 = __shfl_down_sync(FULL, nd.x, 1);
-      if (lane == 31) {
-        s2 = zs[2];
-        d2 = zd[2];
-        ns2 = sm.ZS[wy + 1][AX];
-        nd2 = sm.ZD[wy + 1][AX];
-      }
-      const float S0[3] = {zs[0], zs[1], s2}, D0[3] = {zd[0], zd[1], d2};
+      const float s2 = sm.ZS[wy][c0 + 2], d2 = sm.ZD[wy][c0 + 2];
+      const float ns2 = sm.ZS[wy + 1][c0 + 2], nd2 = sm.ZD[wy + 1][c0 + 2];
+      const float S0[3] = {zs0, zs1, s2}, D0[3] = {zd0, zd1, d2};
       const float S1[3] = {ns.x, ns.y, ns2}, D1[3] = {nd.x, nd.y, nd2};
       float Y[4][3];  // (y, z) mode m4 = my + 2 mz, per column
 #pragma unroll
@@ -909,27 +914,33 @@ __device__ inline void apply_tile_wide(const Grid3& g, const Tiling& t, int tile
       float B[4][3];
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) {
-        const float la = fmaf(s0, mp[2 * m4], k0 * kp[2 * m4]), lb = fmaf(s0, mp[2 * m4 + 1], k0 * kp[2 * m4 + 1]);
-        const float ma = fmaf(s1, mp[2 * m4], k1 * kp[2 * m4]), mb = fmaf(s1, mp[2 * m4 + 1], k1 * kp[2 * m4 + 1]);
+        const float la = fmaf(s0, cf.mp[2 * m4], k0 * cf.kp[2 * m4]);
+        const float lb = fmaf(s0, cf.mp[2 * m4 + 1], k0 * cf.kp[2 * m4 + 1]);
+        const float ma = fmaf(s1, cf.mp[2 * m4], k1 * cf.kp[2 * m4]);
+        const float mb = fmaf(s1, cf.mp[2 * m4 + 1], k1 * cf.kp[2 * m4 + 1]);
         const float a0 = Y[m4][0], a1 = Y[m4][1], a2 = Y[m4][2];
         B[m4][0] = fmaf(la, a0, lb * a1);
-        B[m4][1] = fmaf(lb, a0, la * a1) + fmaf(ma, a1, mb * a2);
+        B[m4][1] = fmaf(lb, a0, fmaf(la + ma, a1, mb * a2));
         B[m4][2] = fmaf(mb, a1, ma * a2);
       }
       float r1s[3], r1d[3];
+      r0s0 = B[0][0] + B[1][0];
+      r0s1 = B[0][1] + B[1][1];
+      r0s2 = B[0][2] + B[1][2];
+      r0d0 = B[2][0] + B[3][0];
+      r0d1 = B[2][1] + B[3][1];
+      r0d2 = B[2][2] + B[3][2];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        r0s[c] = B[0][c] + B[1][c];
         r1s[c] = B[0][c] - B[1][c];
-        r0d[c] = B[2][c] + B[3][c];
         r1d[c] = B[2][c] - B[3][c];
       }
-      // column 2l + 2 is the next lane's first column
-      const float t0 = __shfl_up_sync(FULL, r0s[2], 1), t1 = __shfl_up_sync(FULL, r0d[2], 1);
+      // column 2l + 2 is the next lane's first column (lane 31 keeps it: column AX)
+      const float t0 = __shfl_up_sync(FULL, r0s2, 1), t1 = __shfl_up_sync(FULL, r0d2, 1);
       const float t2 = __shfl_up_sync(FULL, r1s[2], 1), t3 = __shfl_up_sync(FULL, r1d[2], 1);
       if (lane > 0) {
-        r0s[0] += t0;
-        r0d[0] += t1;
+        r0s0 += t0;
+        r0d0 += t1;
         r1s[0] += t2;
         r1d[0] += t3;
       }
@@ -943,62 +954,61 @@ __device__ inline void apply_tile_wide(const Grid3& g, const Tiling& t, int tile
     __syncthreads();
     // node row wy: own element row plus the row below, then z-backward
     if (row_on) {
-      float cs[3] = {r0s[0], r0s[1], r0s[2]}, cd[3] = {r0d[0], r0d[1], r0d[2]};
       if (wy > 0) {
         const float2 ps = *reinterpret_cast<const float2*>(&sm.R1s[wy - 1][c0]);
         const float2 pd = *reinterpret_cast<const float2*>(&sm.R1d[wy - 1][c0]);
-        cs[0] += ps.x;
-        cs[1] += ps.y;
-        cd[0] += pd.x;
-        cd[1] += pd.y;
+        r0s0 += ps.x;
+        r0s1 += ps.y;
+        r0d0 += pd.x;
+        r0d1 += pd.y;
         if (lane == 31) {
-          cs[2] += sm.R1s[wy - 1][AX];
-          cd[2] += sm.R1d[wy - 1][AX];
+          r0s2 += sm.R1s[wy - 1][AX];
+          r0d2 += sm.R1d[wy - 1][AX];
         }
       }
-      float out[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        out[c] = carry[c] + (cs[c] + cd[c]);
-        carry[c] = cs[c] - cd[c];
+      const float out0 = carry0 + (r0s0 + r0d0), out1 = carry1 + (r0s1 + r0d1), out2 = carry2 + (r0s2 + r0d2);
+      carry0 = r0s0 - r0d0;
+      carry1 = r0s1 - r0d1;
+      carry2 = r0s2 - r0d2;
+      const size_t lk = (size_t)S * ke;
+      if (v0) {
+        o01[lk + c0] = out0;
+        vd = fmaf(uL0, out0, vd);
       }
-      const int b = nb + S * ke;
-      if (v0) emit(b + c0, ys, out[0], uL[0]);
-      if (v1) emit(b + c1, ys, out[1], uL[1]);
-      if (vx) emit(b + AX, ys | xs, out[2], uL[2]);
+      if (v1) {
+        o01[lk + c1] = out1;
+        vd = fmaf(uL1, out1, vd);
+      }
+      if (vx) {
+        ox[lk] = out2;
+        vd = fmaf(uL2, out2, vd);
+      }
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) uL[c] = uH[c];
+    uL0 = uH0;
+    uL1 = uH1;
+    uL2 = uH2;
   }
   // top node layer of the tile: only the contributions of element layer ke1 - 1
   if (row_on) {
-    const int zs4 = ke1 < g.nz ? 4 : 0;
-    const int b = nb + S * ke1;
-    if (v0) emit(b + c0, ys | zs4, carry[0], uL[0]);
-    if (v1) emit(b + c1, ys | zs4, carry[1], uL[1]);
-    if (vx) emit(b + AX, ys | xs | zs4, carry[2], uL[2]);
+    const size_t top = (size_t)S * ke1;
+    const int zb = ke1 < g.nz ? 4 : 0;
+    float* t01 = ((ys | zb) ? X + (size_t)((ys | zb) - 1) * nn : q) + nb + top;
+    float* tx = ((sx | zb) ? X + (size_t)((sx | zb) - 1) * nn : q) + nb + AX + top;
+    if (v0) {
+      t01[c0] = carry0;
+      vd = fmaf(uL0, carry0, vd);
+    }
+    if (v1) {
+      t01[c1] = carry1;
+      vd = fmaf(uL1, carry1, vd);
+    }
+    if (vx) {
+      tx[0] = carry2;
+      vd = fmaf(uL2, carry2, vd);
+    }
   }
   cp_async_wait<0>();
   __syncthreads();
-}
-
-struct WideCoef {
-  float mp[8], kp[8];  // eigenvalue factors (pair form) of the mass and stiffness parts
-};
-
-// One wide tile of w = A z for the two-phase CG: stores the partials (own and
-// exchange) and returns the tile's sum of z_n times its partials.  Not
-// inlined: the tile loop gets the kernel's whole register budget.
-static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Tiling t, int tile, WideSmem* sm, float* ring,
-                                                  const float* z, const float* sk, const WideCoef cf, float* q,
-                                                  float* X) {
-  const int nn = g.nnx * g.nny * g.nnz;
-  float vd = 0.0f;
-  auto emit = [&](int n, int slot, float y, float xin) {
-    store_partial(q, X, nn, n, slot, y, false);
-    vd = fmaf(xin, y, vd);
-  };
-  apply_tile_wide(g, t, tile, *sm, ring, z, sk, cf.mp, cf.kp, emit);
   return vd;
 }
 
