@@ -590,7 +590,11 @@ def run_roofline(args):
             bu, ba = WIDE_UPDATE_BYTES * nn, WIDE_APPLY_BYTES * nn
             o.update({"scheme": "two-phase, wide tiles",
                       "update_phase": {"us": 1e6 * tu, "bytes": bu, "GBps": bu / tu / 1e9,
-                                       "frac_of_measured_hbm": bu / tu / 1e9 / HBM_GBS},
+                                       "frac_of_measured_hbm": bu / tu / 1e9 / HBM_GBS,
+                                       "block0_share_us": 1e6 * statistics.median(
+                                           seg[(names["cg_u_start"], names["cg_u_end"])]),
+                                       "reduce_and_barrier_us": 1e6 * statistics.median(
+                                           seg[(names["cg_u_end"], names["cg_update"])])},
                       "apply_phase": {"us": 1e6 * ta, "bytes": ba, "GBps": ba / ta / 1e9,
                                       "frac_of_measured_hbm": ba / ta / 1e9 / HBM_GBS},
                       "bytes_per_pass": bu + ba, "GBps": (bu + ba) / t / 1e9,

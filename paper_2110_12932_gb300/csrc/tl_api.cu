@@ -229,7 +229,7 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
   if ((s = alloc_n(p, &L.F, (size_t)L.g.nnx * L.g.nny)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.G, (size_t)MAXRECT * (L.g.nnx + L.g.nny))) != TL_OK) return s;
   if ((s = alloc_n(p, &L.q, nn)) != TL_OK) return s;
-  if ((s = alloc_n(p, &L.X, nn * NXB)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.X, (size_t)xplane((int)nn) * NXB)) != TL_OK) return s;
   if (p->cfg.precision == TL_FP64) {
     if ((s = alloc_n(p, &L.r2, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.p0, nn)) != TL_OK) return s;
@@ -237,7 +237,7 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
     if ((s = alloc_n(p, &L.s0, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.s1, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.q2, nn)) != TL_OK) return s;
-    if ((s = alloc_n(p, &L.X2, nn * NXB)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.X2, (size_t)xplane((int)nn) * NXB)) != TL_OK) return s;
   }
   if ((s = alloc_n(p, &L.dinv, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.s_e, ne)) != TL_OK) return s;
@@ -248,9 +248,9 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
     if ((s = alloc_n(p, &L.r32, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.r32b, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.q32, nn)) != TL_OK) return s;
-    if ((s = alloc_n(p, &L.X32, nn * NXB)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.X32, (size_t)xplane((int)nn) * NXB)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.q32b, nn)) != TL_OK) return s;
-    if ((s = alloc_n(p, &L.X32b, nn * NXB)) != TL_OK) return s;
+    if ((s = alloc_n(p, &L.X32b, (size_t)xplane((int)nn) * NXB)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.p0f, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.p1f, nn)) != TL_OK) return s;
     if ((s = alloc_n(p, &L.s0f, nn)) != TL_OK) return s;
@@ -756,7 +756,7 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   // buffers read before being written in a solve start at zero
   for (Level* L : {&C, &F}) {
     size_t nn = (size_t)L->g.nnx * L->g.nny * L->g.nnz;
-    cudaMemsetAsync(L->X, 0, nn * NXB * sizeof(double), p->stream);
+    cudaMemsetAsync(L->X, 0, (size_t)xplane((int)nn) * NXB * sizeof(double), p->stream);
   }
   cudaMemsetAsync(p->bar, 0, BAR_WORDS * sizeof(unsigned int), p->stream);
   cudaMemsetAsync(C.trace, 0, 2 * TRACE_CAP * sizeof(unsigned long long), p->stream);

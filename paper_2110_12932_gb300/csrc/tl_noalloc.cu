@@ -187,8 +187,8 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
   a.q = c.take<double>(nn);
   a.q2 = c.take<double>(nn);
   a.dinv = c.take<double>(nn);
-  a.X = c.take<double>(nn * NXB);
-  a.X2 = c.take<double>(nn * NXB);
+  a.X = c.take<double>((size_t)xplane((int)nn) * NXB);
+  a.X2 = c.take<double>((size_t)xplane((int)nn) * NXB);
   a.s_e = c.take<double>(ne);
   a.k_e = c.take<double>(ne);
   a.lam = c.take<double>(8 * ne);

@@ -46,6 +46,9 @@ __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" 
 static_assert(NT >= WX * WY, "a block must cover a tile's window columns");
 constexpr int MAXRECT = 8;
 constexpr int NXB = 7;                // exchange buffers
+// Stride of the exchange planes: the node count rounded up to four, so that a
+// plane starts on a 16-byte boundary (vector loads of four FP32 partials).
+__host__ __device__ inline int xplane(int nn) { return (nn + 3) & ~3; }
 
 struct DirSpec {
   int faces;    // bit0 x=0, bit1 x=nx, bit2 y=0, bit3 y=ny, bit4 z=0
@@ -545,20 +548,21 @@ template <typename R>
 __device__ inline R gather_partials(const R* prim, const R* X, int nn, int n, int lf) {
   R v = __ldcg(prim + n);
   if (lf) {
-    if (lf & 1) v += __ldcg(X + 0 * nn + n);
-    if (lf & 2) v += __ldcg(X + 1 * nn + n);
-    if ((lf & 3) == 3) v += __ldcg(X + 2 * nn + n);
-    if (lf & 4) v += __ldcg(X + 3 * nn + n);
-    if ((lf & 5) == 5) v += __ldcg(X + 4 * nn + n);
-    if ((lf & 6) == 6) v += __ldcg(X + 5 * nn + n);
-    if (lf == 7) v += __ldcg(X + 6 * nn + n);
+    const size_t xs = xplane(nn);
+    if (lf & 1) v += __ldcg(X + 0 * xs + n);
+    if (lf & 2) v += __ldcg(X + 1 * xs + n);
+    if ((lf & 3) == 3) v += __ldcg(X + 2 * xs + n);
+    if (lf & 4) v += __ldcg(X + 3 * xs + n);
+    if ((lf & 5) == 5) v += __ldcg(X + 4 * xs + n);
+    if ((lf & 6) == 6) v += __ldcg(X + 5 * xs + n);
+    if (lf == 7) v += __ldcg(X + 6 * xs + n);
   }
   return v;
 }
 
 template <typename R>
 __device__ inline void store_partial(R* prim, R* X, int nn, int n, int slot, R v, bool add) {
-  R* dst = slot == 0 ? prim + n : X + (slot - 1) * nn + n;
+  R* dst = slot == 0 ? prim + n : X + (size_t)(slot - 1) * xplane(nn) + n;
   if (add) v += *dst;
   *dst = v;
 }
@@ -651,6 +655,7 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
     R* s_nxt = nxt ? c.s[1] : c.s[0];
     R* q_out = (k >= 0 && nxt) ? c.q[1] : c.q[0];
     R* X_out = (k >= 0 && nxt) ? c.X[1] : c.X[0];
+    const size_t xs = xplane(nn);
     R sg = R(0), vd = R(0), vr = R(0);
     for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
       // raw inputs of a window node: 0 dinv, 1 r, 2 own partial of w, 3 p, 4 s,
@@ -670,13 +675,13 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
         const bool lz = kk > 0 && kk < g.nz && (kk % t.ez) == 0;
         const int lf = low_faces(g, t, i, ly, lz);
         if (lf) {
-          if (lf & 1) cp_async<sizeof(R)>(raw + 5 * NT, X_cur + 0 * nn + n);
-          if (lf & 2) cp_async<sizeof(R)>(raw + 6 * NT, X_cur + 1 * nn + n);
-          if ((lf & 3) == 3) cp_async<sizeof(R)>(raw + 7 * NT, X_cur + 2 * nn + n);
-          if (lf & 4) cp_async<sizeof(R)>(raw + 8 * NT, X_cur + 3 * nn + n);
-          if ((lf & 5) == 5) cp_async<sizeof(R)>(raw + 9 * NT, X_cur + 4 * nn + n);
-          if ((lf & 6) == 6) cp_async<sizeof(R)>(raw + 10 * NT, X_cur + 5 * nn + n);
-          if (lf == 7) cp_async<sizeof(R)>(raw + 11 * NT, X_cur + 6 * nn + n);
+          if (lf & 1) cp_async<sizeof(R)>(raw + 5 * NT, X_cur + 0 * xs + n);
+          if (lf & 2) cp_async<sizeof(R)>(raw + 6 * NT, X_cur + 1 * xs + n);
+          if ((lf & 3) == 3) cp_async<sizeof(R)>(raw + 7 * NT, X_cur + 2 * xs + n);
+          if (lf & 4) cp_async<sizeof(R)>(raw + 8 * NT, X_cur + 3 * xs + n);
+          if ((lf & 5) == 5) cp_async<sizeof(R)>(raw + 9 * NT, X_cur + 4 * xs + n);
+          if ((lf & 6) == 6) cp_async<sizeof(R)>(raw + 10 * NT, X_cur + 5 * xs + n);
+          if (lf == 7) cp_async<sizeof(R)>(raw + 11 * NT, X_cur + 6 * xs + n);
         }
       };
       auto finish = [&](int n, int i, int j, int kk, bool owned, const R* raw) -> R {
@@ -833,8 +838,8 @@ static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Ti
   // plate's own boundary); the top node layer adds the high-z bit
   const int ys = (wy == ey && je0 + ey < g.ny) ? 2 : 0;
   const int sx = ys | ((ie0 + AX < g.nx) ? 1 : 0);
-  float* o01 = (ys ? X + (size_t)(ys - 1) * nn : q) + nb;
-  float* ox = (sx ? X + (size_t)(sx - 1) * nn : q) + nb + AX;
+  float* o01 = (ys ? X + (size_t)(ys - 1) * xplane(nn) : q) + nb;
+  float* ox = (sx ? X + (size_t)(sx - 1) * xplane(nn) : q) + nb + AX;
   float* my = ring + threadIdx.x;
 #pragma unroll
   for (int st = 0; st < WSTAGES; ++st) {
@@ -992,8 +997,8 @@ static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Ti
   if (row_on) {
     const size_t top = (size_t)S * ke1;
     const int zb = ke1 < g.nz ? 4 : 0;
-    float* t01 = ((ys | zb) ? X + (size_t)((ys | zb) - 1) * nn : q) + nb + top;
-    float* tx = ((sx | zb) ? X + (size_t)((sx | zb) - 1) * nn : q) + nb + AX + top;
+    float* t01 = ((ys | zb) ? X + (size_t)((ys | zb) - 1) * xplane(nn) : q) + nb + top;
+    float* tx = ((sx | zb) ? X + (size_t)((sx | zb) - 1) * xplane(nn) : q) + nb + AX + top;
     if (v0) {
       t01[c0] = carry0;
       vd = fmaf(uL0, carry0, vd);
@@ -1049,9 +1054,10 @@ struct Sums2 { R a, b; };
 // stores), so every array streams at full line width whatever the row
 // length.  The lane's first node gets its (i, j, k) from two exact
 // multiply-high divisions, the others by increments.  A node's low tile faces
-// decide which exchange partials its owner adds; the y-face partial (a
-// quarter of all nodes on wide tiles) is loaded with the main inputs, the
-// rarer x, z and edge partials afterwards.  k < 0: z = D^-1 r only.
+// decide which exchange partials its owner adds; the x-, y- and z-face
+// partials are loaded with the main inputs (an x face falls in every warp's
+// 128 nodes, so a dependent load there would stall every step), the edge
+// partials afterwards.  k < 0: z = D^-1 r only.
 // Dirichlet nodes (dinv = 0) keep their r, p, s, x and get z = 0.  Returns the
 // thread's sums of <r,z> and <r,r>.  Not inlined: it gets the kernel's whole
 // register budget.
@@ -1064,6 +1070,7 @@ static __device__ __noinline__ Sums2<R> cg_update(const Grid3 g, const Tiling t,
   const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny), mz = div_magic(t.ez);
   const bool init = k < 0, first = k == 0;
   const int ngroups = (nn + VEC - 1) / VEC;
+  const size_t xs = xplane(nn);
   R vgam = R(0), vrr = R(0);
   auto load = [&](const R* a, int n0, int cnt, R (&o)[VEC]) {
     if (cnt == VEC) {
@@ -1108,23 +1115,35 @@ static __device__ __noinline__ Sums2<R> cg_update(const Grid3 g, const Tiling t,
       store(c.z, n0, cnt, zn);
       continue;
     }
-    // low tile faces of the group's nodes
+    // low tile faces of the group's nodes: the y and z faces once per row,
+    // the x face per node; a group that crosses a row end (or the array end)
+    // walks node by node
     int lf[VEC];
+    int rowf = -1;  // the group's y / z face bits when it lies in one row, else -1
     {
       const int row = div_by(n0, g.nnx, mx);
       int i = n0 - row * g.nnx;
       int kz = div_by(row, g.nny, my);
       int j = row - kz * g.nny;
+      auto row_faces = [&](int jj, int kk) {
+        const bool ly = t.nty > 1 && jj > 0 && jj < g.ny && (jj & (t.ey - 1)) == 0;
+        const bool lz = kk > 0 && kk < g.nz && kk - div_by(kk, t.ez, mz) * t.ez == 0;
+        return (ly ? 2 : 0) | (lz ? 4 : 0);
+      };
+      if (cnt == VEC && i + VEC <= g.nnx) {
+        rowf = row_faces(j, kz);
 #pragma unroll
-      for (int m = 0; m < VEC; ++m) {
-        const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
-        const bool lz = kz > 0 && kz < g.nz && kz - div_by(kz, t.ez, mz) * t.ez == 0;
-        lf[m] = m < cnt ? low_faces(g, t, i, ly, lz) : 0;
-        if (++i == g.nnx) {
-          i = 0;
-          if (++j == g.nny) {
-            j = 0;
-            ++kz;
+        for (int m = 0; m < VEC; ++m) lf[m] = rowf | low_faces(g, t, i + m, false, false);
+      } else {
+#pragma unroll
+        for (int m = 0; m < VEC; ++m) {
+          lf[m] = m < cnt ? (row_faces(j, kz) | low_faces(g, t, i, false, false)) : 0;
+          if (++i == g.nnx) {
+            i = 0;
+            if (++j == g.nny) {
+              j = 0;
+              ++kz;
+            }
           }
         }
       }
@@ -1139,8 +1158,22 @@ static __device__ __noinline__ Sums2<R> cg_update(const Grid3 g, const Tiling t,
 #pragma unroll
       for (int m = 0; m < VEC; ++m) pk[m] = sk[m] = R(0);
     }
+    R wx[VEC], wz[VEC];
+    if (rowf >= 0) {  // one row: whole-group y / z face partials as vectors
 #pragma unroll
-    for (int m = 0; m < VEC; ++m) wy[m] = (lf[m] & 2) ? __ldcg(c.X + 1 * nn + n0 + m) : R(0);
+      for (int m = 0; m < VEC; ++m) wy[m] = wz[m] = R(0);
+      if (rowf & 2) load(c.X + 1 * xs, n0, VEC, wy);
+      if (rowf & 4) load(c.X + 3 * xs, n0, VEC, wz);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) wx[m] = (lf[m] & 1) ? __ldcg(c.X + 0 * xs + n0 + m) : R(0);
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) {
+        wx[m] = (lf[m] & 1) ? __ldcg(c.X + 0 * xs + n0 + m) : R(0);
+        wy[m] = (lf[m] & 2) ? __ldcg(c.X + 1 * xs + n0 + m) : R(0);
+        wz[m] = (lf[m] & 4) ? __ldcg(c.X + 3 * xs + n0 + m) : R(0);
+      }
+    }
     R pn[VEC], sn[VEC], rn[VEC], xn[VEC], zn[VEC];
 #pragma unroll
     for (int m = 0; m < VEC; ++m) {
@@ -1154,13 +1187,13 @@ static __device__ __noinline__ Sums2<R> cg_update(const Grid3 g, const Tiling t,
       const int f = lf[m];
       R wv = w[m];
       if (f) {  // neighbours' partials, in the order gather_partials uses
-        if (f & 1) wv += __ldcg(c.X + 0 * nn + n);
+        if (f & 1) wv += wx[m];
         if (f & 2) wv += wy[m];
-        if ((f & 3) == 3) wv += __ldcg(c.X + 2 * nn + n);
-        if (f & 4) wv += __ldcg(c.X + 3 * nn + n);
-        if ((f & 5) == 5) wv += __ldcg(c.X + 4 * nn + n);
-        if ((f & 6) == 6) wv += __ldcg(c.X + 5 * nn + n);
-        if (f == 7) wv += __ldcg(c.X + 6 * nn + n);
+        if ((f & 3) == 3) wv += __ldcg(c.X + 2 * xs + n);
+        if (f & 4) wv += wz[m];
+        if ((f & 5) == 5) wv += __ldcg(c.X + 4 * xs + n);
+        if ((f & 6) == 6) wv += __ldcg(c.X + 5 * xs + n);
+        if (f == 7) wv += __ldcg(c.X + 6 * xs + n);
       }
       const R z0 = dv[m] * rk[m];
       pn[m] = first ? z0 : fma(beta, pk[m], z0);
