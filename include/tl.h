@@ -285,6 +285,22 @@ tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double* T_in, dou
                               uint8_t* state, void* stream);
 
 /* Release every device buffer of the problem; NULL is ignored. */
+/* ---- Checkpoint / resume -------------------------------------------------
+ * At a macro-step boundary (before PREDICT) the whole state of a problem is:
+ * the coarse field T+^n, the fine patch field and its origin, the coarse
+ * element states and the plate-wide fine state map, the macro-step index, and
+ * the counters / energy account.  tl_checkpoint_save copies it into a
+ * caller-owned host buffer of tl_checkpoint_size bytes (an opaque format tied
+ * to this library build); tl_checkpoint_load puts it into a problem created
+ * from the same configuration, after which the run continues bit-identically
+ * to one that never stopped.  Both synchronise the problem's stream.
+ * Errors: TL_EINVAL (NULL, wrong size, a buffer from another configuration or
+ * build), TL_ESTATE (not between macro steps, or an earlier device failure),
+ * TL_ECUDA. */
+tl_status tl_checkpoint_size(const tl_problem* p, size_t* bytes);
+tl_status tl_checkpoint_save(const tl_problem* p, void* host_out, size_t bytes);
+tl_status tl_checkpoint_load(tl_problem* p, const void* host_in, size_t bytes);
+
 void tl_destroy_problem(tl_problem* p);
 
 /* Static description of a status code. */

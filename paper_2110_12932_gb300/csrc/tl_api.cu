@@ -898,6 +898,116 @@ tl_status tl_get_state(const tl_problem* p, tl_level level, uint8_t* host_out, s
   return TL_OK;
 }
 
+// Checkpoint layout: header, coarse T, fine T (doubles), the device counters,
+// coarse states, plate-wide fine state map (bytes).
+struct CkptHeader {
+  uint64_t magic;
+  uint32_t version, stats_bytes;
+  int32_t dims[12];   // NXc NYc NZc, fine nx ny nz, map sx sy sz, r, m, precision
+  int32_t n, oi, oj, ok;
+  int64_t patch_moves;
+};
+constexpr uint64_t CKPT_MAGIC = 0x746c636b70743031ull;  // "tlckpt01"
+
+static void ckpt_dims(const tl_problem* p, int32_t (&d)[12]) {
+  const Level &C = p->C, &F = p->Fi;
+  const int32_t v[12] = {C.g.nx, C.g.ny, C.g.nz, F.g.nx, F.g.ny, F.g.nz, F.st_sx, F.st_sy, F.st_sz,
+                         p->cfg.r, p->cfg.m, (int32_t)p->cfg.precision};
+  for (int i = 0; i < 12; ++i) d[i] = v[i];
+}
+
+static size_t ckpt_bytes(const tl_problem* p) {
+  const Level &C = p->C, &F = p->Fi;
+  const size_t nc = (size_t)C.g.nnx * C.g.nny * C.g.nnz, nf = (size_t)F.g.nnx * F.g.nny * F.g.nnz;
+  const size_t ec = (size_t)C.g.nx * C.g.ny * C.g.nz, sm = (size_t)F.st_sx * F.st_sy * F.st_sz;
+  return sizeof(CkptHeader) + (nc + nf) * sizeof(double) + sizeof(DevStats) + ec + sm;
+}
+
+static tl_status ckpt_ready(const tl_problem* p) {
+  if (p->phase != NEED_PREDICT) return TL_ESTATE;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = 0;
+  e = cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  return st == 0 ? TL_OK : TL_ESTATE;
+}
+
+tl_status tl_checkpoint_size(const tl_problem* p, size_t* bytes) {
+  if (!p || !bytes) return TL_EINVAL;
+  *bytes = ckpt_bytes(p);
+  return TL_OK;
+}
+
+tl_status tl_checkpoint_save(const tl_problem* p, void* host_out, size_t bytes) {
+  if (!p || !host_out || bytes != ckpt_bytes(p)) return TL_EINVAL;
+  tl_status s = ckpt_ready(p);
+  if (s != TL_OK) return s;
+  const Level &C = p->C, &F = p->Fi;
+  const size_t nc = (size_t)C.g.nnx * C.g.nny * C.g.nnz, nf = (size_t)F.g.nnx * F.g.nny * F.g.nnz;
+  const size_t ec = (size_t)C.g.nx * C.g.ny * C.g.nz, sm = (size_t)F.st_sx * F.st_sy * F.st_sz;
+  unsigned char* b = static_cast<unsigned char*>(host_out);
+  CkptHeader h{};
+  h.magic = CKPT_MAGIC;
+  h.version = 1;
+  h.stats_bytes = (uint32_t)sizeof(DevStats);
+  ckpt_dims(p, h.dims);
+  h.n = p->n;
+  h.oi = p->oi;
+  h.oj = p->oj;
+  h.ok = p->ok;
+  h.patch_moves = p->patch_moves;
+  std::memcpy(b, &h, sizeof h);
+  b += sizeof h;
+  cudaError_t e = cudaMemcpy(b, C.T, nc * sizeof(double), cudaMemcpyDeviceToHost);
+  b += nc * sizeof(double);
+  if (e == cudaSuccess) e = cudaMemcpy(b, F.T, nf * sizeof(double), cudaMemcpyDeviceToHost);
+  b += nf * sizeof(double);
+  if (e == cudaSuccess) e = cudaMemcpy(b, p->stats, sizeof(DevStats), cudaMemcpyDeviceToHost);
+  b += sizeof(DevStats);
+  if (e == cudaSuccess) e = cudaMemcpy(b, C.state, ec, cudaMemcpyDeviceToHost);
+  b += ec;
+  if (e == cudaSuccess) e = cudaMemcpy(b, F.state, sm, cudaMemcpyDeviceToHost);
+  return cuda_status(e);
+}
+
+tl_status tl_checkpoint_load(tl_problem* p, const void* host_in, size_t bytes) {
+  if (!p || !host_in || bytes != ckpt_bytes(p)) return TL_EINVAL;
+  CkptHeader h;
+  std::memcpy(&h, host_in, sizeof h);
+  int32_t d[12];
+  ckpt_dims(p, d);
+  if (h.magic != CKPT_MAGIC || h.version != 1 || h.stats_bytes != sizeof(DevStats) ||
+      std::memcmp(d, h.dims, sizeof d) != 0)
+    return TL_EINVAL;
+  if (h.n < 0 || h.oi < 0 || h.oj < 0 || h.oi + p->cfg.pNXc > p->cfg.NXc || h.oj + p->cfg.pNYc > p->cfg.NYc ||
+      h.ok != p->ok)
+    return TL_EINVAL;
+  tl_status s = ckpt_ready(p);
+  if (s != TL_OK) return s;
+  const Level &C = p->C, &F = p->Fi;
+  const size_t nc = (size_t)C.g.nnx * C.g.nny * C.g.nnz, nf = (size_t)F.g.nnx * F.g.nny * F.g.nnz;
+  const size_t ec = (size_t)C.g.nx * C.g.ny * C.g.nz, sm = (size_t)F.st_sx * F.st_sy * F.st_sz;
+  const unsigned char* b = static_cast<const unsigned char*>(host_in) + sizeof h;
+  cudaError_t e = cudaMemcpy(C.T, b, nc * sizeof(double), cudaMemcpyHostToDevice);
+  b += nc * sizeof(double);
+  if (e == cudaSuccess) e = cudaMemcpy(F.T, b, nf * sizeof(double), cudaMemcpyHostToDevice);
+  b += nf * sizeof(double);
+  if (e == cudaSuccess) e = cudaMemcpy(p->stats, b, sizeof(DevStats), cudaMemcpyHostToDevice);
+  b += sizeof(DevStats);
+  if (e == cudaSuccess) e = cudaMemcpy(C.state, b, ec, cudaMemcpyHostToDevice);
+  b += ec;
+  if (e == cudaSuccess) e = cudaMemcpy(F.state, b, sm, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e);
+  p->n = h.n;
+  p->oi = h.oi;
+  p->oj = h.oj;
+  p->patch_moves = h.patch_moves;
+  p->sub = 0;
+  p->phase = NEED_PREDICT;
+  return TL_OK;
+}
+
 tl_status tl_get_stats(const tl_problem* p, tl_stats* out) {
   if (!p || !out) return TL_EINVAL;
   DevStats d{};

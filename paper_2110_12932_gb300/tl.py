@@ -90,6 +90,7 @@ EXPORTS = [
     "tl_sync", "tl_node_count", "tl_get_temperature", "tl_get_state", "tl_get_stats",
     "tl_destroy_problem", "tl_status_string", "tl_box_step_noalloc", "tl_trace_last_solve",
     "tl_batch_create", "tl_batch_add", "tl_batch_round", "tl_batch_poll", "tl_batch_info", "tl_batch_destroy",
+    "tl_checkpoint_size", "tl_checkpoint_save", "tl_checkpoint_load",
 ]
 
 _lib = None
@@ -132,6 +133,9 @@ def load(path=LIB_PATH):
                                         C.c_void_p]
     lib.tl_box_step_noalloc.restype = C.c_int
     lib.tl_trace_last_solve.argtypes = [P, C.c_int, C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_size_t)]
+    lib.tl_checkpoint_size.argtypes = [P, C.POINTER(C.c_size_t)]
+    lib.tl_checkpoint_save.argtypes = [P, C.c_void_p, C.c_size_t]
+    lib.tl_checkpoint_load.argtypes = [P, C.c_void_p, C.c_size_t]
     lib.tl_trace_last_solve.restype = C.c_int
     lib.tl_batch_create.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(P)]
     lib.tl_batch_create.restype = C.c_int
@@ -250,6 +254,27 @@ TRACE_MARKS = {0: "start", 1: "phase0", 2: "rhs", 3: "resid", 4: "cg_pass", 5: "
                11: "rr_value", 12: "breakdown_value", 13: "cg_update", 14: "cg_u_start", 15: "cg_u_end"}
 
 
+def tl_checkpoint_size(h):
+    n = C.c_size_t()
+    st = load().tl_checkpoint_size(h, C.byref(n))
+    return st, n.value
+
+
+def tl_checkpoint_save(h):
+    """Returns (status, numpy uint8 buffer)."""
+    st, n = tl_checkpoint_size(h)
+    if st != TL_OK:
+        return st, None
+    buf = np.empty(n, dtype=np.uint8)
+    st = load().tl_checkpoint_save(h, buf.ctypes.data_as(C.c_void_p), n)
+    return st, buf
+
+
+def tl_checkpoint_load(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    return load().tl_checkpoint_load(h, buf.ctypes.data_as(C.c_void_p), buf.size)
+
+
 def tl_trace_last_solve(h, level, cap=1024):
     """Returns (status, [(marker, ns), ...]) of the level's most recent solve."""
     buf = (C.c_uint64 * (2 * cap))()
@@ -314,6 +339,15 @@ class Problem:
         st, ev = tl_trace_last_solve(self.h, level)
         _check(st, "tl_trace_last_solve")
         return ev
+
+    def checkpoint(self):
+        """The problem's state between macro steps as an opaque byte buffer."""
+        st, buf = tl_checkpoint_save(self.h)
+        _check(st, "tl_checkpoint_save")
+        return buf
+
+    def restore(self, buf):
+        _check(tl_checkpoint_load(self.h, buf), "tl_checkpoint_load")
 
     def close(self):
         if self.h:

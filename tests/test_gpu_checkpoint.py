@@ -1,0 +1,72 @@
+"""Checkpoint / resume: a run stopped between macro steps, saved, restored
+into a fresh problem and continued is bit-identical to one that never
+stopped (temperatures, origin, states, counters and energy account)."""
+import numpy as np
+import pytest
+
+from paper_2110_12932_gb300 import build as tlbuild
+from paper_2110_12932_gb300 import tl, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    tlbuild.build()
+    return tl.load()
+
+
+def snapshot(p):
+    Tf, org = p.temperature(tl.TL_FINE)
+    Tc, _ = p.temperature(tl.TL_COARSE)
+    st = p.stats()
+    keep = {k: v for k, v in st.items() if k not in ("launches", "time")}
+    return Tf, tuple(org), Tc, p.state(tl.TL_FINE), p.state(tl.TL_COARSE), keep
+
+
+@pytest.mark.parametrize("precision", [tl.TL_FP64, tl.TL_FP32_REFINED])
+def test_resume_is_bit_identical(precision):
+    cfg = workloads.workload("single_track_tiny", precision=precision,
+                             tol=1e-12 if precision == tl.TL_FP64 else 1e-10)
+    a = tl.Problem(cfg)
+    a.macro_steps(24)
+    ref = snapshot(a)
+    a.close()
+
+    b = tl.Problem(cfg)
+    b.macro_steps(11)
+    buf = b.checkpoint()
+    b.close()
+    c = tl.Problem(cfg)
+    c.restore(buf)
+    c.macro_steps(13)
+    got = snapshot(c)
+    c.close()
+    for x, y in zip(ref[:5], got[:5]):
+        if isinstance(x, np.ndarray):
+            assert np.array_equal(x, y)
+        else:
+            assert x == y
+    assert ref[5] == got[5]
+
+
+def test_checkpoint_errors():
+    cfg = workloads.workload("single_track_tiny")
+    p = tl.Problem(cfg)
+    p.macro_steps(2)
+    buf = p.checkpoint()
+    p.predict()  # inside a macro step: no checkpoint, no restore
+    st, _ = tl.tl_checkpoint_save(p.h)
+    assert st == tl.TL_ESTATE
+    assert tl.tl_checkpoint_load(p.h, buf) == tl.TL_ESTATE
+    p.close()
+    q = tl.Problem(dict(cfg, pNXc=3))  # another patch size: rejected
+    assert tl.tl_checkpoint_load(q.h, buf) == tl.TL_EINVAL
+    assert tl.tl_checkpoint_load(q.h, buf[:-1]) == tl.TL_EINVAL
+    q.close()
+    r = tl.Problem(cfg)
+    bad = buf.copy()
+    bad[0] ^= 0xFF  # not a checkpoint
+    assert tl.tl_checkpoint_load(r.h, bad) == tl.TL_EINVAL
+    r.restore(buf)
+    r.close()
