@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
     ap.add_argument("--mem-cap-gb", type=float, default=120.0)
     ap.add_argument("--launches-per-round", type=int, default=10)
+    ap.add_argument("--inner-tiles", type=int, default=0, choices=[0, 1, 2],
+                    help="batch / serve: tiling of the FP32 inner CG (0 by mesh size, 1 element tiles, 2 wide tiles)")
     return ap.parse_args()
 
 
@@ -358,7 +360,7 @@ def run_batch(args):
     # jobs are dealt round-robin to the ranks (no exchange between them)
     jobs = ranks.deal(workloads.batch_jobs(args.jobs), rank, ws)
     for j in jobs:
-        j.update(precision=1, tol=1e-10, tol_inner=1e-5)
+        j.update(precision=1, tol=1e-10, tol_inner=1e-5, inner_tiles=args.inner_tiles)
     work = sum(fine_nodes(j) * j["m"] * j["macro_steps"] for j in jobs)
 
     # warm-up: one short batch
@@ -436,6 +438,7 @@ def run_batch(args):
                 "config": {"workload": f"batch_jobs({args.jobs}, seed 20211025)", "jobs": len(jobs),
                            "fine_dof_substeps": total_work, "precision": "fp32_refined", "tol": 1e-10,
                            "launches_per_round": args.launches_per_round, "graph_mode": info["graph_mode"],
+                           "inner_tiles": args.inner_tiles,
                            "step": "one batched cooperative launch (each job's next solve)"},
                 "gpu_launches": launches, "clocks": clk, "wall_s": wall,
                 "all_ok": all(s == 0 for s in status),
@@ -484,6 +487,8 @@ def run_serve(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     arrivals = ranks.deal(workloads.serving_arrivals(args.rate, args.duration), rank, ws)
+    for _, c in arrivals:
+        c["inner_tiles"] = args.inner_tiles
     work = sum(fine_nodes(c) * c["m"] * c["macro_steps"] for _, c in arrivals)
     srv = serve.Server(mem_cap_bytes=args.mem_cap_gb * 1e9, max_jobs=256,
                        launches_per_round=args.launches_per_round, stream=sp)

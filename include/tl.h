@@ -96,7 +96,8 @@ typedef struct {
   double tol;             /* relative residual of each solve (FP64 measure)    */
   double tol_inner;       /* relative residual of each FP32 inner solve        */
   int max_iter;           /* CG iteration cap per solve (inner cap when refined) */
-  /* refined path, tiling of the FP32 inner CG: 0 = chosen by mesh size,
+  /* refined path, tiling of the FP32 inner CG: 0 = chosen per solve from the
+   * elements each block of the grid (or batch slice) gets (wide from 1024),
    * 1 = element tiles of up to 16 x 8 x ez with the vector update fused into
    * the apply (one grid barrier per iteration; small meshes), 2 = wide tiles
    * of up to 64 x 4 x ez with a separate streaming update (two barriers per

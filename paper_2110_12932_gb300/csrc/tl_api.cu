@@ -213,10 +213,19 @@ Tiling wide_tiling(const Grid3& g, int /*nblk*/) {
   return Tiling{AX, AY, ez, ntx, nty, (g.nz + ez - 1) / ez};
 }
 
-// With inner_tiles = 0 the refined path switches its inner CG to wide tiles
-// from this many elements (measured crossover: the fused element-tile CG is
-// faster at 1.3e5 elements, the wide two-phase CG at 1.0e6).
-constexpr long long WIDE_MIN_ELEMS = 1LL << 19;
+// With inner_tiles = 0 the refined path runs its inner CG on wide tiles when
+// the mesh gives the blocks that solve it at least this many elements each.
+// Measured: the fused element-tile CG is faster with 256 elements per block
+// (10 mm patch on the whole GPU; a batch job alone), the wide two-phase CG
+// with 1.7e3 (20 mm patch), 1.4e4 (256 x 256 x 128) and ~2e4 (crowded batch
+// rounds, 64 jobs).
+constexpr long long WIDE_MIN_ELEMS_PER_BLOCK = 1024;
+
+bool use_wide(const tl_config& c, const Grid3& g, int blocks) {
+  if (c.precision != TL_FP32_REFINED) return false;
+  if (c.inner_tiles != 0) return c.inner_tiles == 2;
+  return (long long)g.nx * g.ny * g.nz >= WIDE_MIN_ELEMS_PER_BLOCK * std::max(1, blocks);
+}
 
 tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
   const size_t nn = (size_t)L.g.nnx * L.g.nny * L.g.nnz;
@@ -721,9 +730,7 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   F.grid = std::min(p->max_coop, F.t.ntx * F.t.nty * F.t.ntz);
   p->red_stride = std::max(C.grid, F.grid);
   for (Level* L : {&C, &F}) {
-    const long long ne = (long long)L->g.nx * L->g.ny * L->g.nz;
-    L->wide = c.precision == TL_FP32_REFINED &&
-              (c.inner_tiles == 2 || (c.inner_tiles == 0 && ne >= WIDE_MIN_ELEMS));
+    L->wide = use_wide(c, L->g, L->grid);
     if (L->wide) L->tw = wide_tiling(L->g, L->grid);
   }
   if ((s = alloc_level(p, C, true)) != TL_OK || (s = alloc_level(p, F, false)) != TL_OK ||
@@ -1223,11 +1230,15 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
       choose_tiling(tmpc, nb[q], 1);
       choose_tiling(tmpf, nb[q], 1);
       SolveArgs* args = b->h_args + (size_t)q * b->R;
-      const Tiling twc = j.p->C.wide ? wide_tiling(tmpc.g, nb[q]) : Tiling{};
-      const Tiling twf = j.p->Fi.wide ? wide_tiling(tmpf.g, nb[q]) : Tiling{};
+      // inner CG tiling for the slice: wide tiles when the slice is crowded
+      const bool wc = use_wide(j.p->cfg, tmpc.g, nb[q]), wf = use_wide(j.p->cfg, tmpf.g, nb[q]);
+      const Tiling twc = wc ? wide_tiling(tmpc.g, nb[q]) : Tiling{};
+      const Tiling twf = wf ? wide_tiling(tmpf.g, nb[q]) : Tiling{};
       for (int sv = 0; sv < tab.nsolves[q]; ++sv) {
-        args[sv].t = (args[sv].level == 1) ? tmpf.t : tmpc.t;
-        args[sv].tw = (args[sv].level == 1) ? twf : twc;
+        const bool fine = args[sv].level == 1;
+        args[sv].t = fine ? tmpf.t : tmpc.t;
+        args[sv].wide = fine ? wf : wc;
+        args[sv].tw = fine ? twf : twc;
       }
       ++q;
     }
