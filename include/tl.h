@@ -103,6 +103,15 @@ typedef struct {
    * of up to 64 x 4 x ez with a separate streaming update (two barriers per
    * iteration; large meshes).  Ignored by TL_FP64. */
   int inner_tiles;
+  /* iterated two-level coupling at the correction step (the local and global
+   * problems solved in turn until they agree): after the correction, the last
+   * micro step is solved again from its start with the corrected coarse field
+   * in place of the predictor in its Dirichlet data, injected, and the
+   * correction redone from T+^n, until max|T+ change| <= coupling_tol max|T+|
+   * or coupling_sweeps corrections were made.  coupling_sweeps <= 1: the
+   * plain one-pass correction.  Not available in batches. */
+  int coupling_sweeps;
+  double coupling_tol;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
   /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks
    * must be 16-byte aligned (else tl_create_problem returns TL_EINVAL) */
@@ -127,6 +136,7 @@ typedef struct {
   double energy_fine_stored, energy_fine_laser, energy_fine_flux;
   double energy_coarse_stored, energy_coarse_laser, energy_coarse_flux;
   double time;                               /* simulated time t_n [s]         */
+  int64_t coupling_resolves;                 /* extra corrections of the iterated coupling */
 } tl_stats;
 
 /* Validate *cfg, allocate and initialise (T = T0 on both levels, states by
@@ -285,7 +295,6 @@ typedef struct {
 tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double* T_in, double* T_out,
                               uint8_t* state, void* stream);
 
-/* Release every device buffer of the problem; NULL is ignored. */
 /* ---- Checkpoint / resume -------------------------------------------------
  * At a macro-step boundary (before PREDICT) the whole state of a problem is:
  * the coarse field T+^n, the fine patch field and its origin, the coarse
@@ -302,6 +311,7 @@ tl_status tl_checkpoint_size(const tl_problem* p, size_t* bytes);
 tl_status tl_checkpoint_save(const tl_problem* p, void* host_out, size_t bytes);
 tl_status tl_checkpoint_load(tl_problem* p, const void* host_in, size_t bytes);
 
+/* Release every device buffer of the problem; NULL is ignored. */
 void tl_destroy_problem(tl_problem* p);
 
 /* Static description of a status code. */

@@ -32,6 +32,15 @@ One macro step t_n -> t_n + Dt (Algorithm 1), this oracle's reading:
   4. Correction: inject the fine values at the coarse nodes that coincide
      with free fine nodes, then redo the coarse backward-Euler step from
      T+^n with those nodes held as Dirichlet data -> T+^{n+1}.
+  5. Iterated coupling (coupling_sweeps > 1; the paper solves the local and
+     global problems of the correction step iteratively until convergence,
+     Section 3 after Eq. localProblem, and Algorithm 1's correction step):
+     re-solve the last micro step from its starting fine field and states
+     with the corrected coarse field in place of T~+ in its Dirichlet data,
+     inject again and redo step 4 from T+^n (coarse states as at t_n), until
+     max|T+^{n+1,(k)} - T+^{n+1,(k-1)}| <= coupling_tol max|T+^{n+1,(k)}| or
+     coupling_sweeps corrections were made.  Only the final solves count in
+     the energy account.
 
 Coefficients are lagged: each backward-Euler step evaluates rho c_e and k_e
 at the element mean of the step's starting temperature and the element's
@@ -376,15 +385,18 @@ class TwoLevel:
         self._I_now = None
         self._I_pred = None
 
-    def fine_substep(self, i):
+    def fine_substep(self, i, coarse_end=None):
+        """Micro step i; coarse_end replaces the predictor T~+ in the
+        Dirichlet data (re-solves of the iterated coupling)."""
         c = self.cfg
         mesh = self.fine_mesh()
         if self._I_now is None:
             self._I_now = self._interp_fine(self.Tc, self.origin)
             self._I_pred = self._interp_fine(self.Tc_pred, self.origin)
+        I_end = self._I_pred if coarse_end is None else self._interp_fine(coarse_end, self.origin)
         w = (i / self.m) if int(c.get("bc_weight_literal", 0)) else ((i + 1) / self.m)
         idx, on_bottom = self.fine_dirichlet()
-        g = (1.0 - w) * self._I_now[idx] + w * self._I_pred[idx]
+        g = (1.0 - w) * self._I_now[idx] + w * I_end[idx]
         g[on_bottom] = c["T_bottom"]
         st = self.fine_state()
         st_flat = st.reshape(-1)
@@ -393,17 +405,58 @@ class TwoLevel:
         t = (self.n * self.m + i + 1) * self.dt
         F = self.fine_load(mesh, t)
         Tn = be_step(mesh, self.Tf, rc / self.dt, k, F, idx, g)
+        if i == self.m - 1:  # start of the last micro step: what a coupling re-solve starts from
+            self._last_start = (self.Tf.copy(), st.copy())
         if self.track_energy:
             e = energy_terms(mesh, self.Tf, Tn, rc / self.dt, k, F, idx, self.dt)
-            self.energy["fine_stored"] += e["stored"]
-            self.energy["fine_laser"] += e["laser"]
-            self.energy["fine_flux"] += e["flux"]
-            self.step_energy.append(("fine", e))
+            self._add_energy("fine", e)
+            self._last_fine_e = e
         new_state = self.mat.update_state(mesh.element_mean(Tn), st_flat)
         st[...] = new_state.reshape(st.shape)
         self.Tf = Tn
 
+    def _add_energy(self, level, e, sign=1.0):
+        for key in ("stored", "laser", "flux"):
+            self.energy[f"{level}_{key}"] += sign * e[key]
+        if sign > 0:
+            self.step_energy.append((level, e))
+        else:  # the superseded solve is the latest entry of its level
+            for j in range(len(self.step_energy) - 1, -1, -1):
+                if self.step_energy[j][0] == level:
+                    del self.step_energy[j]
+                    break
+
     def restrict_and_correct(self):
+        """Steps 4 and 5: correction, iterated with re-solves of the last
+        micro step while coupling_sweeps allows and the coarse field moves."""
+        c = self.cfg
+        sweeps = int(c.get("coupling_sweeps", 1))
+        tol = float(c.get("coupling_tol", 1e-10))
+        Tn, state, e = self._correction()
+        self.coupling_history = []
+        for _ in range(1, sweeps):
+            # last micro step again, from its start, ending on the corrected field
+            T0f, st0 = self._last_start
+            self.fine_state()[...] = st0
+            self.Tf = T0f.copy()
+            if self.track_energy:
+                self._add_energy("fine", self._last_fine_e, sign=-1.0)
+            self.fine_substep(self.m - 1, coarse_end=Tn)
+            Tk, state_k, e_k = self._correction()
+            diff = float(np.max(np.abs(Tk - Tn)) / np.max(np.abs(Tk)))
+            self.coupling_history.append(diff)
+            Tn, state, e = Tk, state_k, e_k
+            if diff <= tol:
+                break
+        if self.track_energy:
+            self._add_energy("coarse", e)
+        self.state_c = state
+        self.Tc = Tn
+        self.Tc_pred = None
+
+    def _correction(self):
+        """Injection and the coarse re-solve from T+^n (step 4), not committed:
+        returns (T+^{n+1}, coarse states, energy terms or None)."""
         c = self.cfg
         (i0, i1), (j0, j1), (k0, k1) = self.injection_box()
         I, J, K = np.meshgrid(np.arange(i0, i1 + 1), np.arange(j0, j1 + 1),
@@ -419,15 +472,8 @@ class TwoLevel:
         dir_idx = np.concatenate([self.coarse_bottom, inj_idx])
         g = np.concatenate([np.full(len(self.coarse_bottom), float(c["T_bottom"])), inj_vals])
         Tn = be_step(self.coarse, self.Tc, rc / self.Dt, k, F, dir_idx, g)
-        if self.track_energy:
-            e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt)
-            self.energy["coarse_stored"] += e["stored"]
-            self.energy["coarse_laser"] += e["laser"]
-            self.energy["coarse_flux"] += e["flux"]
-            self.step_energy.append(("coarse", e))
-        self.state_c = self.mat.update_state(self.coarse.element_mean(Tn), self.state_c)
-        self.Tc = Tn
-        self.Tc_pred = None
+        e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt) if self.track_energy else None
+        return Tn, self.mat.update_state(self.coarse.element_mean(Tn), self.state_c), e
 
     def macro_step(self):
         self.predict()

@@ -60,6 +60,9 @@ struct Level {
   float* dinv32 = nullptr;
   float* sk32 = nullptr;
   double* inj = nullptr;  // coarse only
+  double* T3 = nullptr;   // iterated coupling (coarse): the corrected fields of two consecutive sweeps
+  double* T3b = nullptr;
+  uint8_t* state_snap = nullptr;  // iterated coupling: states before the superseded solve (fine: patch window)
   unsigned long long* trace = nullptr;  // phase timestamps of the level's last solve
   uint8_t* state = nullptr;
   int st_sx = 0, st_sy = 0, st_sz = 0;
@@ -86,6 +89,8 @@ struct tl_problem {
   float* red32 = nullptr;
   int red_stride = 0;
   DevStats* stats = nullptr;
+  unsigned long long* d_diff = nullptr;  // iterated coupling: max |change|, max |T+| (IEEE bits)
+  long long coupling_resolves = 0;
   std::vector<void*> allocs;
   int nsm = 0, max_coop = 0;
 };
@@ -268,6 +273,13 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
     if ((s = alloc_n(p, &L.sk32, 2 * ne)) != TL_OK) return s;
   }
   if (coarse && (s = alloc_n(p, &L.inj, nn)) != TL_OK) return s;
+  if (p->cfg.coupling_sweeps > 1) {
+    if (coarse) {
+      if ((s = alloc_n(p, &L.T3, nn)) != TL_OK) return s;
+      if ((s = alloc_n(p, &L.T3b, nn)) != TL_OK) return s;
+    }
+    if ((s = alloc_n(p, &L.state_snap, ne)) != TL_OK) return s;
+  }
   if ((s = alloc_n(p, &L.trace, 2 * TRACE_CAP)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.state, (size_t)L.st_sx * L.st_sy * L.st_sz)) != TL_OK) return s;
   return TL_OK;
@@ -551,6 +563,7 @@ tl_status validate(const tl_config* c) {
   if (c->precision != TL_FP64 && c->precision != TL_FP32_REFINED) return TL_EINVAL;
   if (c->precision == TL_FP32_REFINED && !(c->tol_inner > 0 && c->tol_inner < 1)) return TL_EINVAL;
   if (c->inner_tiles < 0 || c->inner_tiles > 2) return TL_EINVAL;
+  if (c->coupling_sweeps > 1 && !(c->coupling_tol > 0)) return TL_EINVAL;
   if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
   for (int j = 0; j < c->ntracks; ++j) {
     const tl_track& k = c->path[j];
@@ -637,6 +650,118 @@ void next_batched_solve(tl_problem* p, SolveArgs& a, long long* weight) {
   p->phase = NEED_PREDICT;
   p->n++;
   *weight = (long long)p->C.g.nx * p->C.g.ny * p->C.g.nz;
+}
+
+
+// Injection of the fine field at the coarse nodes that coincide with free
+// fine nodes (into the coarse level's `inj`).
+tl_status launch_restrict(tl_problem* p) {
+  int box[6];
+  injection_box(p, box);
+  if (box[0] <= box[1] && box[2] <= box[3] && box[4] <= box[5]) {
+    long long nb = (long long)(box[1] - box[0] + 1) * (box[3] - box[2] + 1) * (box[5] - box[4] + 1);
+    int blocks = (int)std::min<long long>(1024, (nb + 255) / 256);
+    restrict_kernel<<<blocks, 256, 0, p->stream>>>(p->Fi.g, p->C.g, p->Fi.T, p->C.inj, box[0], box[1], box[2],
+                                                   box[3], box[4], box[5], p->oi, p->oj, p->ok, p->cfg.r);
+    p->launches++;
+    return cuda_status(cudaGetLastError());
+  }
+  return TL_OK;
+}
+
+// The fine element states of the patch window <-> the compact snapshot
+// (a fine solve changes no other entry of the plate-wide map).
+tl_status copy_state_window(tl_problem* p, bool save) {
+  Level& F = p->Fi;
+  const size_t ox = (size_t)p->oi * p->cfg.r, oy = (size_t)p->oj * p->cfg.r;
+  for (int k = 0; k < F.g.nz; ++k) {
+    uint8_t* win = F.state + (size_t)F.st_sx * F.st_sy * k + oy * F.st_sx + ox;
+    uint8_t* cmp = F.state_snap + (size_t)F.g.nx * F.g.ny * k;
+    cudaError_t e = save ? cudaMemcpy2DAsync(cmp, (size_t)F.g.nx, win, (size_t)F.st_sx, (size_t)F.g.nx,
+                                             (size_t)F.g.ny, cudaMemcpyDeviceToDevice, p->stream)
+                         : cudaMemcpy2DAsync(win, (size_t)F.st_sx, cmp, (size_t)F.g.nx, (size_t)F.g.nx,
+                                             (size_t)F.g.ny, cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return TL_OK;
+}
+
+// Iterated coupling: the start of the last micro step (fine field into the
+// move buffer T2, which is free between patch moves; states of the window).
+tl_status save_last_start(tl_problem* p) {
+  Level& F = p->Fi;
+  const size_t nf = (size_t)F.g.nnx * F.g.nny * F.g.nnz;
+  cudaError_t e = cudaMemcpyAsync(F.T2, F.T, nf * sizeof(double), cudaMemcpyDeviceToDevice, p->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return copy_state_window(p, true);
+}
+
+// The correction step with the iterated coupling: correction into T3; then,
+// while sweeps remain and the corrected field still moves by more than
+// coupling_tol of its size, the last micro step again from its start with the
+// corrected field as its end data, injection, and the correction again from
+// T+^n with the coarse states of t_n.  Superseded solves leave the energy
+// account.  The final corrected field becomes T+^{n+1}.  After a failed
+// solve (sticky device status) the coarse field is left at T+^n.
+tl_status coupled_correct(tl_problem* p) {
+  const tl_config& c = p->cfg;
+  Level& C = p->C;
+  Level& F = p->Fi;
+  const size_t nc = (size_t)C.g.nnx * C.g.nny * C.g.nnz, ec = (size_t)C.g.nx * C.g.ny * C.g.nz;
+  const size_t nf = (size_t)F.g.nnx * F.g.nny * F.g.nnz;
+  cudaError_t e = cudaMemcpyAsync(C.state_snap, C.state, ec, cudaMemcpyDeviceToDevice, p->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  double* cur = C.T3;
+  double* prev = C.T3b;
+  SolveArgs a{};
+  build_coarse_args(p, true, false, a);
+  a.T_out = cur;
+  tl_status s = launch_solve(p, C, a);
+  if (s != TL_OK) return s;
+  int st = 0;
+  for (int k = 1; k < c.coupling_sweeps; ++k) {
+    if ((s = copy_state_window(p, false)) != TL_OK) return s;
+    e = cudaMemcpyAsync(F.T, F.T2, nf * sizeof(double), cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (c.energy) {
+      energy_rollback_kernel<<<1, 32, 0, p->stream>>>(p->stats, 1);
+      p->launches++;
+    }
+    SolveArgs af{};
+    build_fine_args(p, c.m - 1, af);
+    af.dv.Tc1 = cur;
+    if ((s = launch_solve(p, F, af)) != TL_OK) return s;
+    if ((s = launch_restrict(p)) != TL_OK) return s;
+    e = cudaMemcpyAsync(C.state, C.state_snap, ec, cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (c.energy) {
+      energy_rollback_kernel<<<1, 32, 0, p->stream>>>(p->stats, 0);
+      p->launches++;
+    }
+    SolveArgs ac{};
+    build_coarse_args(p, true, false, ac);
+    ac.T_out = prev;
+    if ((s = launch_solve(p, C, ac)) != TL_OK) return s;
+    std::swap(cur, prev);
+    p->coupling_resolves++;
+    e = cudaMemsetAsync(p->d_diff, 0, 2 * sizeof(unsigned long long), p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int blocks = (int)std::min<size_t>(1024, (nc + 255) / 256);
+    max_diff_kernel<<<blocks, 256, 0, p->stream>>>(cur, prev, (long long)nc, p->d_diff);
+    p->launches++;
+    unsigned long long h[2] = {0, 0};
+    e = cudaMemcpyAsync(h, p->d_diff, sizeof h, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, p->status, sizeof st, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (st != 0) return TL_OK;  // reported by tl_sync; T+^n kept
+    double d, m;
+    std::memcpy(&d, &h[0], sizeof d);
+    std::memcpy(&m, &h[1], sizeof m);
+    if (d <= c.coupling_tol * m) break;
+  }
+  e = cudaMemcpyAsync(C.T, cur, nc * sizeof(double), cudaMemcpyDeviceToDevice, p->stream);
+  return cuda_status(e);
 }
 
 }  // namespace
@@ -737,7 +862,7 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
       (s = alloc_n(p, &p->bar, BAR_WORDS)) != TL_OK ||
       (s = alloc_n(p, &p->red, (size_t)RS_N * p->red_stride)) != TL_OK ||
       (s = alloc_n(p, &p->red32, (size_t)RS_N * p->red_stride)) != TL_OK ||
-      (s = alloc_n(p, &p->stats, 1)) != TL_OK) {
+      (s = alloc_n(p, &p->stats, 1)) != TL_OK || (s = alloc_n(p, &p->d_diff, 2)) != TL_OK) {
     release(p);
     delete p;
     return s;
@@ -799,7 +924,7 @@ tl_status tl_coarse_step(tl_problem* p, tl_phase phase) {
   }
   if (phase == TL_CORRECT) {
     if (p->phase != NEED_CORRECT) return TL_ESTATE;
-    tl_status s = coarse_solve(p, true);
+    tl_status s = p->cfg.coupling_sweeps > 1 ? coupled_correct(p) : coarse_solve(p, true);
     if (s != TL_OK) return s;
     p->phase = NEED_PREDICT;
     p->n++;
@@ -812,6 +937,10 @@ tl_status tl_fine_substeps(tl_problem* p, int nsub) {
   if (!p || nsub < 0) return TL_EINVAL;
   if (p->phase != IN_SUBSTEPS || p->sub + nsub > p->cfg.m) return TL_ESTATE;
   for (int k = 0; k < nsub; ++k) {
+    if (p->cfg.coupling_sweeps > 1 && p->sub == p->cfg.m - 1) {
+      tl_status s = save_last_start(p);
+      if (s != TL_OK) return s;
+    }
     tl_status s = fine_solve(p, p->sub);
     if (s != TL_OK) return s;
     p->sub++;
@@ -822,17 +951,8 @@ tl_status tl_fine_substeps(tl_problem* p, int nsub) {
 tl_status tl_restrict(tl_problem* p) {
   if (!p) return TL_EINVAL;
   if (p->phase != IN_SUBSTEPS || p->sub != p->cfg.m) return TL_ESTATE;
-  int box[6];
-  injection_box(p, box);
-  if (box[0] <= box[1] && box[2] <= box[3] && box[4] <= box[5]) {
-    long long nb = (long long)(box[1] - box[0] + 1) * (box[3] - box[2] + 1) * (box[5] - box[4] + 1);
-    int blocks = (int)std::min<long long>(1024, (nb + 255) / 256);
-    restrict_kernel<<<blocks, 256, 0, p->stream>>>(p->Fi.g, p->C.g, p->Fi.T, p->C.inj, box[0], box[1], box[2],
-                                                   box[3], box[4], box[5], p->oi, p->oj, p->ok, p->cfg.r);
-    p->launches++;
-    tl_status s = cuda_status(cudaGetLastError());
-    if (s != TL_OK) return s;
-  }
+  tl_status s = launch_restrict(p);
+  if (s != TL_OK) return s;
   p->phase = NEED_CORRECT;
   return TL_OK;
 }
@@ -912,7 +1032,7 @@ struct CkptHeader {
   uint32_t version, stats_bytes;
   int32_t dims[12];   // NXc NYc NZc, fine nx ny nz, map sx sy sz, r, m, precision
   int32_t n, oi, oj, ok;
-  int64_t patch_moves;
+  int64_t patch_moves, coupling_resolves;
 };
 constexpr uint64_t CKPT_MAGIC = 0x746c636b70743031ull;  // "tlckpt01"
 
@@ -964,6 +1084,7 @@ tl_status tl_checkpoint_save(const tl_problem* p, void* host_out, size_t bytes) 
   h.oj = p->oj;
   h.ok = p->ok;
   h.patch_moves = p->patch_moves;
+  h.coupling_resolves = p->coupling_resolves;
   std::memcpy(b, &h, sizeof h);
   b += sizeof h;
   cudaError_t e = cudaMemcpy(b, C.T, nc * sizeof(double), cudaMemcpyDeviceToHost);
@@ -1010,6 +1131,7 @@ tl_status tl_checkpoint_load(tl_problem* p, const void* host_in, size_t bytes) {
   p->oi = h.oi;
   p->oj = h.oj;
   p->patch_moves = h.patch_moves;
+  p->coupling_resolves = h.coupling_resolves;
   p->sub = 0;
   p->phase = NEED_PREDICT;
   return TL_OK;
@@ -1044,6 +1166,7 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out) {
   out->energy_fine_laser = d.e_laser[1];
   out->energy_fine_flux = d.e_flux[1];
   out->time = p->n * p->cfg.dt_coarse;
+  out->coupling_resolves = p->coupling_resolves;
   return TL_OK;
 }
 
@@ -1112,6 +1235,7 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
 
 tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out) {
   if (!b || !p || macro_steps < 0 || !id_out) return TL_EINVAL;
+  if (p->cfg.coupling_sweeps > 1) return TL_EINVAL;  // batched sequences use the one-pass correction
   if (p->phase != NEED_PREDICT) return TL_ESTATE;  // join only between macro steps
   int active = 0;
   for (const auto& j : b->jobs) active += j.active ? 1 : 0;

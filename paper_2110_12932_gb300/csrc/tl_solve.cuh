@@ -244,6 +244,7 @@ struct DevStats {
   double e_stored[2], e_laser[2], e_flux[2];
   long long iters[2], solves[2], outer[2];
   int max_iters[2], last_iters[2];
+  double e_last[2][3];  // the last solve's stored / laser / flux terms per level (for rollback)
 };
 
 // Converts eight Hadamard factors (index = x mode + 2 y mode + 4 z mode) to
@@ -1636,6 +1637,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
         a.stats->e_stored[lvl] += te[0];
         a.stats->e_laser[lvl] += te[1];
         a.stats->e_flux[lvl] += te[2];
+        a.stats->e_last[lvl][0] = te[0];
+        a.stats->e_last[lvl][1] = te[1];
+        a.stats->e_last[lvl][2] = te[2];
       }
     }
   }
@@ -1741,6 +1745,38 @@ __global__ void restrict_kernel(Grid3 fg, Grid3 cg, const double* __restrict__ T
        n += (long long)gridDim.x * blockDim.x) {
     int I = bi0 + (int)(n % bx), J = bj0 + (int)((n / bx) % by), K = bk0 + (int)(n / ((long long)bx * by));
     inj[node_id(cg, I, J, K)] = Tf[node_id(fg, (I - oi) * r, (J - oj) * r, (K - ok) * r)];
+  }
+}
+
+// Takes the last solve of a level out of the energy account (a solve the
+// iterated coupling supersedes).  One thread.
+__global__ void energy_rollback_kernel(DevStats* s, int lvl) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s->e_stored[lvl] -= s->e_last[lvl][0];
+    s->e_laser[lvl] -= s->e_last[lvl][1];
+    s->e_flux[lvl] -= s->e_last[lvl][2];
+  }
+}
+
+// out[0] = max |a - b|, out[1] = max |a| as IEEE bit patterns (the order of
+// non-negative doubles is the order of their patterns, so the atomic maximum
+// is exact and independent of the schedule).  out must start at zero.
+__global__ void max_diff_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                                unsigned long long* out) {
+  double d = 0.0, m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = a[i];
+    d = fmax(d, fabs(x - b[i]));
+    m = fmax(m, fabs(x));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(d));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(m));
   }
 }
 

@@ -46,6 +46,7 @@ class tl_config(C.Structure):
         ("coarse_source", C.c_int), ("bc_weight_literal", C.c_int), ("energy", C.c_int),
         ("precision", C.c_int), ("tol", C.c_double), ("tol_inner", C.c_double),
         ("max_iter", C.c_int), ("inner_tiles", C.c_int),
+        ("coupling_sweeps", C.c_int), ("coupling_tol", C.c_double),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
@@ -66,6 +67,7 @@ class tl_stats(C.Structure):
         ("energy_coarse_stored", C.c_double), ("energy_coarse_laser", C.c_double),
         ("energy_coarse_flux", C.c_double),
         ("time", C.c_double),
+        ("coupling_resolves", C.c_int64),
     ]
 
 

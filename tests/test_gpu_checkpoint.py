@@ -24,10 +24,10 @@ def snapshot(p):
     return Tf, tuple(org), Tc, p.state(tl.TL_FINE), p.state(tl.TL_COARSE), keep
 
 
-@pytest.mark.parametrize("precision", [tl.TL_FP64, tl.TL_FP32_REFINED])
-def test_resume_is_bit_identical(precision):
+@pytest.mark.parametrize("precision,sweeps", [(tl.TL_FP64, 1), (tl.TL_FP32_REFINED, 1), (tl.TL_FP64, 4)])
+def test_resume_is_bit_identical(precision, sweeps):
     cfg = workloads.workload("single_track_tiny", precision=precision,
-                             tol=1e-12 if precision == tl.TL_FP64 else 1e-10)
+                             tol=1e-12 if precision == tl.TL_FP64 else 1e-10, coupling_sweeps=sweeps)
     a = tl.Problem(cfg)
     a.macro_steps(24)
     ref = snapshot(a)

@@ -286,3 +286,51 @@ def test_refined_20mm_full_size_against_fp64_gpu_path():
     for lvl in ("fine", "coarse"):
         s_, l_, f_ = (st[f"energy_{lvl}_{k}"] for k in ("stored", "laser", "flux"))
         assert abs(s_ - l_ - f_) <= 1e-7 * max(abs(s_), abs(l_)), lvl
+
+
+# ---- iterated two-level coupling at the correction step ---------------------
+
+@pytest.mark.parametrize("precision", [tl.TL_FP64, tl.TL_FP32_REFINED])
+def test_coupled_correction_against_oracle(precision):
+    cfg = workloads.workload("single_track_tiny", coupling_sweeps=6, coupling_tol=1e-10, precision=precision,
+                             tol=1e-12 if precision == tl.TL_FP64 else 1e-10)
+    bar = TOL if precision == tl.TL_FP64 else REFINED_TOL
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg)
+    for _ in range(4):
+        prob.macro_steps(5)
+        ref.run(5)
+        Tf, org = prob.temperature(tl.TL_FINE)
+        Tc, _ = prob.temperature(tl.TL_COARSE)
+        assert tuple(org) == tuple(ref.origin)
+        assert rel(Tf, ref.Tf) <= bar and rel(Tc, ref.Tc) <= bar
+        assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+        assert np.array_equal(prob.state(tl.TL_COARSE), ref.state_c)
+    st = prob.stats()
+    assert st["coupling_resolves"] >= 20  # at least one re-solve per macro step
+    for lvl in ("fine", "coarse"):
+        for k in ("stored", "laser", "flux"):
+            o = ref.energy[f"{lvl}_{k}"]
+            assert abs(st[f"energy_{lvl}_{k}"] - o) <= 1e-7 * max(abs(o), abs(ref.energy[f"{lvl}_laser"]))
+    prob.close()
+
+
+def test_coupled_correction_multitrack_first_macro_step():
+    cfg = workloads.workload("multitrack_10mm", coupling_sweeps=2, coupling_tol=1e-10)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    prob.macro_steps(1)
+    ref.run(1)
+    compare(prob, ref, "coupled macro 1")
+    assert prob.stats()["coupling_resolves"] >= 1
+    prob.close()
+
+
+def test_coupled_problems_stay_out_of_batches():
+    cfg = workloads.workload("single_track_tiny", coupling_sweeps=3)
+    p = tl.Problem(cfg)
+    b = tl.Batch(launches_per_round=2, max_jobs=2)
+    with pytest.raises(tl.TLError):
+        b.add(p, 2)
+    b.close()
+    p.close()

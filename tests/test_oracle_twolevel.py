@@ -186,3 +186,68 @@ def test_error_grows_with_time_ratio():
         errs.append(np.linalg.norm(o.Tf - Tref) / np.linalg.norm(Tref))
     assert errs[0] < 1e-12, errs
     assert errs[0] < errs[1] < errs[2] < errs[3], errs
+
+
+# ---- iterated two-level coupling at the correction step ---------------------
+
+def _run(cfg, n, energy=False):
+    o = TL.TwoLevel(cfg, energy=energy)
+    hist = []
+    for _ in range(n):
+        o.macro_step()
+        hist.append(list(getattr(o, "coupling_history", [])))
+    return o, hist
+
+
+def test_coupling_one_sweep_is_the_plain_correction():
+    cfg = W.single_track_tiny()
+    a, _ = _run(cfg, 6)
+    b, _ = _run(dict(cfg, coupling_sweeps=1), 6)
+    assert np.array_equal(a.Tc, b.Tc) and np.array_equal(a.Tf, b.Tf)
+
+
+def test_coupling_contracts_to_a_fixed_point():
+    """The sweeps of the coupled correction contract: every change of the
+    coarse field is smaller than the previous one and the last is below the
+    tolerance; the converged field differs from the one-sweep correction by a
+    small but non-zero amount (the iteration does something)."""
+    cfg = W.single_track_tiny()
+    one, _ = _run(cfg, 8)
+    it, hist = _run(dict(cfg, coupling_sweeps=30, coupling_tol=1e-13), 8)
+    for h in hist:
+        assert len(h) >= 1 and h[-1] <= 1e-13
+        assert all(b < a for a, b in zip(h, h[1:])), h
+    d = np.linalg.norm(it.Tc - one.Tc) / np.linalg.norm(one.Tc)
+    assert 1e-12 < d < 1e-3, d
+
+
+def test_coupling_keeps_the_unit_ratio_identity():
+    """r = m = 1 with the Gaussian on both levels: the corrected field equals
+    the predictor, so re-solving reproduces the same fine field and the first
+    re-solve already meets any tolerance; the result stays the single-level
+    solve."""
+    cfg = W.single_track_tiny()
+    cfg.update(r=1, m=1, coarse_source=1, pNXc=6, pNYc=4, pNZc=2, coupling_sweeps=5, coupling_tol=1e-12)
+    o = TL.TwoLevel(cfg)
+    sl = TL.SingleLevel(cfg, cfg["NXc"], cfg["NYc"], cfg["NZc"], cfg["dt_coarse"])
+    for n in range(10):
+        o.macro_step()
+        sl.step()
+        assert len(o.coupling_history) == 1 and o.coupling_history[0] <= 1e-12
+        assert np.linalg.norm(o.Tc - sl.T) / np.linalg.norm(sl.T) < 1e-12
+
+
+def test_coupling_energy_account_counts_final_solves():
+    """With re-solves the account keeps one fine entry per micro step and one
+    coarse entry per correction, and each satisfies the energy identity."""
+    cfg = dict(W.single_track_tiny(), coupling_sweeps=6, coupling_tol=1e-12)
+    o, hist = _run(cfg, 5, energy=True)
+    assert sum(len(h) for h in hist) > 5  # re-solves happened
+    fine = [e for lvl, e in o.step_energy if lvl == "fine"]
+    coarse = [e for lvl, e in o.step_energy if lvl == "coarse"]
+    assert len(fine) == 5 * cfg["m"] and len(coarse) == 5
+    for e in fine + coarse:
+        assert abs(e["stored"] - e["laser"] - e["flux"]) <= 1e-9 * max(abs(e["stored"]), abs(e["laser"]), 1e-30)
+    for lvl in ("fine", "coarse"):
+        tot = sum(e["stored"] for l2, e in o.step_energy if l2 == lvl)
+        assert abs(tot - o.energy[f"{lvl}_stored"]) <= 1e-9 * abs(tot)
