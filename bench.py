@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
     ap.add_argument("--mem-cap-gb", type=float, default=120.0)
     ap.add_argument("--launches-per-round", type=int, default=10)
+    ap.add_argument("--coupling-sweeps", type=int, default=1,
+                    help="plain: corrections of the iterated two-level coupling per macro step (1 = one pass)")
     ap.add_argument("--inner-tiles", type=int, default=0, choices=[0, 1, 2],
                     help="batch / serve: tiling of the FP32 inner CG (0 by mesh size, 1 element tiles, 2 wide tiles)")
     return ap.parse_args()
@@ -264,8 +266,9 @@ def run_ours(args):
     rank, ws, local = dist_setup(args.gpus)
     tlbuild.build()
     tl.load()
-    cfg = workloads.workload(args.workload, precision=0, tol=1e-12)
-    cfg_ref = workloads.workload(args.workload, precision=1, tol=1e-10, tol_inner=1e-5)
+    cfg = workloads.workload(args.workload, precision=0, tol=1e-12, coupling_sweeps=args.coupling_sweeps)
+    cfg_ref = workloads.workload(args.workload, precision=1, tol=1e-10, tol_inner=1e-5,
+                                 coupling_sweeps=args.coupling_sweeps)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     nfn = fine_nodes(cfg)
@@ -349,10 +352,12 @@ def run_ours(args):
                 "config": {"workload": cfg["name"], "fine_nodes": nfn, "fine_elements": ne,
                            "coarse_nodes": (cfg["NXc"] + 1) * (cfg["NYc"] + 1) * (cfg["NZc"] + 1),
                            "m": m, "r": r, "tol": cfg["tol"], "precision": "fp64",
+                           "coupling_sweeps": args.coupling_sweeps,
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "flushed (256 MB write) between timed macro steps, outside the events"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "wall_s": wall,
+                "coupling_resolves_per_step": st.get("coupling_resolves", 0) / max(1, K),
                 "cg_iters": {"fine_per_solve": fine_iters,
                              "coarse_per_solve": st["cg_iters_coarse"] / max(1, st["solves_coarse"])},
                 "fp32_refined": refined}
