@@ -372,11 +372,11 @@ struct Tracer {
 
 template <typename R>
 struct ApplySmem {
-  R X[2][WY][WX];                          // input values of two node layers
-  union {
-    R Z[2][WY][WX];                        // z sum / difference per node column
-    struct { R L[2][TYE][WX]; R H[2][TYE][WX]; } yb;  // y-backward to low / high node row
-  } a;
+  // A window column's input values stay in its thread's registers.  Z and the
+  // y-backward are separate arrays, so that a layer needs no barrier after
+  // its last stage: every array's next write comes after a later barrier.
+  R Z[2][WY][WX];                          // z sum / difference per node column
+  struct { R L[2][TYE][WX]; R H[2][TYE][WX]; } yb;  // y-backward to low / high node row
   R Y[4][TYE][WX];                         // (y,z)-modes per element row x node column
   R XL[4][TYE][TXE];                       // x-backward to the element's left node column
   R XR[4][TYE][TXE];                       // ... and to its right node column
@@ -435,12 +435,10 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
   if (LAM_STAGED && has_e) lam_fetch(welem + ke0 * Se, raw1 + LSLOT * NT);
   cp_async_commit();
   cp_async_wait<1>();
-  int cur = 0;
-  if (has_w) sm.X[cur][wlj][wli] = finish(wnode + ke0 * S, wi, wj, ke0, owned_at(ke0), raw0);
+  R xcur = R(0);  // the column's value at node layer ke
+  if (has_w) xcur = finish(wnode + ke0 * S, wi, wj, ke0, owned_at(ke0), raw0);
   R carry = R(0);
-  __syncthreads();
   for (int ke = ke0; ke < ke1; ++ke) {
-    const int nxt = cur ^ 1;
     // eigenvalues of this layer's element: from registers loaded now (used in
     // stage 3), or built in stage 3 from the staged element data
     R l8[8];
@@ -449,13 +447,13 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
     cp_async_wait<0>();
     R* rnext = ((ke + 1 - ke0) & 1) ? raw1 : raw0;
     R* rfree = ((ke - ke0) & 1) ? raw1 : raw0;
+    const R lo = xcur;
     if (has_w) {
-      R hi = finish(wnode + (ke + 1) * S, wi, wj, ke + 1, owned_at(ke + 1), rnext);
+      const R hi = finish(wnode + (ke + 1) * S, wi, wj, ke + 1, owned_at(ke + 1), rnext);
       if (ke + 2 <= ke1) fetch(wnode + (ke + 2) * S, wi, wj, ke + 2, owned_at(ke + 2), rfree);
-      R lo = sm.X[cur][wlj][wli];
-      sm.X[nxt][wlj][wli] = hi;
-      sm.a.Z[0][wlj][wli] = lo + hi;
-      sm.a.Z[1][wlj][wli] = lo - hi;
+      xcur = hi;
+      sm.Z[0][wlj][wli] = lo + hi;
+      sm.Z[1][wlj][wli] = lo - hi;
     }
     if (LAM_STAGED && has_e) {
       lam(welem + ke * Se, rnext + LSLOT * NT, l8);
@@ -467,7 +465,7 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
     if (has_r) {
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
-        R a = sm.a.Z[z][wlj][wli], b = sm.a.Z[z][wlj + 1][wli];
+        R a = sm.Z[z][wlj][wli], b = sm.Z[z][wlj + 1][wli];
         sm.Y[2 * z][wlj][wli] = a + b;
         sm.Y[2 * z + 1][wlj][wli] = a - b;
       }
@@ -496,27 +494,25 @@ __device__ inline void apply_tile(const Grid3& g, const Tiling& t, int tile, App
       }
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
-        sm.a.yb.L[z][wlj][wli] = B[2 * z] + B[2 * z + 1];
-        sm.a.yb.H[z][wlj][wli] = B[2 * z] - B[2 * z + 1];
+        sm.yb.L[z][wlj][wli] = B[2 * z] + B[2 * z + 1];
+        sm.yb.H[z][wlj][wli] = B[2 * z] - B[2 * z + 1];
       }
     }
     __syncthreads();
     // stage 5: gather y-backward per node column, z-backward, emit layer ke
     if (has_w) {
-      R C0 = wlj < ey ? sm.a.yb.L[0][wlj][wli] : R(0);
-      R C1 = wlj < ey ? sm.a.yb.L[1][wlj][wli] : R(0);
+      R C0 = wlj < ey ? sm.yb.L[0][wlj][wli] : R(0);
+      R C1 = wlj < ey ? sm.yb.L[1][wlj][wli] : R(0);
       if (wlj > 0) {
-        C0 += sm.a.yb.H[0][wlj - 1][wli];
-        C1 += sm.a.yb.H[1][wlj - 1][wli];
+        C0 += sm.yb.H[0][wlj - 1][wli];
+        C1 += sm.yb.H[1][wlj - 1][wli];
       }
-      emit(wnode + ke * S, wslot, carry + (C0 + C1), sm.X[cur][wlj][wli]);
+      emit(wnode + ke * S, wslot, carry + (C0 + C1), lo);
       carry = C0 - C1;
     }
-    __syncthreads();
-    cur = nxt;
   }
   // top node layer of the tile: only the contributions of element layer ke1-1
-  if (has_w) emit(wnode + ke1 * S, wslot | (ke1 < g.nz ? 4 : 0), carry, sm.X[cur][wlj][wli]);
+  if (has_w) emit(wnode + ke1 * S, wslot | (ke1 < g.nz ? 4 : 0), carry, xcur);
   cp_async_wait<0>();
   __syncthreads();
 }
