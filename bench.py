@@ -36,7 +36,7 @@ FLOPS_VEC_PER_NODE = 14     # PCG vector update, fused dots, p = z + beta p
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 fine micro-step launch of
 # this workload, from the ncu capture summarised in
 # profiles/solve_kernel_fp64_multitrack_10mm.md (the patch is L2-resident)
-FINE_LAUNCH_DRAM_BYTES = 4.734208e6 + 2.489344e6
+FINE_LAUNCH_DRAM_BYTES = 4.738304e6 + 2.513920e6
 
 
 def parse():
@@ -129,68 +129,74 @@ def fine_nodes(cfg):
 
 
 def oracle_solves(o):
-    """The oracle's Algorithm-1 sequence one solve at a time: yields the
-    number of fine DOF-substeps each solve advanced (0 for coarse solves)."""
-    nf = fine_nodes(o.cfg)
+    """The oracle's Algorithm-1 sequence one solve at a time: yields "coarse"
+    or "fine" after each solve."""
     while True:
         o.predict()
-        yield 0
+        yield "coarse"
         for i in range(o.m):
             o.fine_substep(i)
-            yield nf
+            yield "fine"
         o.restrict_and_correct()
         o.n += 1
-        yield 0
+        yield "coarse"
 
 
-def cpu_baseline(cfg, budget_s=20.0):
-    """The oracle as it stands, solve by solve through the same workload's
-    sequence (predictor, micro steps, corrector, ...) until the time budget is
-    spent and at least one micro step is done."""
+def oracle_sample(cfg, budget_s, max_solves=None, warmup=0):
+    """Times the oracle solve by solve through the workload's sequence until
+    the budget is spent (with at least one coarse and one fine solve done) and
+    scales the mean solve times to one macro step (2 coarse + m fine solves):
+    returns (fine DOF-substeps/s, solves, coarse solves, fine solves, seconds)."""
     import time as _t
 
     from oracle import twolevel as TL
     o = TL.TwoLevel(cfg, energy=False)
-    t0 = _t.perf_counter()
-    work = solves = 0
-    for w in oracle_solves(o):
-        work += w
-        solves += 1
-        if work > 0 and _t.perf_counter() - t0 > budget_s:
+    seq = oracle_solves(o)
+    for _ in range(warmup):
+        next(seq)
+    tc = tf = 0.0
+    nc = nf = 0
+    t_all = _t.perf_counter()
+    while True:
+        t0 = _t.perf_counter()
+        kind = next(seq)
+        dt = _t.perf_counter() - t0
+        if kind == "coarse":
+            tc, nc = tc + dt, nc + 1
+        else:
+            tf, nf = tf + dt, nf + 1
+        done = nc + nf
+        if nc and nf and (_t.perf_counter() - t_all > budget_s or (max_solves and done >= max_solves)):
             break
-    dt = _t.perf_counter() - t0
-    return {"value": work / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"first {solves} solves of {cfg['name']} (coarse predictor + {work // fine_nodes(cfg)} "
-                      f"fine micro steps), single-threaded SciPy, {dt:.1f} s; host has {os.cpu_count()} cores"}
+    m = cfg["m"]
+    t_macro = 2 * tc / nc + m * tf / nf
+    return m * fine_nodes(cfg) / t_macro, done, nc, nf, _t.perf_counter() - t_all
+
+
+def cpu_baseline(cfg, budget_s=20.0):
+    """The oracle as it stands on a bounded sample of the same workload."""
+    val, done, nc, nf, dt = oracle_sample(cfg, budget_s)
+    return {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} solves of {cfg['name']} ({nc} coarse, {nf} fine), single-threaded SciPy, "
+                      f"{dt:.1f} s, mean solve times scaled to a macro step (2 coarse + {cfg['m']} fine); "
+                      f"host has {os.cpu_count()} cores"}
 
 
 def run_reference(args):
     """The oracle on the same workload: a step is one solve of its Algorithm-1
-    sequence (coarse predictor / corrector or fine micro step); the value is
-    fine DOF-substeps over the wall time of the timed solves."""
+    sequence (coarse predictor / corrector or fine micro step); the value
+    scales the mean coarse and fine solve times to a macro step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cfg = workloads.workload(args.workload)
-    from oracle import twolevel as TL
     budget = 120.0
     t_start = time.perf_counter()
-    o = TL.TwoLevel(cfg, energy=False)
-    seq = oracle_solves(o)
     warm = max(0, min(args.warmup, 1))
-    for _ in range(warm):
-        next(seq)
-    done = work = 0
-    t0 = time.perf_counter()
-    for w in seq:
-        work += w
-        done += 1
-        if done >= args.steps or (work > 0 and time.perf_counter() - t0 > budget):
-            break
-    dt = time.perf_counter() - t0
-    val = work / dt
-    sample = (f"{done} solves of {cfg['name']} ({work // fine_nodes(cfg)} fine micro steps) after {warm} warm-up "
-              f"solve, single-threaded FP64 SciPy oracle, {dt:.1f} s (time-capped at {budget:.0f} s)")
+    val, done, nc, nf, dt = oracle_sample(cfg, budget, max_solves=max(2, args.steps), warmup=warm)
+    sample = (f"{done} solves of {cfg['name']} ({nc} coarse, {nf} fine) after {warm} warm-up solve, "
+              f"single-threaded FP64 SciPy oracle, {dt:.1f} s (time-capped at {budget:.0f} s), mean solve "
+              f"times scaled to a macro step (2 coarse + {cfg['m']} fine)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DOF-substeps/s",
             "n_gpus": args.gpus, "steps": done, "warmup": warm,
             "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True, "scaling": "weak",
