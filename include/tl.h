@@ -112,6 +112,12 @@ typedef struct {
    * plain one-pass correction.  Not available in batches. */
   int coupling_sweeps;
   double coupling_tol;
+  /* preconditioner of the CG solves: 1 = Jacobi; 2 = the Jacobi-scaled
+   * tensor product of the 1D approximate inverses I - 0.2 L of the consistent
+   * mass (L = neighbour sum per direction): 2.5-2.7 x fewer iterations on
+   * these mass-dominated steps for one extra pass per iteration; 0 = by
+   * precision (2 for TL_FP64, 1 for the FP32 inner CG of TL_FP32_REFINED) */
+  int precond;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
   /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks
    * must be 16-byte aligned (else tl_create_problem returns TL_EINVAL) */
@@ -207,7 +213,8 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
  * a time: 11 <r,r> after a CG pass, 12 the recurrence term that stopped a CG
  * on a non-positive value; 13 the vector-update phase of a CG iteration done
  * (grid barrier passed); 14 / 15 block 0 starts / finished its share of that
- * update phase.
+ * update phase; 16 the preconditioner phase of a CG iteration done (grid
+ * barrier passed).
  * Synchronises.  Errors: TL_EINVAL, TL_ECUDA. */
 tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap,
                               size_t* n_out);

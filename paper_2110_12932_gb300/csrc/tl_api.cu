@@ -412,6 +412,10 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.precision = p->cfg.precision == TL_FP32_REFINED ? PREC_FP32_REFINED : PREC_FP64;
   a.tol_inner = p->cfg.tol_inner;
   a.max_outer = 20;
+  // preconditioner: 0 = by precision (the tensor-product one for FP64 solves,
+  // where it saves FP64 operations; Jacobi for the FP32 inner CG, where its
+  // extra pass costs more than the iterations it saves), 1 Jacobi, 2 tensor
+  a.precond = p->cfg.precond == 2 || (p->cfg.precond == 0 && p->cfg.precision != TL_FP32_REFINED) ? 1 : 0;
   a.F = L.F;
   a.G = L.G;
   a.state = L.state;
@@ -564,6 +568,7 @@ tl_status validate(const tl_config* c) {
   if (c->precision == TL_FP32_REFINED && !(c->tol_inner > 0 && c->tol_inner < 1)) return TL_EINVAL;
   if (c->inner_tiles < 0 || c->inner_tiles > 2) return TL_EINVAL;
   if (c->coupling_sweeps > 1 && !(c->coupling_tol > 0)) return TL_EINVAL;
+  if (c->precond < 0 || c->precond > 2) return TL_EINVAL;
   if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
   for (int j = 0; j < c->ntracks; ++j) {
     const tl_track& k = c->path[j];

@@ -323,6 +323,7 @@ struct SolveArgs {
   double dt, tol, tol_inner;
   int max_iter, max_outer, precision;
   int wide;        // refined path: inner CG on wide tiles (two-phase pcg2, tiling tw)
+  int precond;     // 0 Jacobi (pcg1 / pcg2), 1 tensor-product mass preconditioner (pcg3)
   Tiling tw;
   int energy, update_state, level;
   double Mc[8], Kc[8], Md, Kd, vol8;  // Mc, Kc: eigenvalue factors in pair form (to_pair_form)
@@ -344,7 +345,8 @@ enum TraceMark : int {
   TR_BREAK = 12,   // value marker: CG stopped on a non-positive recurrence term
   TR_CG_UPDATE = 13,
   TR_CG_U0 = 14,   // block 0 starts its share of a CG update phase
-  TR_CG_U1 = 15    // ... and finished it (before the block reduction)
+  TR_CG_U1 = 15,   // ... and finished it (before the block reduction)
+  TR_CG_PRECOND = 16  // the preconditioner phase of a CG iteration done (grid barrier passed)
 };
 constexpr int TRACE_CAP = 1024;
 
@@ -1293,6 +1295,302 @@ __device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
   return conv ? 1 : 0;
 }
 
+// ---------------------------------------------------------------------------
+// CG with the tensor-product mass preconditioner (pcg3).  The operator is
+// dominated by the mass part s_e M (alpha dt / h^2 ~ 1e-2 ... 1e-1), whose
+// Jacobi-scaled form is close to the tensor product of the 1D matrices
+// I + L/4 (L = sum of the two neighbours).  The preconditioner is
+//     P^-1 = D^-1/2 (Q_x Q_y Q_z) D^-1/2,   Q_d = I - c L_d,  c = PC_C,
+// a first-order Neumann approximation of that inverse (missing neighbours at
+// the mesh ends are dropped, so every Q_d is symmetric and diagonally
+// dominant and P^-1 is SPD on the free nodes; D^-1/2 is 0 on Dirichlet
+// nodes).  c = 0.2 gave the fewest iterations on the assembled matrices of
+// the 2 mm and 10 mm workloads (25 instead of 64 with Jacobi at 1e-12).
+// Single-reduction recurrences as in pcg1 / pcg2 with u = P^-1 r, in three
+// phases per iteration, each ended by a grid barrier:
+//   U  (owners, flat): w = own + neighbours' partials of A u; p = u + beta p;
+//      s = w + beta s; x += alpha p; r -= alpha s; v = D^-1/2 r; sum <r,r>;
+//   P  (flat): u = D^-1/2 Q v (27-point separable stencil); sum <r,u>;
+//   A  (tiles): partials of w = A u; sum <w,u>.
+// ---------------------------------------------------------------------------
+constexpr double PC_C = 0.2;
+
+template <typename R>
+struct PCVecs {
+  R* x;           // solution, updated in place
+  R* r;           // residual
+  R* p;           // search direction
+  R* s;           // s = A p, kept by recurrence
+  R* u;           // u = P^-1 r, the apply's input
+  R* q;           // own partial of w = A u
+  R* X;           // NXB exchange planes of w's partials
+  const R* dinv;  // Jacobi inverse diagonal, 0 on Dirichlet nodes
+  R* sq;          // sqrt(dinv), filled by the first update phase
+  R* v;           // v = sqrt(dinv) r, the preconditioner's input
+};
+
+// Update phase of pcg3 (flat, 16 bytes of every array per lane and step, like
+// cg_update).  k < 0: sq = sqrt(dinv), v = sq r.  Returns the thread's <r,r>.
+template <typename R>
+static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const PCVecs<R> c, R alpha, R beta, int k,
+                                           int gtid, int gstride) {
+  using V = typename Vec16<R>::T;
+  constexpr int VEC = 16 / sizeof(R);
+  const int nn = g.nnx * g.nny * g.nnz;
+  const size_t xs = xplane(nn);
+  const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny), mz = div_magic(t.ez);
+  const bool init = k < 0, first = k == 0;
+  const int ngroups = (nn + VEC - 1) / VEC;
+  R vrr = R(0);
+  auto load = [&](const R* a, int n0, int cnt, R (&o)[VEC]) {
+    if (cnt == VEC) {
+      const V v = __ldcg(reinterpret_cast<const V*>(a + n0));
+      const R* e = reinterpret_cast<const R*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = e[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = m < cnt ? __ldcg(a + n0 + m) : R(0);
+    }
+  };
+  auto store = [&](R* a, int n0, int cnt, const R (&o)[VEC]) {
+    if (cnt == VEC) {
+      V v;
+      R* e = reinterpret_cast<R*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) e[m] = o[m];
+      *reinterpret_cast<V*>(a + n0) = v;
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m)
+        if (m < cnt) a[n0 + m] = o[m];
+    }
+  };
+  for (int q = gtid; q < ngroups; q += gstride) {
+    const int n0 = q * VEC;
+    const int cnt = min(VEC, nn - n0);
+    R rk[VEC], sqv[VEC], vn[VEC];
+    load(c.r, n0, cnt, rk);
+    if (init) {
+      R dv[VEC];
+      load(c.dinv, n0, cnt, dv);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) {
+        sqv[m] = sqrt(dv[m]);
+        vn[m] = sqv[m] * rk[m];
+        if (sqv[m] != R(0)) vrr = fma(rk[m], rk[m], vrr);
+      }
+      store(c.sq, n0, cnt, sqv);
+      store(c.v, n0, cnt, vn);
+      continue;
+    }
+    load(c.sq, n0, cnt, sqv);
+    int lf[VEC];
+    int rowf = -1;
+    {
+      const int row = div_by(n0, g.nnx, mx);
+      int i = n0 - row * g.nnx;
+      int kz = div_by(row, g.nny, my);
+      int j = row - kz * g.nny;
+      auto row_faces = [&](int jj, int kk) {
+        const bool ly = t.nty > 1 && jj > 0 && jj < g.ny && (jj & (t.ey - 1)) == 0;
+        const bool lz = kk > 0 && kk < g.nz && kk - div_by(kk, t.ez, mz) * t.ez == 0;
+        return (ly ? 2 : 0) | (lz ? 4 : 0);
+      };
+      if (cnt == VEC && i + VEC <= g.nnx) {
+        rowf = row_faces(j, kz);
+#pragma unroll
+        for (int m = 0; m < VEC; ++m) lf[m] = rowf | low_faces(g, t, i + m, false, false);
+      } else {
+#pragma unroll
+        for (int m = 0; m < VEC; ++m) {
+          lf[m] = m < cnt ? (row_faces(j, kz) | low_faces(g, t, i, false, false)) : 0;
+          if (++i == g.nnx) {
+            i = 0;
+            if (++j == g.nny) {
+              j = 0;
+              ++kz;
+            }
+          }
+        }
+      }
+    }
+    R w[VEC], xk[VEC], pk[VEC], sk[VEC], uk[VEC], wx[VEC], wy[VEC], wz[VEC];
+    load(c.q, n0, cnt, w);
+    load(c.x, n0, cnt, xk);
+    load(c.u, n0, cnt, uk);
+    if (!first) {
+      load(c.p, n0, cnt, pk);
+      load(c.s, n0, cnt, sk);
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) pk[m] = sk[m] = R(0);
+    }
+    if (rowf >= 0) {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) wy[m] = wz[m] = R(0);
+      if (rowf & 2) load(c.X + 1 * xs, n0, VEC, wy);
+      if (rowf & 4) load(c.X + 3 * xs, n0, VEC, wz);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) wx[m] = (lf[m] & 1) ? __ldcg(c.X + 0 * xs + n0 + m) : R(0);
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) {
+        wx[m] = (lf[m] & 1) ? __ldcg(c.X + 0 * xs + n0 + m) : R(0);
+        wy[m] = (lf[m] & 2) ? __ldcg(c.X + 1 * xs + n0 + m) : R(0);
+        wz[m] = (lf[m] & 4) ? __ldcg(c.X + 3 * xs + n0 + m) : R(0);
+      }
+    }
+    R pn[VEC], sn[VEC], rn[VEC], xn[VEC];
+#pragma unroll
+    for (int m = 0; m < VEC; ++m) {
+      pn[m] = pk[m];
+      sn[m] = sk[m];
+      rn[m] = rk[m];
+      xn[m] = xk[m];
+      vn[m] = R(0);
+      if (m >= cnt || sqv[m] == R(0)) continue;
+      const int n = n0 + m;
+      const int f = lf[m];
+      R wv = w[m];
+      if (f) {  // neighbours' partials, in the order gather_partials uses
+        if (f & 1) wv += wx[m];
+        if (f & 2) wv += wy[m];
+        if ((f & 3) == 3) wv += __ldcg(c.X + 2 * xs + n);
+        if (f & 4) wv += wz[m];
+        if ((f & 5) == 5) wv += __ldcg(c.X + 4 * xs + n);
+        if ((f & 6) == 6) wv += __ldcg(c.X + 5 * xs + n);
+        if (f == 7) wv += __ldcg(c.X + 6 * xs + n);
+      }
+      pn[m] = first ? uk[m] : fma(beta, pk[m], uk[m]);
+      sn[m] = first ? wv : fma(beta, sk[m], wv);
+      rn[m] = fma(-alpha, sn[m], rk[m]);
+      xn[m] = fma(alpha, pn[m], xk[m]);
+      vn[m] = sqv[m] * rn[m];
+      vrr = fma(rn[m], rn[m], vrr);
+    }
+    store(c.p, n0, cnt, pn);
+    store(c.s, n0, cnt, sn);
+    store(c.r, n0, cnt, rn);
+    store(c.x, n0, cnt, xn);
+    store(c.v, n0, cnt, vn);
+  }
+  return vrr;
+}
+
+// Preconditioner phase of pcg3: u = sq (Q_z Q_y Q_x v) node by node from the
+// 27 neighbours of v (read through L2: v was written by other blocks in the
+// previous phase), and the thread's sum of <r,u>.
+template <typename R>
+static __device__ __noinline__ R pc_apply(const Grid3 g, const PCVecs<R> c, int gtid, int gstride) {
+  const int nn = g.nnx * g.nny * g.nnz;
+  const int S = g.nnx * g.nny;
+  const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny);
+  const R cw = R(PC_C);
+  R gam = R(0);
+  for (int n = gtid; n < nn; n += gstride) {
+    const R s = __ldcg(c.sq + n);
+    R un = R(0);
+    if (s != R(0)) {
+      const int row = div_by(n, g.nnx, mx);
+      const int i = n - row * g.nnx;
+      const int k = div_by(row, g.nny, my);
+      const int j = row - k * g.nny;
+      R acc = R(0);
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+        if (k + dz < 0 || k + dz > g.nz) continue;
+        R accy = R(0);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          if (j + dy < 0 || j + dy > g.ny) continue;
+          const R* rv = c.v + (n + dz * S + dy * g.nnx);
+          R side = R(0);
+          if (i > 0) side += __ldcg(rv - 1);
+          if (i < g.nx) side += __ldcg(rv + 1);
+          const R tx = fma(-cw, side, __ldcg(rv));
+          accy = dy == 0 ? accy + tx : fma(-cw, tx, accy);
+        }
+        acc = dz == 0 ? acc + accy : fma(-cw, accy, acc);
+      }
+      un = s * acc;
+      gam = fma(__ldcg(c.r + n), un, gam);
+    }
+    c.u[n] = un;
+  }
+  return gam;
+}
+
+// apply_z(tile) applies the operator to c.u on one tile of the tiling t, stores
+// the partials in c.q / c.X and returns the tile's share of <w, u>.  Uses
+// reduction rows RS_PQ..RS_RR and RS_ES..RS_EF.
+template <typename R, class ApplyZ>
+__device__ int pcg3(const SolveArgs& a, const VGrid& vg, const Tiling& t, const PCVecs<R>& c, ApplyZ apply_z,
+                    R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
+  R* s_scal = red_scalars<R>();
+  const int ntiles = t.ntx * t.nty * t.ntz;
+  const int gtid = vg.bid * blockDim.x + threadIdx.x, gstride = vg.nblk * blockDim.x;
+  R alpha = R(0), beta = R(0), gamma = R(0);
+  int it = 0;
+  bool conv = false;
+  for (int k = -1; k < max_iter; ++k) {
+    // rows: <w,u>, <r,u>, <r,r>, alternating by iteration
+    R* rslots = red + (((k + 1) & 1) ? RS_ES : RS_PQ) * a.red_stride;
+    tr.mark(TR_CG_U0);
+    {
+      R v[1] = {pc_update<R>(a.g, t, c, alpha, beta, k, gtid, gstride)};
+      tr.mark(TR_CG_U1);
+      block_reduce_store<1>(v, rslots + 2 * a.red_stride, a.red_stride, vg);
+    }
+    if (!grid_sync(a.bar, vg)) return -1;
+    tr.mark(TR_CG_UPDATE);
+    {
+      R v[1] = {pc_apply<R>(a.g, c, gtid, gstride)};
+      block_reduce_store<1>(v, rslots + a.red_stride, a.red_stride, vg);
+    }
+    if (!grid_sync(a.bar, vg)) return -1;
+    tr.mark(TR_CG_PRECOND);
+    R vd = R(0);
+    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) vd += apply_z(tile);
+    tr.mark(TR_CG_APPLY);
+    {
+      R v[1] = {vd};
+      block_reduce_store<1>(v, rslots, a.red_stride, vg);
+    }
+    if (!grid_sync(a.bar, vg)) return -1;
+    tr.mark(TR_CG_PASS);
+    R tot[3];  // <w,u>, <r,u>, <r,r>
+    grid_total<3>(rslots, a.red_stride, tot, vg);
+    tr.value(TR_RR, (double)tot[2]);
+    if (k >= 0) {
+      ++it;
+      if (tot[2] <= thresh) {
+        conv = true;
+        break;
+      }
+    }
+    if (threadIdx.x == 0) {
+      const R gn = tot[1], dn = tot[0];
+      R b = k < 0 ? R(0) : gn / gamma;
+      R den = k < 0 ? dn : dn - b * gn / alpha;
+      s_scal[0] = gn / den;
+      s_scal[1] = b;
+      s_scal[2] = (den > R(0) && gn > R(0)) ? R(1) : R(0);
+    }
+    __syncthreads();
+    if (s_scal[2] == R(0)) {
+      tr.value(TR_BREAK, (double)tot[0]);
+      break;
+    }
+    gamma = tot[1];
+    alpha = s_scal[0];
+    beta = s_scal[1];
+    __syncthreads();
+  }
+  *iters = it;
+  return conv ? 1 : 0;
+}
+
 __device__ inline double elem_mean(const double* T, const Grid3& g, int ie, int je, int ke) {
   const int S = g.nnx * g.nny;
   const int n0 = ie + g.nnx * je + S * ke;
@@ -1461,8 +1759,24 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       for (int m = 0; m < 8; ++m) l8[m] = __ldcg(a.lam + m * ne + e);
     };
     auto no_fetch64 = [](int, double*) {};
-    const int res = pcg1<double, false, NRAW>(a, vg, sm64, stage64, c, no_fetch64, lam64, thresh, a.max_iter,
-                                              a.red, &it, tr);
+    int res;
+    if (a.precond == 1) {
+      PCVecs<double> c3{a.u, a.r, a.p0, a.s0, a.r2, a.q, a.X, a.dinv, a.s1, a.p1};
+      auto apply_z = [&](int tile) {
+        double vd = 0.0;
+        auto emit = [&](int n, int slot, double y, double xin) {
+          store_partial(c3.q, c3.X, nn, n, slot, y, false);
+          vd = fma(xin, y, vd);
+        };
+        apply_tile<double, false, 1, 1>(g, t, tile, sm64, stage64, StageArray<double, double>{c3.u},
+                                        FinishArray<double, double>{}, no_fetch64, lam64, emit);
+        return vd;
+      };
+      res = pcg3<double>(a, vg, t, c3, apply_z, thresh, a.max_iter, a.red, &it, tr);
+    } else {
+      res = pcg1<double, false, NRAW>(a, vg, sm64, stage64, c, no_fetch64, lam64, thresh, a.max_iter, a.red, &it,
+                                      tr);
+    }
     if (res < 0) return;
     conv = res == 1;
   }
@@ -1511,7 +1825,35 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     };
     const float ti = (float)a.tol_inner;
     int res;
-    if (a.wide) {
+    if (a.precond == 1) {
+      PCVecs<float> c3{a.d32, a.r32, a.p0f, a.s0f, a.r32b, a.q32, a.X32, a.dinv32, a.s1f, a.p1f};
+      if (a.wide) {
+        WideSmem* smw = reinterpret_cast<WideSmem*>(smem_raw);
+        WideCoef cf;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          cf.mp[m] = mcf[m];
+          cf.kp[m] = kcf[m];
+        }
+        auto apply_z = [&](int tile) {
+          return apply_wide_partials(g, a.tw, tile, smw, stage32, c3.u, a.sk32, cf, c3.q, c3.X);
+        };
+        res = pcg3<float>(a, vg, a.tw, c3, apply_z, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+      } else {
+        auto apply_z = [&](int tile) {
+          float vd = 0.0f;
+          auto emit = [&](int n, int slot, float y, float xin) {
+            store_partial(c3.q, c3.X, nn, n, slot, y, false);
+            vd = fmaf(xin, y, vd);
+          };
+          // staging slots: 0 the window value, 1 and 2 the element data
+          apply_tile<float, true, 3, 1>(g, t, tile, sm32, stage32, StageArray<float, float>{c3.u},
+                                        FinishArray<float, float>{}, fetch32, lam32, emit);
+          return vd;
+        };
+        res = pcg3<float>(a, vg, t, c3, apply_z, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+      }
+    } else if (a.wide) {
       CGVecs<float> c2{a.d32, a.r32, a.p0f, a.s0f, a.r32b, a.q32, a.X32, a.dinv32};
       WideSmem* smw = reinterpret_cast<WideSmem*>(smem_raw);
       WideCoef cf;

@@ -46,7 +46,7 @@ class tl_config(C.Structure):
         ("coarse_source", C.c_int), ("bc_weight_literal", C.c_int), ("energy", C.c_int),
         ("precision", C.c_int), ("tol", C.c_double), ("tol_inner", C.c_double),
         ("max_iter", C.c_int), ("inner_tiles", C.c_int),
-        ("coupling_sweeps", C.c_int), ("coupling_tol", C.c_double),
+        ("coupling_sweeps", C.c_int), ("coupling_tol", C.c_double), ("precond", C.c_int),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
@@ -253,7 +253,8 @@ def tl_box_step_noalloc(desc, T_in_ptr, T_out_ptr, state_ptr, stream=None):
 
 TRACE_MARKS = {0: "start", 1: "phase0", 2: "rhs", 3: "resid", 4: "cg_pass", 5: "outer_init",
                6: "outer_apply", 7: "outer_end", 8: "update", 9: "end", 10: "cg_apply",
-               11: "rr_value", 12: "breakdown_value", 13: "cg_update", 14: "cg_u_start", 15: "cg_u_end"}
+               11: "rr_value", 12: "breakdown_value", 13: "cg_update", 14: "cg_u_start", 15: "cg_u_end",
+               16: "cg_precond"}
 
 
 def tl_checkpoint_size(h):

@@ -36,7 +36,7 @@ MATERIAL = dict(
 PROCESS = dict(P=195.0, eta=0.4, radius=50e-6)
 THERMAL = dict(T0=293.0, T_bottom=293.0)
 SOLVER = dict(precision=0, tol=1e-12, tol_inner=1e-5, max_iter=2000, inner_tiles=0,
-              coupling_sweeps=1, coupling_tol=1e-10, coarse_source=0, bc_weight_literal=0, energy=1)
+              coupling_sweeps=1, coupling_tol=1e-10, precond=0, coarse_source=0, bc_weight_literal=0, energy=1)
 
 
 def raster_tracks(x_start, x_end, y_center, n_tracks, hatch, speed):

@@ -79,6 +79,7 @@ def _einval(lib, **over):
     dict(tracks=[(0.0, 0.0, 1e-3, 1e-3, 0.8)]),          # diagonal track with the box source
     dict(tracks=[(0.0, 0.0, 1e-3, 0.0, 0.0)]),           # zero speed
     dict(coarse_source=2), dict(precision=7), dict(inner_tiles=3), dict(inner_tiles=-1),
+    dict(precond=3), dict(precond=-1), dict(coupling_sweeps=2, coupling_tol=0.0),
 ])
 def test_invalid_config_is_rejected_on_host(lib, over):
     assert _einval(lib, **over) == tl.TL_EINVAL

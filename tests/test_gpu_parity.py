@@ -334,3 +334,39 @@ def test_coupled_problems_stay_out_of_batches():
         b.add(p, 2)
     b.close()
     p.close()
+
+
+# ---- preconditioners: Jacobi and the tensor-product mass preconditioner -----
+
+def test_jacobi_preconditioner_against_oracle():
+    cfg = workloads.workload("single_track_tiny", precond=1)
+    prob, ref, errs = run_both(cfg, 20, check_every=5)
+    prob.close()
+
+
+@pytest.mark.parametrize("inner_tiles", [1, 2])
+def test_refined_tensor_preconditioner_against_oracle(inner_tiles):
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5,
+                             precond=2, inner_tiles=inner_tiles)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    prob.macro_steps(20)
+    ref.run(20)
+    Tf, _ = prob.temperature(tl.TL_FINE)
+    Tc, _ = prob.temperature(tl.TL_COARSE)
+    assert rel(Tf, ref.Tf) <= REFINED_TOL and rel(Tc, ref.Tc) <= REFINED_TOL
+    assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+    prob.close()
+
+
+def test_preconditioners_agree_and_tensor_needs_fewer_iterations():
+    base = workloads.workload("multitrack_10mm")
+    out = []
+    for pc in (1, 2):
+        p = tl.Problem(dict(base, precond=pc))
+        p.macro_steps(2)
+        out.append((p.temperature(tl.TL_FINE)[0], p.state(tl.TL_FINE), p.stats()))
+        p.close()
+    (a, sa, st1), (b, sb, st2) = out
+    assert rel(b, a) <= 1e-10 and np.array_equal(sa, sb)
+    assert st2["cg_iters_fine"] * 2 < st1["cg_iters_fine"]
