@@ -18,8 +18,9 @@
  * (thermalEqn) (Section 2.1, latent heat omitted) on a uniform mesh of
  * trilinear hexahedra, with conductivity and heat capacity evaluated at the
  * element-mean temperature of the step's start (lagged), a powder/solid/
- * melted element state, and a Jacobi-preconditioned conjugate gradient
- * solve run entirely on the GPU.
+ * melted element state, and a preconditioned conjugate gradient solve
+ * (tensor-product mass preconditioner by default, Jacobi on request) run
+ * entirely on the GPU.
  *
  * Ownership: the library owns every device buffer of a problem; host
  * buffers passed to getters belong to the caller.  Calls are ordered on the
@@ -115,8 +116,8 @@ typedef struct {
   /* preconditioner of the CG solves: 1 = Jacobi; 2 = the Jacobi-scaled
    * tensor product of the 1D approximate inverses I - 0.2 L of the consistent
    * mass (L = neighbour sum per direction): 2.5-2.7 x fewer iterations on
-   * these mass-dominated steps for one extra pass per iteration; 0 = by
-   * precision (2 for TL_FP64, 1 for the FP32 inner CG of TL_FP32_REFINED) */
+   * these mass-dominated steps for one extra pass per iteration; 0 = the
+   * default, the same as 2 */
   int precond;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
   /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks

@@ -324,6 +324,7 @@ struct SolveArgs {
   int max_iter, max_outer, precision;
   int wide;        // refined path: inner CG on wide tiles (two-phase pcg2, tiling tw)
   int precond;     // 0 Jacobi (pcg1 / pcg2), 1 tensor-product mass preconditioner (pcg3)
+  Tiling tp;       // pcg3: node-owned tiles of the preconditioner pass (ex x ey columns, ez layers)
   Tiling tw;
   int energy, update_state, level;
   double Mc[8], Kc[8], Md, Kd, vol8;  // Mc, Kc: eigenvalue factors in pair form (to_pair_form)
@@ -1314,6 +1315,10 @@ __device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
 //   A  (tiles): partials of w = A u; sum <w,u>.
 // ---------------------------------------------------------------------------
 constexpr double PC_C = 0.2;
+// Preconditioner tiles are at least two columns wide and at most NT columns in
+// all, so a window holds at most (2 + 2) (NT / 2 + 2) nodes: PC_WM per thread.
+constexpr int PC_WN_MAX = 4 * (NT / 2 + 2);
+constexpr int PC_WM = (PC_WN_MAX + NT - 1) / NT;
 
 template <typename R>
 struct PCVecs {
@@ -1478,45 +1483,105 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
   return vrr;
 }
 
-// Preconditioner phase of pcg3: u = sq (Q_z Q_y Q_x v) node by node from the
-// 27 neighbours of v (read through L2: v was written by other blocks in the
-// previous phase), and the thread's sum of <r,u>.
+// Preconditioner phase of pcg3: u = sq (Q_z Q_y Q_x v) and the block's sum of
+// <r,u>.  Node-owned tiles of tp.ex x tp.ey columns (at most NT) and tp.ez
+// node layers; a tile marches up from one layer below its range to one above,
+// loads the (ex+2) x (ey+2) window of v of each layer into shared memory
+// (zeros outside the mesh, which drops the missing neighbours), applies
+// Q_x Q_y there, and keeps three consecutive layers of the result per column
+// in registers for Q_z.  The windows (with sq and r of the owned nodes)
+// arrive by cp.async several layers ahead in a ring of slots; one block
+// barrier per layer.
 template <typename R>
-static __device__ __noinline__ R pc_apply(const Grid3 g, const PCVecs<R> c, int gtid, int gstride) {
-  const int nn = g.nnx * g.nny * g.nnz;
+static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const PCVecs<R> c, R* win, const VGrid vg) {
   const int S = g.nnx * g.nny;
-  const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny);
+  // NS ring slots, D = NS - 1 layers in flight: a tile column is narrow, so
+  // several layers must be in flight to cover the memory latency
+  constexpr int NS = sizeof(R) == 4 ? 8 : 5, D = NS - 1;
+  static_assert(NS * (PC_WN_MAX + 2 * NT) * (int)sizeof(R) <= STAGE_BYTES,
+                "ring of the widest window fits the dynamic shared memory");
+  const int TX = tp.ex, TY = tp.ey, WXP = TX + 2, WN = (TX + 2) * (TY + 2), SL = WN + 2 * NT;
+  const int ntiles = tp.ntx * tp.nty * tp.ntz;
   const R cw = R(PC_C);
+  const int tid = threadIdx.x;
+  const int ty = tid / TX, tx = tid - ty * TX;
   R gam = R(0);
-  for (int n = gtid; n < nn; n += gstride) {
-    const R s = __ldcg(c.sq + n);
-    R un = R(0);
-    if (s != R(0)) {
-      const int row = div_by(n, g.nnx, mx);
-      const int i = n - row * g.nnx;
-      const int k = div_by(row, g.nny, my);
-      const int j = row - k * g.nny;
-      R acc = R(0);
+  for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
+    const int txy = tp.ntx * tp.nty;
+    const int tiz = tile / txy, trem = tile - tiz * txy;
+    const int tiy = trem / tp.ntx, tix = trem - tiy * tp.ntx;
+    const int i0 = tix * TX, j0 = tiy * TY, k0 = tiz * tp.ez, k1 = min(k0 + tp.ez, g.nnz);
+    const int i = i0 + tx, j = j0 + ty;
+    const bool own = ty < TY && i < g.nnx && j < g.nny;
+    R tm = R(0), tc = R(0);  // xy-filtered values of layers L - 2, L - 1
+    R sq_c = R(0), r_c = R(0);  // sq, r of the column's node at layer L - 1
+    // slot of layer L: its window of v (zeros outside the mesh), then sq and r
+    // of the owned nodes; async copies, one group per layer
+    // this thread's window entries (w = tid + m NT) and their in-layer node
+    // offsets, -1 outside the mesh; fixed for the tile
+    int woff[PC_WM];
 #pragma unroll
-      for (int dz = -1; dz <= 1; ++dz) {
-        if (k + dz < 0 || k + dz > g.nz) continue;
-        R accy = R(0);
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-          if (j + dy < 0 || j + dy > g.ny) continue;
-          const R* rv = c.v + (n + dz * S + dy * g.nnx);
-          R side = R(0);
-          if (i > 0) side += __ldcg(rv - 1);
-          if (i < g.nx) side += __ldcg(rv + 1);
-          const R tx = fma(-cw, side, __ldcg(rv));
-          accy = dy == 0 ? accy + tx : fma(-cw, tx, accy);
-        }
-        acc = dz == 0 ? acc + accy : fma(-cw, accy, acc);
-      }
-      un = s * acc;
-      gam = fma(__ldcg(c.r + n), un, gam);
+    for (int m = 0; m < PC_WM; ++m) {
+      const int w = tid + m * NT;
+      const int wy = w / WXP, wx = w - wy * WXP;
+      const int gi = i0 - 1 + wx, gj = j0 - 1 + wy;
+      woff[m] = (w < WN && gi >= 0 && gi < g.nnx && gj >= 0 && gj < g.nny) ? gi + g.nnx * gj : -1;
     }
-    c.u[n] = un;
+    const int own_off = i + g.nnx * j;
+    auto load_layer = [&](int L, int slot) {
+      if (L >= 0 && L < g.nnz && L <= k1) {
+        R* buf = win + slot * SL;
+        const R* vL = c.v + (size_t)S * L;
+#pragma unroll
+        for (int m = 0; m < PC_WM; ++m) {
+          const int w = tid + m * NT;
+          if (woff[m] >= 0)
+            cp_async<sizeof(R)>(buf + w, vL + woff[m]);
+          else if (w < WN)
+            buf[w] = R(0);
+        }
+        if (own && L >= k0 && L < k1) {
+          const size_t n = (size_t)S * L + own_off;
+          cp_async<sizeof(R)>(buf + WN + tid, c.sq + n);
+          cp_async<sizeof(R)>(buf + WN + NT + tid, c.r + n);
+        }
+      }
+      cp_async_commit();
+    };
+    for (int d = 0; d < D; ++d) load_layer(k0 - 1 + d, d);
+    int sl = 0;
+    for (int L = k0 - 1; L <= k1; ++L) {
+      cp_async_wait<D - 1>();  // layer L has landed (L + 1 .. L + D - 1 may be in flight)
+      __syncthreads();         // ... for every thread; the slot of layer L - 1 is free again
+      load_layer(L + D, sl == 0 ? NS - 1 : sl - 1);
+      const R* buf = win + sl * SL;
+      R tl = R(0);
+      if (own && L >= 0 && L < g.nnz) {
+        R acc = R(0);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const R* row = buf + (ty + dy) * WXP + tx;
+          const R t = fma(-cw, row[0] + row[2], row[1]);
+          acc = dy == 1 ? acc + t : fma(-cw, t, acc);
+        }
+        tl = acc;
+      }
+      if (own && L >= k0 + 1) {  // layer L - 1 is complete
+        const int n = i + g.nnx * j + S * (L - 1);
+        const R un = sq_c * fma(-cw, tm + tl, tc);
+        c.u[n] = un;
+        if (sq_c != R(0)) gam = fma(r_c, un, gam);
+      }
+      if (own && L >= k0 && L < k1) {
+        sq_c = buf[WN + tid];
+        r_c = buf[WN + NT + tid];
+      }
+      tm = tc;
+      tc = tl;
+      sl = sl == NS - 1 ? 0 : sl + 1;
+    }
+    cp_async_wait<0>();
+    __syncthreads();  // the window is free for the next tile
   }
   return gam;
 }
@@ -1526,7 +1591,7 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const PCVecs<R> c, int 
 // reduction rows RS_PQ..RS_RR and RS_ES..RS_EF.
 template <typename R, class ApplyZ>
 __device__ int pcg3(const SolveArgs& a, const VGrid& vg, const Tiling& t, const PCVecs<R>& c, ApplyZ apply_z,
-                    R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
+                    R* win, R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
   R* s_scal = red_scalars<R>();
   const int ntiles = t.ntx * t.nty * t.ntz;
   const int gtid = vg.bid * blockDim.x + threadIdx.x, gstride = vg.nblk * blockDim.x;
@@ -1545,7 +1610,7 @@ __device__ int pcg3(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
     if (!grid_sync(a.bar, vg)) return -1;
     tr.mark(TR_CG_UPDATE);
     {
-      R v[1] = {pc_apply<R>(a.g, c, gtid, gstride)};
+      R v[1] = {pc_apply<R>(a.g, a.tp, c, win, vg)};
       block_reduce_store<1>(v, rslots + a.red_stride, a.red_stride, vg);
     }
     if (!grid_sync(a.bar, vg)) return -1;
@@ -1772,7 +1837,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
                                         FinishArray<double, double>{}, no_fetch64, lam64, emit);
         return vd;
       };
-      res = pcg3<double>(a, vg, t, c3, apply_z, thresh, a.max_iter, a.red, &it, tr);
+      res = pcg3<double>(a, vg, t, c3, apply_z, stage64, thresh, a.max_iter, a.red, &it, tr);
     } else {
       res = pcg1<double, false, NRAW>(a, vg, sm64, stage64, c, no_fetch64, lam64, thresh, a.max_iter, a.red, &it,
                                       tr);
@@ -1838,7 +1903,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
         auto apply_z = [&](int tile) {
           return apply_wide_partials(g, a.tw, tile, smw, stage32, c3.u, a.sk32, cf, c3.q, c3.X);
         };
-        res = pcg3<float>(a, vg, a.tw, c3, apply_z, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+        res = pcg3<float>(a, vg, a.tw, c3, apply_z, stage32, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
       } else {
         auto apply_z = [&](int tile) {
           float vd = 0.0f;
@@ -1851,7 +1916,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
                                         FinishArray<float, float>{}, fetch32, lam32, emit);
           return vd;
         };
-        res = pcg3<float>(a, vg, t, c3, apply_z, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+        res = pcg3<float>(a, vg, t, c3, apply_z, stage32, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
       }
     } else if (a.wide) {
       CGVecs<float> c2{a.d32, a.r32, a.p0f, a.s0f, a.r32b, a.q32, a.X32, a.dinv32};

@@ -344,10 +344,11 @@ def test_jacobi_preconditioner_against_oracle():
     prob.close()
 
 
+@pytest.mark.parametrize("precond", [1, 2])
 @pytest.mark.parametrize("inner_tiles", [1, 2])
-def test_refined_tensor_preconditioner_against_oracle(inner_tiles):
+def test_refined_preconditioners_against_oracle(inner_tiles, precond):
     cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5,
-                             precond=2, inner_tiles=inner_tiles)
+                             precond=precond, inner_tiles=inner_tiles)
     prob = tl.Problem(cfg)
     ref = TL.TwoLevel(cfg, energy=False)
     prob.macro_steps(20)
@@ -362,7 +363,7 @@ def test_refined_tensor_preconditioner_against_oracle(inner_tiles):
 def test_preconditioners_agree_and_tensor_needs_fewer_iterations():
     base = workloads.workload("multitrack_10mm")
     out = []
-    for pc in (1, 2):
+    for pc in (1, 0):  # 0: the default, the tensor-product preconditioner
         p = tl.Problem(dict(base, precond=pc))
         p.macro_steps(2)
         out.append((p.temperature(tl.TL_FINE)[0], p.state(tl.TL_FINE), p.stats()))
