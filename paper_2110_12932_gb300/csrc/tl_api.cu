@@ -855,7 +855,7 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
     cudaGetLastError();
     return TL_ECUDA;
   }
-  p->max_coop = per_sm * p->nsm;
+  p->max_coop = std::min(per_sm * p->nsm, MAX_GRID_BLOCKS);
   const tl_config& c = p->cfg;
   const int r = c.r;
   // coarse level
@@ -1226,7 +1226,7 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
     e = cudaFuncSetAttribute(batch_kernel_for(m), cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_BYTES);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_for(m), NT, STAGE_BYTES);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
-    b->max_coop_v[m] = per_sm * b->nsm;
+    b->max_coop_v[m] = std::min(per_sm * b->nsm, MAX_GRID_BLOCKS);
     b->max_coop = std::min(b->max_coop, b->max_coop_v[m]);
   }
   if (e != cudaSuccess) {

@@ -49,15 +49,16 @@ __host__ __device__ inline int split_lo(int n, int parts, int a) {
 }
 
 // ---------------------------------------------------------------------------
-// Time-limited grid barrier for cooperative (co-resident) launches.
-// Two-level arrival: blocks arrive on the counter of their group of
-// BAR_GROUP consecutive blocks; the last of a group arrives on the root
-// counter; the last group releases the generation word.  Every wait gives up
-// after `limit_ns` of global time, records ST_TIMEOUT and returns false; a
-// block that sees an error recorded by another returns false too, so that all
-// blocks leave the kernel.
-// Word layout (BAR_WORDS unsigned ints, zero at creation): [0] root counter,
-// [1 .. BAR_MAXG] group counters, [BAR_GEN] generation, [BAR_STATUS] status.
+// Time-limited grid barrier for cooperative (co-resident) launches.  Every
+// block arrives on one counter; the last arrival resets it and releases the
+// generation word.  (Measured on GB300 with 152 to 608 blocks: 2.2 - 2.4 us
+// per barrier, against 2.9 - 3.2 us with a two-level tree of 32-block groups;
+// the arrivals on one word do not queue noticeably at this block count.)
+// Every wait gives up after `limit_ns` of global time, records ST_TIMEOUT and
+// returns false; a block that sees an error recorded by another returns false
+// too, so that all blocks leave the kernel.
+// Word layout (BAR_WORDS unsigned ints, zero at creation): [0] counter,
+// [BAR_GEN] generation, [BAR_STATUS] status.
 // ---------------------------------------------------------------------------
 // The block range a solve runs on: a whole cooperative grid, or one job's
 // slice of a batched grid.  bid is the block's index within the slice.
@@ -65,16 +66,14 @@ struct VGrid {
   int bid, nblk;
 };
 
-constexpr int BAR_GROUP = 32;
-constexpr int BAR_MAXG = 64;
-constexpr int BAR_GEN = BAR_MAXG + 1;
-constexpr int BAR_STATUS = BAR_MAXG + 2;
-constexpr int BAR_WORDS = BAR_MAXG + 3;
+constexpr int BAR_GEN = 1;
+constexpr int BAR_STATUS = 2;
+constexpr int BAR_WORDS = 4;
 
 struct Barrier {
-  unsigned int* count;  // root counter followed by the group counters
+  unsigned int* count;
   unsigned int* gen;
-  int* status;          // sticky device status word
+  int* status;  // sticky device status word
 };
 
 __device__ inline unsigned long long global_ns() {
@@ -94,117 +93,152 @@ __device__ inline void st_release_u32(unsigned int* p, unsigned int v) {
 __device__ inline int ld_volatile_i32(const int* p) {
   return *(volatile const int*)p;
 }
+// The barriers' result flag, shared by all of a kernel's barrier calls.
+__device__ inline int* bar_ok_flag() {
+  __shared__ int ok;
+  return &ok;
+}
+
+// Each block keeps the generation of its next barrier in shared memory (thread
+// 0 reads and writes it): every use of a barrier releases exactly one
+// generation, and none is released before every block has arrived, so the
+// copy read once by bar_begin stays exact, and the arrival path needs no read
+// of the generation word.
+__device__ inline unsigned int* bar_gen_local() {
+  __shared__ unsigned int gen;
+  return &gen;
+}
+__device__ inline void bar_begin(const Barrier& b) {
+  if (threadIdx.x == 0) *bar_gen_local() = ld_acquire_u32(b.gen);
+  __syncthreads();
+}
+
+// Waits (thread 0) until the generation moves past g; false if the time limit
+// passed (recorded in the status word) or another block recorded a time-out.
+// The status word and the clock are looked at every 16th poll only.
+__device__ inline bool bar_wait(const Barrier& b, unsigned int g, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned int poll = 1; ld_acquire_u32(b.gen) == g; ++poll) {
+    if ((poll & 15) == 0) {
+      if (ld_volatile_i32(b.status) == ST_TIMEOUT) return false;
+      if (global_ns() - t0 > limit_ns) {
+        atomicExch(b.status, (int)ST_TIMEOUT);
+        return false;
+      }
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
 
 __device__ inline bool grid_sync(const Barrier& b, const VGrid& vg, unsigned long long limit_ns = 1000000000ull) {
-  __shared__ int s_ok;
+  int* s_ok = bar_ok_flag();
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int g = ld_acquire_u32(b.gen);
-    __threadfence();
-    const unsigned int grp = (unsigned int)vg.bid / BAR_GROUP;
-    const unsigned int ngroups = ((unsigned int)vg.nblk + BAR_GROUP - 1) / BAR_GROUP;
-    const unsigned int gsize = min((unsigned int)BAR_GROUP, (unsigned int)vg.nblk - grp * BAR_GROUP);
-    bool released = false;
-    if (atomicAdd(b.count + 1 + grp, 1u) == gsize - 1) {
-      __threadfence();  // acquire side: the group's arrivals
-      atomicExch(b.count + 1 + grp, 0u);
-      if (atomicAdd(b.count, 1u) == ngroups - 1) {
-        __threadfence();  // acquire side: every group's arrival
-        atomicExch(b.count, 0u);
-        st_release_u32(b.gen, g + 1u);
-        released = true;
-      }
+    const unsigned int g = *bar_gen_local();
+    __threadfence();  // release side: this block's writes
+    bool ok = true;
+    if (atomicAdd(b.count, 1u) == (unsigned int)vg.nblk - 1u) {
+      __threadfence();  // acquire side: every block's arrival
+      atomicExch(b.count, 0u);
+      st_release_u32(b.gen, g + 1u);
+    } else {
+      ok = bar_wait(b, g, limit_ns);
     }
-    if (!released) {
-      const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(b.gen) == g) {
-        if (ld_volatile_i32(b.status) == ST_TIMEOUT) { ok = 0; break; }
-        if (global_ns() - t0 > limit_ns) {
-          atomicExch(b.status, (int)ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    if (ld_volatile_i32(b.status) == ST_TIMEOUT) ok = 0;
-    s_ok = ok;
+    *bar_gen_local() = g + 1u;
+    *s_ok = ok;
   }
   __syncthreads();
-  return s_ok != 0;
+  return *s_ok != 0;
 }
 
 // ---------------------------------------------------------------------------
 // Deterministic reductions in the solve's own precision: per-thread partial ->
-// warp sum (fixed shuffle tree) -> per-warp partials in shared memory -> one
-// warp sums them -> one slot per block; after a grid barrier warp 0 of every
-// block sums the slots in the same fixed order, so all blocks hold bitwise
-// equal totals.  On GB300 an FP64 warp instruction occupies the SM
-// sub-partition's FP64 unit for ~64 cycles, so FP32 solves reduce in FP32.
+// block sum in a fixed order (block_reduce_store) -> one slot per block ->
+// after a grid barrier every block forms the grid totals from the slots
+// (grid_sync_total), bitwise equal in all blocks.  On GB300 an FP64 warp
+// instruction occupies the SM sub-partition's FP64 unit for ~64 cycles, so
+// the block sums keep FP64 additions few and the grid totals of FP64 slots
+// are formed exactly in integer arithmetic; FP32 solves reduce in FP32.
 // ---------------------------------------------------------------------------
-// One shared scratch for all reductions of a kernel (a static array in a
-// template would be allocated once per instantiation): per-warp partials of up
-// to RED_NV values, the block totals, and a few scalars (red_scalars) that the
-// CG broadcasts after a reduction.  The users never overlap in time.
+// Reductions carry at most RED_NV values at once, over at most
+// MAX_GRID_BLOCKS block slots (the exact FP64 totals rely on it).
 constexpr int RED_NV = 3;
+constexpr int MAX_GRID_BLOCKS = 2048;
+// One shared scratch for all reductions of a kernel (a static array in a
+// template would be allocated once per instantiation): the lane values of
+// warps 1 .. RED_W (block_reduce_store) or per-warp partials (the grid
+// totals), RED_NV totals, and a few scalars (red_scalars) that the CG
+// broadcasts after a reduction.  The users never overlap in time.
+constexpr int RED_W = 4;  // blocks of up to 32 (RED_W + 1) threads
 __device__ inline double* red_scratch() {
-  __shared__ double buf[RED_NV * 32 + RED_NV + 4];
+  __shared__ double buf[RED_W * 32 + RED_NV + 4];
   return buf;
 }
 template <typename T>
+__device__ inline T* red_totals() {
+  return reinterpret_cast<T*>(red_scratch() + RED_W * 32);
+}
+template <typename T>
 __device__ inline T* red_scalars() {
-  return reinterpret_cast<T*>(red_scratch() + RED_NV * 32 + RED_NV);
+  return reinterpret_cast<T*>(red_scratch() + RED_W * 32 + RED_NV);
 }
 
+// Sum of one value over a warp, in a fixed shuffle tree (lane 0 holds it).
+template <typename T>
+__device__ inline T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block sums of NV values into slot vg.bid of NV rows.  Warps 1 .. RED_W park
+// their lane values in shared memory and warp 0 alone adds: per value it adds
+// those columns to its own lanes, then runs one shuffle tree (RED_W + 5 warp
+// additions instead of a tree per warp; FP64 additions are the cost).
 template <int NV, typename T>
 __device__ inline void block_reduce_store(T (&v)[NV], T* slots, int stride, const VGrid& vg) {
   static_assert(NV <= RED_NV && sizeof(T) <= sizeof(double), "reduction scratch");
-  T (*s_part)[32] = reinterpret_cast<T (*)[32]>(red_scratch());
+  T (*s_lane)[32] = reinterpret_cast<T (*)[32]>(red_scratch());
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
-    T x = v[a];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) s_part[a][warp] = x;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      T x = lane < nwarps ? s_part[a][lane] : T(0);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (a > 0) __syncthreads();  // warp 0 has read the previous value's columns
+    if (warp > 0) s_lane[warp - 1][lane] = v[a];
+    __syncthreads();
+    if (warp == 0) {
+      T x = v[a];
+      for (int w = 1; w < nwarps; ++w) x += s_lane[w - 1][lane];
+      x = warp_sum(x);
       if (lane == 0) slots[(size_t)a * stride + vg.bid] = x;
     }
   }
   __syncthreads();
 }
 
-// Every thread of the block loads up to four slots per value at once (one L2
-// round trip for grids of up to 4 x blockDim blocks), then the block sums them
-// in a fixed tree.
-template <int NV, typename T>
-__device__ inline void grid_total(const T* slots, int stride, T (&out)[NV], const VGrid& vg) {
-  static_assert(NV <= RED_NV && sizeof(T) <= sizeof(double), "reduction scratch");
-  T (*s_part)[32] = reinterpret_cast<T (*)[32]>(red_scratch());
-  T* s_tot = reinterpret_cast<T*>(red_scratch() + RED_NV * 32);
+// FP32 grid totals: every thread of the block loads up to four slots per
+// value at once (one L2 round trip for grids of up to 4 x blockDim blocks),
+// then the block sums them in a fixed tree.
+template <int NV>
+__device__ inline void grid_total(const float* slots, int stride, float (&out)[NV], const VGrid& vg) {
+  static_assert(NV <= RED_NV && RED_W >= NV, "reduction scratch");
+  float (*s_part)[32] = reinterpret_cast<float (*)[32]>(red_scratch());
+  float* s_tot = red_totals<float>();
   constexpr int U = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
-  T x[NV];
+  float x[NV];
 #pragma unroll
-  for (int a = 0; a < NV; ++a) x[a] = T(0);
+  for (int a = 0; a < NV; ++a) x[a] = 0.0f;
   for (int s0 = threadIdx.x; s0 < vg.nblk; s0 += U * blockDim.x) {
-    T v[NV][U];
+    float v[NV][U];
 #pragma unroll
     for (int a = 0; a < NV; ++a)
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int s = s0 + u * blockDim.x;
-        v[a][u] = s < vg.nblk ? __ldcg(slots + (size_t)a * stride + s) : T(0);
+        v[a][u] = s < vg.nblk ? __ldcg(slots + (size_t)a * stride + s) : 0.0f;
       }
 #pragma unroll
     for (int a = 0; a < NV; ++a)
@@ -213,17 +247,15 @@ __device__ inline void grid_total(const T* slots, int stride, T (&out)[NV], cons
   }
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x[a] += __shfl_down_sync(0xffffffffu, x[a], o);
+    x[a] = warp_sum(x[a]);
     if (lane == 0) s_part[a][warp] = x[a];
   }
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-      T y = lane < nwarps ? s_part[a][lane] : T(0);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+      float y = lane < nwarps ? s_part[a][lane] : 0.0f;
+      y = warp_sum(y);
       if (lane == 0) s_tot[a] = y;
     }
   }
@@ -231,6 +263,137 @@ __device__ inline void grid_total(const T* slots, int stride, T (&out)[NV], cons
 #pragma unroll
   for (int a = 0; a < NV; ++a) out[a] = s_tot[a];
   __syncthreads();
+}
+
+// Biased exponent of a double given by its bits, 1 for subnormals (their
+// scale), 0 for zeros.
+__device__ inline int exp_eff(long long b) {
+  const int e = (int)((b >> 52) & 0x7FF);
+  return (e == 0 && (b & 0xFFFFFFFFFFFFFll) != 0) ? 1 : e;
+}
+
+// FP64 grid totals, summed exactly in integers.  For each value row, Emax is
+// the largest biased exponent among the slots; every slot x = +-m 2^(e-1075)
+// (m the 53-bit significand; subnormals: e = 1, no implicit bit) becomes the
+// signed integer +-(m >> (Emax - e + 1)), a multiple of the unit
+// 2^(Emax - 1074) truncated towards zero (each loses less than one unit, at
+// most 2^-51 of the largest magnitude).  Each such integer is below 2^52, so
+// the sum of up to 2^11 slots is exact in 64 bits and independent of the
+// order of the additions; it is rounded to double once and scaled back.  The
+// error, at most n units plus that rounding, is of the order of a plain FP64
+// summation's bound, every block gets the same bits, and all the work runs
+// on the integer pipes.  Warp sums use the 32-bit reduction instruction on
+// three 21-bit limbs of each per-thread integer.  A non-finite slot makes the
+// total NaN.
+template <int NV>
+__device__ inline void grid_total(const double* slots, int stride, double (&out)[NV], const VGrid& vg) {
+  static_assert(NV <= RED_NV, "reduction scratch");
+  constexpr int U = 4;  // slots a thread holds in registers; larger grids are read twice
+  int* s_emax = reinterpret_cast<int*>(red_scratch());  // [RED_W + 1][RED_NV]
+  int* s_limb = s_emax + (RED_W + 1) * RED_NV;           // [RED_W + 1][RED_NV][3]
+  double* s_tot = red_totals<double>();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  const bool one_pass = vg.nblk <= U * (int)blockDim.x;
+  long long bits[NV][U];  // zero (adds nothing) where the thread holds no slot
+  int emax[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    emax[a] = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) bits[a][u] = 0ll;
+  }
+  for (int s0 = threadIdx.x; s0 < vg.nblk; s0 += U * blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int s = s0 + u * blockDim.x;
+        bits[a][u] = s < vg.nblk ? __double_as_longlong(__ldcg(slots + (size_t)a * stride + s)) : 0ll;
+        emax[a] = max(emax[a], exp_eff(bits[a][u]));
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    const int m = (int)__reduce_max_sync(0xffffffffu, (unsigned int)emax[a]);
+    if (lane == 0) s_emax[warp * RED_NV + a] = m;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    int m = 0;
+    for (int w = 0; w < nwarps; ++w) m = max(m, s_emax[w * RED_NV + a]);
+    emax[a] = m;
+  }
+  // the thread's integers (exact: below 2^52 each, at most 2^11 of them)
+  long long acc[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) acc[a] = 0;
+  auto add = [&](int a, long long b) {
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0x7FF) return;  // non-finite: Emax = 0x7FF, handled below
+    const long long frac = b & 0xFFFFFFFFFFFFFll;
+    const long long m = e ? (frac | (1ll << 52)) : frac;  // subnormal: no implicit bit, exponent 1
+    const int sh = emax[a] - max(e, 1) + 1;
+    const long long q = sh < 63 ? (m >> sh) : 0ll;
+    acc[a] += b < 0 ? -q : q;
+  };
+  if (one_pass) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int u = 0; u < U; ++u) add(a, bits[a][u]);
+  } else {
+    for (int s = threadIdx.x; s < vg.nblk; s += blockDim.x)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) add(a, __double_as_longlong(__ldcg(slots + (size_t)a * stride + s)));
+  }
+  // limbs: acc = l0 + 2^21 l1 + 2^42 l2 with l0, l1 in [0, 2^21) and l2 signed
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    const int l0 = (int)(acc[a] & 0x1FFFFF), l1 = (int)((acc[a] >> 21) & 0x1FFFFF), l2 = (int)(acc[a] >> 42);
+    const int w0 = (int)__reduce_add_sync(0xffffffffu, (unsigned int)l0);
+    const int w1 = (int)__reduce_add_sync(0xffffffffu, (unsigned int)l1);
+    const int w2 = __reduce_add_sync(0xffffffffu, l2);
+    if (lane == 0) {
+      int* L = s_limb + (warp * RED_NV + a) * 3;
+      L[0] = w0;
+      L[1] = w1;
+      L[2] = w2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int a = threadIdx.x;
+    long long t = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      const int* L = s_limb + (w * RED_NV + a) * 3;
+      t += (long long)L[0] + ((long long)L[1] << 21) + ((long long)L[2] << 42);
+    }
+    double r;
+    if (emax[a] == 0x7FF)
+      r = __longlong_as_double(0x7FF8000000000000ll);
+    else if (emax[a] == 0)
+      r = 0.0;
+    else
+      r = ldexp(__ll2double_rn(t), emax[a] - 1074);
+    s_tot[a] = r;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = s_tot[a];
+  __syncthreads();
+}
+
+// Grid barrier followed by the grid totals of NV reduction rows (each block's
+// slot values stored by block_reduce_store before the call).  Same time limit
+// and error behaviour as grid_sync; on false the totals are undefined.
+template <int NV, typename T>
+__device__ inline bool grid_sync_total(const Barrier& b, const VGrid& vg, const T* slots, int stride, T (&out)[NV],
+                                       unsigned long long limit_ns = 1000000000ull) {
+  if (!grid_sync(b, vg, limit_ns)) return false;
+  grid_total<NV>(slots, stride, out, vg);
+  return true;
 }
 
 }  // namespace tl

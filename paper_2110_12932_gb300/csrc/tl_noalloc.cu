@@ -25,6 +25,7 @@ namespace {
 
 constexpr size_t kMaxNodes = TL_NOALLOC_MAX_NODES;
 constexpr int kMaxGrid = 1024;       // cooperative grid cap (4 blocks per SM on up to 256 SMs)
+static_assert(kMaxGrid <= MAX_GRID_BLOCKS, "reductions over at most MAX_GRID_BLOCKS slots");
 constexpr size_t kAlign = 256;
 constexpr int kMaxDevices = 64;
 

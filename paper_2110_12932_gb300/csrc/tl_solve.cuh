@@ -44,6 +44,7 @@ __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;"
 template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 static_assert(NT >= WX * WY, "a block must cover a tile's window columns");
+static_assert(NT <= 32 * (RED_W + 1), "block_reduce_store parks the lanes of warps 1 .. RED_W");
 constexpr int MAXRECT = 8;
 constexpr int NXB = 7;                // exchange buffers
 // Stride of the exchange planes: the node count rounded up to four, so that a
@@ -738,10 +739,9 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
       R v[3] = {sg, vd, vr};
       block_reduce_store<3>(v, rslots, a.red_stride, vg);
     }
-    if (!grid_sync(a.bar, vg)) return -1;
-    tr.mark(TR_CG_PASS);
     R tot[3];
-    grid_total<3>(rslots, a.red_stride, tot, vg);
+    if (!grid_sync_total<3>(a.bar, vg, rslots, a.red_stride, tot)) return -1;
+    tr.mark(TR_CG_PASS);
     tr.value(TR_RR, (double)tot[2]);
     if (k >= 0) {
       ++it;
@@ -1262,10 +1262,9 @@ __device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
       R v[1] = {vd};
       block_reduce_store<1>(v, rslots, a.red_stride, vg);
     }
-    if (!grid_sync(a.bar, vg)) return -1;
-    tr.mark(TR_CG_PASS);
     R tot[3];  // <w,u>, <r,u>, <r,r>
-    grid_total<3>(rslots, a.red_stride, tot, vg);
+    if (!grid_sync_total<3>(a.bar, vg, rslots, a.red_stride, tot)) return -1;
+    tr.mark(TR_CG_PASS);
     tr.value(TR_RR, (double)tot[2]);
     if (k >= 0) {
       ++it;
@@ -1622,10 +1621,9 @@ __device__ int pcg3(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
       R v[1] = {vd};
       block_reduce_store<1>(v, rslots, a.red_stride, vg);
     }
-    if (!grid_sync(a.bar, vg)) return -1;
-    tr.mark(TR_CG_PASS);
     R tot[3];  // <w,u>, <r,u>, <r,r>
-    grid_total<3>(rslots, a.red_stride, tot, vg);
+    if (!grid_sync_total<3>(a.bar, vg, rslots, a.red_stride, tot)) return -1;
+    tr.mark(TR_CG_PASS);
     tr.value(TR_RR, (double)tot[2]);
     if (k >= 0) {
       ++it;
@@ -1683,6 +1681,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   ApplySmem<float>& sm32 = *reinterpret_cast<ApplySmem<float>*>(smem_raw);
   double* stage64 = reinterpret_cast<double*>(stage_raw);
   float* stage32 = reinterpret_cast<float*>(stage_raw);
+  bar_begin(a.bar);
   if (ld_volatile_i32(a.bar.status) != 0) return;  // an earlier solve failed: leave state untouched
   Tracer tr{a.trace, vg.bid};
   tr.mark(TR_START);
@@ -1807,10 +1806,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     });
     block_reduce_store<2>(v, a.red + RS_RZ0 * a.red_stride, a.red_stride, vg);
   }
-  if (!grid_sync(a.bar, vg)) return;
-  tr.mark(TR_RESID);
   double tot0[2];
-  grid_total<2>(a.red + RS_RZ0 * a.red_stride, a.red_stride, tot0, vg);
+  if (!grid_sync_total<2>(a.bar, vg, a.red + RS_RZ0 * a.red_stride, a.red_stride, tot0)) return;
+  tr.mark(TR_RESID);
   const double bb = tot0[1];
   const double thresh = a.tol * a.tol * bb;
 
@@ -1865,10 +1863,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       });
       block_reduce_store<2>(v, a.red32 + RS_RZ0 * a.red_stride, a.red_stride, vg);
     }
-    if (!grid_sync(a.bar, vg)) return;
-    tr.mark(TR_OUTER_INIT);
     float t32[2];
-    grid_total<2>(a.red32 + RS_RZ0 * a.red_stride, a.red_stride, t32, vg);
+    if (!grid_sync_total<2>(a.bar, vg, a.red32 + RS_RZ0 * a.red_stride, a.red_stride, t32)) return;
+    tr.mark(TR_OUTER_INIT);
     int inner = 0;
     CGBufs<float> c{a.d32, {a.r32, a.r32b}, {a.p0f, a.p1f}, {a.s0f, a.s1f}, {a.q32, a.q32b}, {a.X32, a.X32b},
                     a.dinv32, nullptr};
@@ -1960,9 +1957,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       v[0] += rn * rn;
     });
     block_reduce_store<1>(v, a.red + RS_RR * a.red_stride, a.red_stride, vg);
-    if (!grid_sync(a.bar, vg)) return;
     double trr[1];
-    grid_total<1>(a.red + RS_RR * a.red_stride, a.red_stride, trr, vg);
+    if (!grid_sync_total<1>(a.bar, vg, a.red + RS_RR * a.red_stride, a.red_stride, trr)) return;
     tr.mark(TR_OUTER_END);
     rr64 = trr[0];
     conv = trr[0] <= thresh;
@@ -2032,10 +2028,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       });
     }
     block_reduce_store<3>(v, a.red + RS_ES * a.red_stride, a.red_stride, vg);
-    if (!grid_sync(a.bar, vg)) return;
+    double te[3];
+    if (!grid_sync_total<3>(a.bar, vg, a.red + RS_ES * a.red_stride, a.red_stride, te)) return;
     if (vg.bid == 0) {
-      double te[3];
-      grid_total<3>(a.red + RS_ES * a.red_stride, a.red_stride, te, vg);
       if (threadIdx.x == 0 && a.energy) {
         a.stats->e_stored[lvl] += te[0];
         a.stats->e_laser[lvl] += te[1];
