@@ -1045,6 +1045,9 @@ __device__ inline int div_by(int n, int d, unsigned long long M) {
 template <typename R> struct Vec16;
 template <> struct Vec16<float> { using T = float4; };
 template <> struct Vec16<double> { using T = double2; };
+template <int N> struct VecP;  // N floats in one access
+template <> struct VecP<2> { using T = float2; };
+template <> struct VecP<4> { using T = float4; };
 
 template <typename R>
 struct Sums2 { R a, b; };
@@ -1081,6 +1084,32 @@ static __device__ __noinline__ Sums2<R> cg_update(const Grid3 g, const Tiling t,
     } else {
 #pragma unroll
       for (int m = 0; m < VEC; ++m) o[m] = m < cnt ? __ldcg(a + n0 + m) : R(0);
+    }
+  };
+  // the preconditioner's FP32 arrays, VEC values at a time (4 B x VEC)
+  using VP = typename VecP<VEC>::T;
+  auto loadp = [&](const float* a, int n0, int cnt, float (&o)[VEC]) {
+    if (cnt == VEC) {
+      const VP v = __ldcg(reinterpret_cast<const VP*>(a + n0));
+      const float* e = reinterpret_cast<const float*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = e[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = m < cnt ? __ldcg(a + n0 + m) : 0.0f;
+    }
+  };
+  auto storep = [&](float* a, int n0, int cnt, const float (&o)[VEC]) {
+    if (cnt == VEC) {
+      VP v;
+      float* e = reinterpret_cast<float*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) e[m] = o[m];
+      *reinterpret_cast<VP*>(a + n0) = v;
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m)
+        if (m < cnt) a[n0 + m] = o[m];
     }
   };
   auto store = [&](R* a, int n0, int cnt, const R (&o)[VEC]) {
@@ -1306,8 +1335,12 @@ __device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
 // dominant and P^-1 is SPD on the free nodes; D^-1/2 is 0 on Dirichlet
 // nodes).  c = 0.2 gave the fewest iterations on the assembled matrices of
 // the 2 mm and 10 mm workloads (25 instead of 64 with Jacobi at 1e-12).
-// Single-reduction recurrences as in pcg1 / pcg2 with u = P^-1 r, in three
-// phases per iteration, each ended by a grid barrier:
+// The preconditioner runs in FP32 in both precisions (sq, v and the filter;
+// u is stored in the solve's precision and <r,u> accumulated in it): it only
+// has to be a fixed SPD approximation, and in an FP64 solve an FP64 filter
+// was bound by the FP64 pipe.  Single-reduction recurrences as in pcg1 / pcg2
+// with u = P^-1 r, in three phases per iteration, each ended by a grid
+// barrier:
 //   U  (owners, flat): w = own + neighbours' partials of A u; p = u + beta p;
 //      s = w + beta s; x += alpha p; r -= alpha s; v = D^-1/2 r; sum <r,r>;
 //   P  (flat): u = D^-1/2 Q v (27-point separable stencil); sum <r,u>;
@@ -1329,8 +1362,8 @@ struct PCVecs {
   R* q;           // own partial of w = A u
   R* X;           // NXB exchange planes of w's partials
   const R* dinv;  // Jacobi inverse diagonal, 0 on Dirichlet nodes
-  R* sq;          // sqrt(dinv), filled by the first update phase
-  R* v;           // v = sqrt(dinv) r, the preconditioner's input
+  float* sq;      // sqrt(dinv), filled by the first update phase
+  float* v;       // v = sqrt(dinv) r, the preconditioner's input
 };
 
 // Update phase of pcg3 (flat, 16 bytes of every array per lane and step, like
@@ -1357,6 +1390,32 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
       for (int m = 0; m < VEC; ++m) o[m] = m < cnt ? __ldcg(a + n0 + m) : R(0);
     }
   };
+  // the preconditioner's FP32 arrays, VEC values at a time (4 B x VEC)
+  using VP = typename VecP<VEC>::T;
+  auto loadp = [&](const float* a, int n0, int cnt, float (&o)[VEC]) {
+    if (cnt == VEC) {
+      const VP v = __ldcg(reinterpret_cast<const VP*>(a + n0));
+      const float* e = reinterpret_cast<const float*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = e[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) o[m] = m < cnt ? __ldcg(a + n0 + m) : 0.0f;
+    }
+  };
+  auto storep = [&](float* a, int n0, int cnt, const float (&o)[VEC]) {
+    if (cnt == VEC) {
+      VP v;
+      float* e = reinterpret_cast<float*>(&v);
+#pragma unroll
+      for (int m = 0; m < VEC; ++m) e[m] = o[m];
+      *reinterpret_cast<VP*>(a + n0) = v;
+    } else {
+#pragma unroll
+      for (int m = 0; m < VEC; ++m)
+        if (m < cnt) a[n0 + m] = o[m];
+    }
+  };
   auto store = [&](R* a, int n0, int cnt, const R (&o)[VEC]) {
     if (cnt == VEC) {
       V v;
@@ -1373,22 +1432,23 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
   for (int q = gtid; q < ngroups; q += gstride) {
     const int n0 = q * VEC;
     const int cnt = min(VEC, nn - n0);
-    R rk[VEC], sqv[VEC], vn[VEC];
+    R rk[VEC];
+    float sqv[VEC], vn[VEC];
     load(c.r, n0, cnt, rk);
     if (init) {
       R dv[VEC];
       load(c.dinv, n0, cnt, dv);
 #pragma unroll
       for (int m = 0; m < VEC; ++m) {
-        sqv[m] = sqrt(dv[m]);
-        vn[m] = sqv[m] * rk[m];
-        if (sqv[m] != R(0)) vrr = fma(rk[m], rk[m], vrr);
+        sqv[m] = (float)sqrt(dv[m]);
+        vn[m] = sqv[m] * (float)rk[m];
+        if (sqv[m] != 0.0f) vrr = fma(rk[m], rk[m], vrr);
       }
-      store(c.sq, n0, cnt, sqv);
-      store(c.v, n0, cnt, vn);
+      storep(c.sq, n0, cnt, sqv);
+      storep(c.v, n0, cnt, vn);
       continue;
     }
-    load(c.sq, n0, cnt, sqv);
+    loadp(c.sq, n0, cnt, sqv);
     int lf[VEC];
     int rowf = -1;
     {
@@ -1452,8 +1512,8 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
       sn[m] = sk[m];
       rn[m] = rk[m];
       xn[m] = xk[m];
-      vn[m] = R(0);
-      if (m >= cnt || sqv[m] == R(0)) continue;
+      vn[m] = 0.0f;
+      if (m >= cnt || sqv[m] == 0.0f) continue;
       const int n = n0 + m;
       const int f = lf[m];
       R wv = w[m];
@@ -1470,14 +1530,14 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
       sn[m] = first ? wv : fma(beta, sk[m], wv);
       rn[m] = fma(-alpha, sn[m], rk[m]);
       xn[m] = fma(alpha, pn[m], xk[m]);
-      vn[m] = sqv[m] * rn[m];
+      vn[m] = sqv[m] * (float)rn[m];
       vrr = fma(rn[m], rn[m], vrr);
     }
     store(c.p, n0, cnt, pn);
     store(c.s, n0, cnt, sn);
     store(c.r, n0, cnt, rn);
     store(c.x, n0, cnt, xn);
-    store(c.v, n0, cnt, vn);
+    storep(c.v, n0, cnt, vn);
   }
   return vrr;
 }
@@ -1492,16 +1552,22 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
 // arrive by cp.async several layers ahead in a ring of slots; one block
 // barrier per layer.
 template <typename R>
-static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const PCVecs<R> c, R* win, const VGrid vg) {
+static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const PCVecs<R> c, R* win_raw,
+                                          const VGrid vg) {
   const int S = g.nnx * g.nny;
   // NS ring slots, D = NS - 1 layers in flight: a tile column is narrow, so
-  // several layers must be in flight to cover the memory latency
-  constexpr int NS = sizeof(R) == 4 ? 8 : 5, D = NS - 1;
-  static_assert(NS * (PC_WN_MAX + 2 * NT) * (int)sizeof(R) <= STAGE_BYTES,
-                "ring of the widest window fits the dynamic shared memory");
-  const int TX = tp.ex, TY = tp.ey, WXP = TX + 2, WN = (TX + 2) * (TY + 2), SL = WN + 2 * NT;
+  // several layers must be in flight to cover the memory latency.  A slot
+  // holds the layer's window of v and sq of the owned nodes (FP32), then r of
+  // the owned nodes (R).
+  constexpr int NS = 8, D = NS - 1;
+  constexpr int SLOT_MAX = ((PC_WN_MAX + NT) * 4 + NT * (int)sizeof(R) + 15) / 16 * 16;
+  static_assert(NS * SLOT_MAX <= STAGE_BYTES, "ring of the widest window fits the dynamic shared memory");
+  const int TX = tp.ex, TY = tp.ey, WXP = TX + 2, WN = (TX + 2) * (TY + 2);
+  const int RB = ((WN + NT) * 4 + 15) / 16 * 16;                 // byte offset of r in a slot
+  const int SB = (RB + NT * (int)sizeof(R) + 15) / 16 * 16;      // slot bytes
+  unsigned char* ring = reinterpret_cast<unsigned char*>(win_raw);
   const int ntiles = tp.ntx * tp.nty * tp.ntz;
-  const R cw = R(PC_C);
+  const float cw = (float)PC_C;
   const int tid = threadIdx.x;
   const int ty = tid / TX, tx = tid - ty * TX;
   R gam = R(0);
@@ -1512,10 +1578,9 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
     const int i0 = tix * TX, j0 = tiy * TY, k0 = tiz * tp.ez, k1 = min(k0 + tp.ez, g.nnz);
     const int i = i0 + tx, j = j0 + ty;
     const bool own = ty < TY && i < g.nnx && j < g.nny;
-    R tm = R(0), tc = R(0);  // xy-filtered values of layers L - 2, L - 1
-    R sq_c = R(0), r_c = R(0);  // sq, r of the column's node at layer L - 1
-    // slot of layer L: its window of v (zeros outside the mesh), then sq and r
-    // of the owned nodes; async copies, one group per layer
+    float tm = 0.0f, tc = 0.0f;  // xy-filtered values of layers L - 2, L - 1
+    float sq_c = 0.0f;           // sq, r of the column's node at layer L - 1
+    R r_c = R(0);
     // this thread's window entries (w = tid + m NT) and their in-layer node
     // offsets, -1 outside the mesh; fixed for the tile
     int woff[PC_WM];
@@ -1527,22 +1592,23 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
       woff[m] = (w < WN && gi >= 0 && gi < g.nnx && gj >= 0 && gj < g.nny) ? gi + g.nnx * gj : -1;
     }
     const int own_off = i + g.nnx * j;
+    // slot of layer L: async copies, zeros outside the mesh, one group per layer
     auto load_layer = [&](int L, int slot) {
       if (L >= 0 && L < g.nnz && L <= k1) {
-        R* buf = win + slot * SL;
-        const R* vL = c.v + (size_t)S * L;
+        float* buf = reinterpret_cast<float*>(ring + slot * SB);
+        const float* vL = c.v + (size_t)S * L;
 #pragma unroll
         for (int m = 0; m < PC_WM; ++m) {
           const int w = tid + m * NT;
           if (woff[m] >= 0)
-            cp_async<sizeof(R)>(buf + w, vL + woff[m]);
+            cp_async<4>(buf + w, vL + woff[m]);
           else if (w < WN)
-            buf[w] = R(0);
+            buf[w] = 0.0f;
         }
         if (own && L >= k0 && L < k1) {
           const size_t n = (size_t)S * L + own_off;
-          cp_async<sizeof(R)>(buf + WN + tid, c.sq + n);
-          cp_async<sizeof(R)>(buf + WN + NT + tid, c.r + n);
+          cp_async<4>(buf + WN + tid, c.sq + n);
+          cp_async<sizeof(R)>(reinterpret_cast<R*>(ring + slot * SB + RB) + tid, c.r + n);
         }
       }
       cp_async_commit();
@@ -1553,27 +1619,27 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
       cp_async_wait<D - 1>();  // layer L has landed (L + 1 .. L + D - 1 may be in flight)
       __syncthreads();         // ... for every thread; the slot of layer L - 1 is free again
       load_layer(L + D, sl == 0 ? NS - 1 : sl - 1);
-      const R* buf = win + sl * SL;
-      R tl = R(0);
+      const float* buf = reinterpret_cast<const float*>(ring + sl * SB);
+      float tl = 0.0f;
       if (own && L >= 0 && L < g.nnz) {
-        R acc = R(0);
+        float acc = 0.0f;
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-          const R* row = buf + (ty + dy) * WXP + tx;
-          const R t = fma(-cw, row[0] + row[2], row[1]);
-          acc = dy == 1 ? acc + t : fma(-cw, t, acc);
+          const float* row = buf + (ty + dy) * WXP + tx;
+          const float t = fmaf(-cw, row[0] + row[2], row[1]);
+          acc = dy == 1 ? acc + t : fmaf(-cw, t, acc);
         }
         tl = acc;
       }
       if (own && L >= k0 + 1) {  // layer L - 1 is complete
         const int n = i + g.nnx * j + S * (L - 1);
-        const R un = sq_c * fma(-cw, tm + tl, tc);
+        const R un = (R)(sq_c * fmaf(-cw, tm + tl, tc));
         c.u[n] = un;
-        if (sq_c != R(0)) gam = fma(r_c, un, gam);
+        if (sq_c != 0.0f) gam = fma(r_c, un, gam);
       }
       if (own && L >= k0 && L < k1) {
         sq_c = buf[WN + tid];
-        r_c = buf[WN + NT + tid];
+        r_c = reinterpret_cast<const R*>(ring + sl * SB + RB)[tid];
       }
       tm = tc;
       tc = tl;
@@ -1824,7 +1890,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     auto no_fetch64 = [](int, double*) {};
     int res;
     if (a.precond == 1) {
-      PCVecs<double> c3{a.u, a.r, a.p0, a.s0, a.r2, a.q, a.X, a.dinv, a.s1, a.p1};
+      // the FP32 preconditioner arrays live in the first halves of s1 and p1
+      // (FP64 arrays of the node count, unused by this CG form)
+      PCVecs<double> c3{a.u, a.r, a.p0, a.s0, a.r2, a.q, a.X, a.dinv, reinterpret_cast<float*>(a.s1),
+                        reinterpret_cast<float*>(a.p1)};
       auto apply_z = [&](int tile) {
         double vd = 0.0;
         auto emit = [&](int n, int slot, double y, double xin) {
