@@ -36,7 +36,7 @@ FLOPS_VEC_PER_NODE = 14     # PCG vector update, fused dots, p = z + beta p
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 fine micro-step launch of
 # this workload, from the ncu capture summarised in
 # profiles/solve_kernel_fp64_multitrack_10mm.md (the patch is L2-resident)
-FINE_LAUNCH_DRAM_BYTES = 4.738304e6 + 2.513920e6
+FINE_LAUNCH_DRAM_BYTES = 3.081472e6 + 1.470464e6
 
 
 def parse():
@@ -306,13 +306,15 @@ def run_ours(args):
     fine_iters = st["cg_iters_fine"] / max(1, st["solves_fine"])
     launch_s = statistics.mean(fine_ms) / 1e3
     achieved = fine_flops(cfg, fine_iters) / launch_s / 1e12
-    peak = 152 * 4 * 2.07e9 / 1e12   # FP64 FMA: 2 DFMA/clk/SM = 4 flop/clk/SM at 2.07 GHz
+    peak = FP64_PEAK_TFLOPS   # FP64 FMA: 2 DFMA/clk/SM = 4 flop/clk/SM at 2.07 GHz
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": FINE_LAUNCH_DRAM_BYTES,
                 "kernel": "tl::solve_kernel (FP64 fine micro step)",
                 "launch_ms": statistics.mean(fine_ms), "cg_iters_per_launch": fine_iters,
                 "flops_per_launch": fine_flops(cfg, fine_iters),
-                "peak_note": "FP64 pipe, derived: 152 SMs x 4 flop/clk x 2.07 GHz; a DFMA loop measured 1.20 TFLOP/s"}
+                "peak_note": "FP64 pipe, derived: 152 SMs x 4 flop/clk x 2.07 GHz; a DFMA loop measured 1.20 TFLOP/s. "
+                             "Counts the FP64 flops of the apply (65 per element) and of the vector work (14 per node) "
+                             "per CG iteration; the FP32 preconditioner filter is not counted"}
 
     # ---- the precision form on the same workload (FP32 inner CG, FP64 defect correction)
     barrier(ws)
@@ -568,26 +570,34 @@ def run_serve(args):
     return 0
 
 
-# Algorithmic bytes per node of one CG iteration.
-#  fused (element tiles; FP64 path and small refined meshes): the window
-#   update fused into the matrix-free apply reads dinv, r, w-partial, p, s, x
-#   and writes p, s, r, x, w-partial (11 nodal values) plus the element data
-#   the apply reads (FP32: s_e, k_e; FP64: eight eigenvalues), elements ~ nodes;
-#  wide (two-phase, large refined meshes): the update phase reads dinv, r, q,
-#   x, p, s and writes p, s, r, x, z (11 FP32 values); the apply phase reads z
-#   and s_e, k_e and writes q (4 values).
-PASS_BYTES = {"fp32": 11 * 4 + 2 * 4, "fp64": 11 * 8 + 8 * 8}
-WIDE_UPDATE_BYTES = 11 * 4
-WIDE_APPLY_BYTES = 4 * 4
-PASS_FLOPS_FP64 = FLOPS_APPLY_PER_ELEM + FLOPS_VEC_PER_NODE
+# Algorithmic bytes per node of one CG iteration of the default form (the
+# tensor-preconditioned CG, three phases; elements ~ nodes):
+#  update: reads r, q, x, u, p, s (solve precision) and sq (FP32), writes
+#   p, s, r, x (solve precision) and v (FP32); exchange partials on tile faces
+#   are not counted;
+#  preconditioner: reads v and sq (FP32) and r, writes u (solve precision);
+#   the v halo comes from L2 and is not counted;
+#  apply: FP32 on wide tiles reads u and two element coefficients and writes
+#   the partial q; FP64 on element tiles reads u and eight FP64 eigenvalues
+#   per element and writes q.
+UPDATE_BYTES = {"fp32": 12 * 4, "fp64": 10 * 8 + 2 * 4}
+PRECOND_BYTES = {"fp32": 4 * 4, "fp64": 2 * 4 + 2 * 8}
+APPLY_BYTES = {"fp32": 4 * 4, "fp64": 2 * 8 + 8 * 8}
+# FP64 flops of the FP64 form's phases (the FP32 preconditioner filter runs on
+# the FP32 pipe and is not counted): update 5 FMA per node, <r,u> 1 FMA per
+# node, apply FLOPS_APPLY_PER_ELEM per element plus <w,u>.
+UPDATE_FLOPS_FP64 = 10
+PRECOND_FLOPS_FP64 = 2
 HBM_GBS = 6688.8  # measured copy bandwidth of this GB300 (read + write bytes)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
 
 def run_roofline(args):
     """A 256 x 256 x 128-element fine patch (8.5M nodes; 32 x 32 x 16 coarse
     elements refined 8x, plate 40 x 40 x 20 coarse): one micro step in each
-    precision, per-phase times from the device phase tracer (block 0's view:
-    a phase ends when the grid barrier after it is passed)."""
+    precision, per-phase times of the CG iterations from the device phase
+    tracer (block 0's view: a phase ends when the grid barrier after it is
+    passed)."""
     import torch
 
     from paper_2110_12932_gb300 import build as tlbuild
@@ -599,6 +609,7 @@ def run_roofline(args):
                               pNXc=32, pNYc=32, pNZc=16, r=8, m=8,
                               tracks=[(1e-3, 2.5e-3, 4e-3, 2.5e-3, 0.8)])
     nn = fine_nodes(base)
+    ne = 256 * 256 * 128
     out = {}
     names = {v: k for k, v in tl.TRACE_MARKS.items()}
     for prec in ("fp32", "fp64"):
@@ -610,44 +621,47 @@ def run_roofline(args):
         torch.cuda.synchronize()
         ev = [e for e in p.trace(tl.TL_FINE) if e[0] not in (names["rr_value"], names["breakdown_value"])]
         p.close()
+        launch = (ev[-1][1] - ev[0][1]) / 1e9
         ends = [b for (m, b) in ev if m == names["cg_pass"]]
         t = statistics.median([(y - x) / 1e9 for x, y in zip(ends, ends[1:])]) if len(ends) > 1 else float("nan")
         seg = {}
         for (m0, a), (m1, b) in zip(ev, ev[1:]):
             seg.setdefault((m0, m1), []).append((b - a) / 1e9)
-        o = {"pass_us": 1e6 * t, "passes": len(ends)}
-        upd = seg.get((names["cg_pass"], names["cg_u_start"]))
-        if upd:  # two-phase (wide) iterations: update phase, apply phase
-            tu = statistics.median(seg[(names["cg_pass"], names["cg_u_start"])]) + \
-                statistics.median(seg[(names["cg_u_start"], names["cg_u_end"])]) + \
-                statistics.median(seg[(names["cg_u_end"], names["cg_update"])])
-            ta = statistics.median(seg[(names["cg_update"], names["cg_apply"])]) + \
-                statistics.median(seg[(names["cg_apply"], names["cg_pass"])])
-            bu, ba = WIDE_UPDATE_BYTES * nn, WIDE_APPLY_BYTES * nn
-            o.update({"scheme": "two-phase, wide tiles",
-                      "update_phase": {"us": 1e6 * tu, "bytes": bu, "GBps": bu / tu / 1e9,
-                                       "frac_of_measured_hbm": bu / tu / 1e9 / HBM_GBS,
-                                       "block0_share_us": 1e6 * statistics.median(
-                                           seg[(names["cg_u_start"], names["cg_u_end"])]),
-                                       "reduce_and_barrier_us": 1e6 * statistics.median(
-                                           seg[(names["cg_u_end"], names["cg_update"])])},
-                      "apply_phase": {"us": 1e6 * ta, "bytes": ba, "GBps": ba / ta / 1e9,
-                                      "frac_of_measured_hbm": ba / ta / 1e9 / HBM_GBS},
-                      "bytes_per_pass": bu + ba, "GBps": (bu + ba) / t / 1e9,
-                      "frac_of_measured_hbm": (bu + ba) / t / 1e9 / HBM_GBS})
-        else:
-            byt = PASS_BYTES[prec] * nn
-            o.update({"scheme": "fused, element tiles", "bytes_per_pass": byt, "GBps": byt / t / 1e9,
-                      "frac_of_measured_hbm": byt / t / 1e9 / HBM_GBS})
-            if prec == "fp64":
-                fl = PASS_FLOPS_FP64 * nn
-                o.update({"TFLOPs": fl / t / 1e12, "frac_of_fp64_peak": fl / t / 1e12 / 1.25856})
+
+        def med(a, b):
+            return statistics.median(seg[(names[a], names[b])])
+
+        tu = med("cg_pass", "cg_u_start") + med("cg_u_start", "cg_u_end") + med("cg_u_end", "cg_update")
+        tp = med("cg_update", "cg_precond")
+        ta = med("cg_precond", "cg_apply") + med("cg_apply", "cg_pass")
+        bu, bp, ba = UPDATE_BYTES[prec] * nn, PRECOND_BYTES[prec] * nn, APPLY_BYTES[prec] * nn
+
+        def phase(us, byt):
+            return {"us": 1e6 * us, "bytes": byt, "GBps": byt / us / 1e9, "frac_of_measured_hbm": byt / us / 1e9 / HBM_GBS}
+
+        o = {"launch_ms": 1e3 * launch, "cg_iterations": len(ends), "iteration_us": 1e6 * t,
+             "scheme": "tensor-preconditioned CG, three phases; apply on "
+                       + ("wide tiles" if prec == "fp32" else "element tiles"),
+             "update_phase": dict(phase(tu, bu), block0_share_us=1e6 * med("cg_u_start", "cg_u_end"),
+                                  reduce_and_barrier_us=1e6 * med("cg_u_end", "cg_update")),
+             "precond_phase": phase(tp, bp),
+             "apply_phase": phase(ta, ba),
+             "bytes_per_iteration": bu + bp + ba, "GBps": (bu + bp + ba) / t / 1e9,
+             "frac_of_measured_hbm": (bu + bp + ba) / t / 1e9 / HBM_GBS}
+        if prec == "fp64":
+            fa = FLOPS_APPLY_PER_ELEM * ne + 2 * nn
+            o["apply_phase"].update({"fp64_flops": fa, "TFLOPs": fa / ta / 1e12,
+                                     "frac_of_fp64_peak": fa / ta / 1e12 / FP64_PEAK_TFLOPS})
+            fi = fa + (UPDATE_FLOPS_FP64 + PRECOND_FLOPS_FP64) * nn
+            o.update({"fp64_flops_per_iteration": fi, "TFLOPs": fi / t / 1e12,
+                      "frac_of_fp64_peak": fi / t / 1e12 / FP64_PEAK_TFLOPS})
         out[prec] = o
-    line = {"metric": "CG pass throughput (matrix-free apply + vector update)", "mode": "roofline",
-            "config": {"fine_nodes": nn, "fine_elements": 256 * 256 * 128,
-                       "bytes_per_node": {"fused": PASS_BYTES, "wide_update": WIDE_UPDATE_BYTES,
-                                          "wide_apply": WIDE_APPLY_BYTES},
-                       "fp64_flops_per_node": PASS_FLOPS_FP64, "hbm_peak_GBps": HBM_GBS},
+    line = {"metric": "CG iteration throughput (update, preconditioner, matrix-free apply)", "mode": "roofline",
+            "config": {"fine_nodes": nn, "fine_elements": ne,
+                       "bytes_per_node": {"update": UPDATE_BYTES, "precond": PRECOND_BYTES, "apply": APPLY_BYTES},
+                       "fp64_flops": {"apply_per_element": FLOPS_APPLY_PER_ELEM, "update_per_node": UPDATE_FLOPS_FP64,
+                                      "precond_per_node": PRECOND_FLOPS_FP64},
+                       "hbm_peak_GBps": HBM_GBS, "fp64_peak_TFLOPs": FP64_PEAK_TFLOPS},
             "results": out}
     print(json.dumps(line), flush=True)
     return 0
