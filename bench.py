@@ -36,7 +36,7 @@ FLOPS_VEC_PER_NODE = 14     # PCG vector update, fused dots, p = z + beta p
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 fine micro-step launch of
 # this workload, from the ncu capture summarised in
 # profiles/solve_kernel_fp64_multitrack_10mm.md (the patch is L2-resident)
-FINE_LAUNCH_DRAM_BYTES = 3.081472e6 + 1.470464e6
+FINE_LAUNCH_DRAM_BYTES = 3.026432e6 + 1.040640e6
 
 
 def parse():

@@ -215,7 +215,10 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
  * on a non-positive value; 13 the vector-update phase of a CG iteration done
  * (grid barrier passed); 14 / 15 block 0 starts / finished its share of that
  * update phase; 16 the preconditioner phase of a CG iteration done (grid
- * barrier passed).
+ * barrier passed); 17 / 18 / 19 block 0 has done its share of the setup's
+ * element coefficients / Dirichlet increments / laser-load tables; 20 / 21
+ * block 0 has done its share of the states and stored energy / Dirichlet
+ * reactions at the end of the solve.
  * Synchronises.  Errors: TL_EINVAL, TL_ECUDA. */
 tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap,
                               size_t* n_out);

@@ -46,6 +46,7 @@ __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" 
 static_assert(NT >= WX * WY, "a block must cover a tile's window columns");
 static_assert(NT <= 32 * (RED_W + 1), "block_reduce_store parks the lanes of warps 1 .. RED_W");
 constexpr int MAXRECT = 8;
+static_assert(MAXRECT >= 3, "the load tables hold 3 (nnx + nny) values for the Gaussian");
 constexpr int NXB = 7;                // exchange buffers
 // Stride of the exchange planes: the node count rounded up to four, so that a
 // plane starts on a 16-byte boundary (vector loads of four FP32 partials).
@@ -79,9 +80,12 @@ __device__ inline int dir_set(const Grid3& g, const DirSpec& d, int i, int j, in
   return -1;
 }
 
-// Calls body(n, i, j, k) once for every Dirichlet node, the candidates of all
-// sets spread evenly over the grid's threads (a node is visited by the first
-// set that holds it).
+// Calls body(n, i, j, k) once for every Dirichlet node (a node is visited by
+// the first set that holds it).  The candidates go in chunks of 32 consecutive
+// ones, one warp per chunk, dealt round-robin over the blocks: the boundary's
+// FP64 work (interpolation, reactions) spreads over all SMs instead of
+// filling the first blocks, and a warp's loads stay contiguous.  Needs
+// blockDim a multiple of 32.
 template <class Body>
 __device__ inline void for_dirichlet(const Grid3& g, const DirSpec& d, const VGrid& vg, Body body) {
   const int bx = d.box[1] - d.box[0] + 1, by = d.box[3] - d.box[2] + 1, bz = d.box[5] - d.box[4] + 1;
@@ -89,7 +93,11 @@ __device__ inline void for_dirichlet(const Grid3& g, const DirSpec& d, const VGr
                      (d.faces & 2) ? g.nny * g.nnz : 0, (d.faces & 4) ? g.nnx * g.nnz : 0,
                      (d.faces & 8) ? g.nnx * g.nnz : 0, (bx > 0 && by > 0 && bz > 0) ? bx * by * bz : 0};
   const int total = sz[0] + sz[1] + sz[2] + sz[3] + sz[4] + sz[5];
-  for (int m = vg.bid * blockDim.x + threadIdx.x; m < total; m += vg.nblk * blockDim.x) {
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int nchunks = (total + 31) >> 5;
+  for (int c = (threadIdx.x >> 5) * vg.nblk + vg.bid; c < nchunks; c += nwarps * vg.nblk) {
+    const int m = c * 32 + lane;
+    if (m >= total) continue;
     int set = 0, r = m;
     while (r >= sz[set]) r -= sz[set++];
     int i, j, k;
@@ -131,13 +139,29 @@ __device__ inline double trilinear_at(const double* Tc, const Grid3& cg, int gi,
   return v;
 }
 
+// (1 - w) I(Tc0) + w I(Tc1) for two coarse fields at one fine node, with the
+// eight trilinear weights formed once (each sum in the order trilinear_at uses).
+__device__ inline double trilinear_blend(const double* Tc0, const double* Tc1, double w, const Grid3& cg, int gi,
+                                         int gj, int gk, int r) {
+  int I = min(gi / r, cg.nx - 1), J = min(gj / r, cg.ny - 1), K = min(gk / r, cg.nz - 1);
+  double tx = (double)(gi - I * r) / r, ty = (double)(gj - J * r) / r, tz = (double)(gk - K * r) / r;
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    int ax = c & 1, ay = (c >> 1) & 1, az = (c >> 2) & 1;
+    double wt = (ax ? tx : 1.0 - tx) * (ay ? ty : 1.0 - ty) * (az ? tz : 1.0 - tz);
+    const long long n = node_id(cg, I + ax, J + ay, K + az);
+    a += wt * __ldcg(Tc0 + n);
+    b += wt * __ldcg(Tc1 + n);
+  }
+  return (1.0 - w) * a + w * b;
+}
+
 __device__ inline double dir_value(const DirValues& dv, int i, int j, int k, long long n) {
   if (dv.kind == 0) {  // fine patch
     int gi = i + dv.oi * dv.r, gj = j + dv.oj * dv.r, gk = k + dv.ok * dv.r;
     if (gk == 0) return dv.T_bottom;
-    double a = trilinear_at(dv.Tc0, dv.cg, gi, gj, gk, dv.r);
-    double b = trilinear_at(dv.Tc1, dv.cg, gi, gj, gk, dv.r);
-    return (1.0 - dv.w) * a + dv.w * b;
+    return trilinear_blend(dv.Tc0, dv.Tc1, dv.w, dv.cg, gi, gj, gk, dv.r);
   }
   if (k == 0) return dv.T_bottom;
   if (dv.kind == 2)  // coarse node (i, j, k) of the injection box: the coinciding fine node
@@ -199,27 +223,76 @@ __device__ inline double hat_box(int i, int n, double h, double o, double x0, do
 }
 
 // The top load is separable: F(i, j) = sum_f c_f Gx_f(i) Gy_f(j) over one
-// Gaussian factor or one factor per rectangle.  Phase 0 tabulates the 1D
-// factors (nf (nnx + nny) values) so that each transcendental is evaluated
-// once per node line instead of once per top node.
+// Gaussian factor or one factor per rectangle.  Phase 0 tabulates what the
+// factors need, so that each transcendental is evaluated once:
+//  Gaussian: entry p < w = nnx + nny holds erf(alpha (x_p - c)) and entry
+//   w + p exp(-(alpha (x_p - c))^2), x_p the position of x node p (p < nnx)
+//   or of y node p - nnx; after the next grid barrier entry 2w + p gets the
+//   1D hat integral of that node from them (hat_gauss_tab, the same
+//   expressions as hat_gauss), and F is formed after the barrier after that;
+//  rectangles: entry f w + idx holds the box factor of x or y node idx.
 __device__ inline int load_factors(const LoadSpec& L) { return L.kind == 1 ? 1 : (L.kind == 2 ? L.nrect : 0); }
 
-__device__ inline double load_factor(const LoadSpec& L, const Grid3& g, int f, int idx) {
+__device__ inline int load_table_size(const LoadSpec& L, const Grid3& g) {
+  const int w = g.nnx + g.nny;
+  return L.kind == 1 ? 2 * w : (L.kind == 2 ? L.nrect * w : 0);
+}
+
+__device__ inline double load_table_entry(const LoadSpec& L, const Grid3& g, int m) {
+  const int w = g.nnx + g.nny;
+  if (L.kind == 1) {
+    const int p = m < w ? m : m - w;
+    const bool isx = p < g.nnx;
+    const int i = isx ? p : p - g.nnx;
+    const double t = L.alpha * ((isx ? L.ox + g.hx * i : L.oy + g.hy * i) - (isx ? L.xc : L.yc));
+    return m < w ? erf(t) : exp(-t * t);
+  }
+  const int f = m / w, idx = m - f * w;
   const bool isx = idx < g.nnx;
   const int i = isx ? idx : idx - g.nnx;
-  if (L.kind == 1)
-    return isx ? hat_gauss(i, g.nx, g.hx, L.ox, L.xc, L.alpha) : hat_gauss(i, g.ny, g.hy, L.oy, L.yc, L.alpha);
   return isx ? hat_box(i, g.nx, g.hx, L.ox, L.rect[f][0], L.rect[f][1])
              : hat_box(i, g.ny, g.hy, L.oy, L.rect[f][2], L.rect[f][3]);
 }
 
+// hat_gauss from the tabulated erf (ef) and exp (ex) values at the node
+// positions of that direction.
+__device__ inline double hat_gauss_tab(int i, int n, double h, double o, double c, double alpha, const double* ef,
+                                       const double* ex) {
+  const double sp = 0.88622692545275801365;  // sqrt(pi)/2
+  double G = 0.0;
+  if (i > 0) {  // element [x_{i-1}, x_i]; node i carries (x - a)/h
+    double a = o + h * (i - 1);
+    double E0 = sp / alpha * (__ldcg(ef + i) - __ldcg(ef + i - 1));
+    double E1 = (__ldcg(ex + i - 1) - __ldcg(ex + i)) / (2.0 * alpha * alpha);
+    G += (E1 + (c - a) * E0) / h;
+  }
+  if (i < n) {  // element [x_i, x_{i+1}]; node i carries (b - x)/h
+    double b = o + h * (i + 1);
+    double E0 = sp / alpha * (__ldcg(ef + i + 1) - __ldcg(ef + i));
+    double E1 = (__ldcg(ex + i) - __ldcg(ex + i + 1)) / (2.0 * alpha * alpha);
+    G += ((b - c) * E0 - E1) / h;
+  }
+  return G;
+}
+
+// Entry p of the Gaussian's hat table (x node p, or y node p - nnx), from the
+// erf / exp entries.
+__device__ inline double gauss_hat_entry(const LoadSpec& L, const Grid3& g, const double* G, int p) {
+  const int w = g.nnx + g.nny;
+  return p < g.nnx ? hat_gauss_tab(p, g.nx, g.hx, L.ox, L.xc, L.alpha, G, G + w)
+                   : hat_gauss_tab(p - g.nnx, g.ny, g.hy, L.oy, L.yc, L.alpha, G + g.nnx, G + w + g.nnx);
+}
+
+// F(i, j) from the tables (the Gaussian: its hat table at G + 2w).
 __device__ inline double top_load_tab(const LoadSpec& L, const Grid3& g, const double* G, int i, int j) {
   const int nf = load_factors(L), w = g.nnx + g.nny;
-  double F = 0.0;
-  for (int f = 0; f < nf; ++f) {
-    const double c = L.kind == 1 ? L.amp : L.rect[f][4];
-    F += c * __ldcg(G + f * w + i) * __ldcg(G + f * w + g.nnx + j);
+  if (L.kind == 1) {
+    double F = 0.0;
+    F += L.amp * __ldcg(G + 2 * w + i) * __ldcg(G + 2 * w + g.nnx + j);
+    return F;
   }
+  double F = 0.0;
+  for (int f = 0; f < nf; ++f) F += L.rect[f][4] * __ldcg(G + f * w + i) * __ldcg(G + f * w + g.nnx + j);
   return F;
 }
 
@@ -348,7 +421,12 @@ enum TraceMark : int {
   TR_CG_UPDATE = 13,
   TR_CG_U0 = 14,   // block 0 starts its share of a CG update phase
   TR_CG_U1 = 15,   // ... and finished it (before the block reduction)
-  TR_CG_PRECOND = 16  // the preconditioner phase of a CG iteration done (grid barrier passed)
+  TR_CG_PRECOND = 16,  // the preconditioner phase of a CG iteration done (grid barrier passed)
+  TR_P0_ELEMS = 17,    // block 0 has done its share of phase 0's element coefficients
+  TR_P0_DIR = 18,      // ... and of the Dirichlet increments
+  TR_P0_LOAD = 19,     // ... and of the laser-load tables (before the grid barrier)
+  TR_END_ELEMS = 20,   // block 0 has done its share of the states and stored energy
+  TR_END_DIR = 21      // ... and of the Dirichlet reactions (before the reduction)
 };
 constexpr int TRACE_CAP = 1024;
 
@@ -1776,13 +1854,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       mv.dst[n] = v;
     }
   }
+  const double inv_dt = 1.0 / a.dt;  // once per thread: an FP64 division is costly here
   for_elems(g, vg, [&](int e, int ie, int je, int ke) {
     const double Tb = elem_mean(a.T_in, g, ie, je, ke);
     const uint8_t st = a.state[(ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox];
     const double rc = a.mat.rho * (a.mat.c0 + a.mat.c1 * (Tb - a.mat.Tref));
     double k = a.mat.k0 + a.mat.k1 * (Tb - a.mat.Tref);
     if (st == POWDER) k = a.mat.powder_factor * k;
-    const double se = rc * (1.0 / a.dt);
+    const double se = rc * inv_dt;
     a.s_e[e] = se;
     a.k_e[e] = k;
 #pragma unroll
@@ -1792,6 +1871,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       a.sk32[ne + e] = (float)k;
     }
   });
+  tr.mark(TR_P0_ELEMS);
   // increments: 0 on free nodes, g - T^k on Dirichlet nodes (disjoint writes)
   for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool, bool) {
     if (!is_dir(g, a.dir, i, j, k)) a.u[n] = 0.0;
@@ -1799,23 +1879,29 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   for_dirichlet(g, a.dir, vg, [&](int n, int i, int j, int k) {
     a.u[n] = dir_value(a.dv, i, j, k, n) - __ldcg(a.T_in + n);
   });
+  tr.mark(TR_P0_DIR);
   {
-    // one table entry per block first (thread 0, then 32, ...): the erf / exp
-    // chains run on many SMs at once instead of in one block
-    const int nf = load_factors(a.ld), w = g.nnx + g.nny;
-    const int lanes = (blockDim.x + 31) / 32;
-    const int slot = (threadIdx.x % 32 == 0) ? threadIdx.x / 32 : -1;
-    if (slot >= 0)
-      for (int m = vg.bid + vg.nblk * slot; m < nf * w; m += vg.nblk * lanes)
-        a.G[m] = load_factor(a.ld, g, m / w, m % w);
+    // the load tables (see load_table_entry), in chunks of 32 entries, one
+    // warp per chunk, dealt round-robin over the blocks
+    const int ne_tab = load_table_size(a.ld, g);
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int c = (threadIdx.x >> 5) * vg.nblk + vg.bid; c * 32 < ne_tab; c += nwarps * vg.nblk) {
+      const int m = c * 32 + lane;
+      if (m < ne_tab) a.G[m] = load_table_entry(a.ld, g, m);
+    }
   }
+  tr.mark(TR_P0_LOAD);
   if (!grid_sync(a.bar, vg)) return;
   tr.mark(TR_PHASE0);
 
   // ---- phase 1: Jacobi diagonal and right-hand side partials --------------
-  for (int n = gtid; n < S; n += gstride) {
-    int j = n / g.nnx, i = n - j * g.nnx;
-    a.F[n] = top_load_tab(a.ld, g, a.G, i, j);
+  if (a.ld.kind == 1) {  // the Gaussian's 1D hat integrals (chunks of 32, round-robin)
+    const int w = g.nnx + g.nny;
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int c = (threadIdx.x >> 5) * vg.nblk + vg.bid; c * 32 < w; c += nwarps * vg.nblk) {
+      const int p = c * 32 + lane;
+      if (p < w) a.G[2 * w + p] = gauss_hat_entry(a.ld, g, a.G, p);
+    }
   }
   for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool, bool) {
     double di = 0.0;
@@ -1862,10 +1948,13 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     double v[2] = {0.0, 0.0};
     for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool ly, bool lz) {
       double rr = 0.0;
-      if (!is_dir(g, a.dir, i, j, k)) {
-        double Fn = (k == g.nz) ? __ldcg(a.F + (n - S * g.nz)) : 0.0;
-        rr = Fn - gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
+      double Fn = 0.0;
+      if (k == g.nz) {  // the top-face load, kept for the energy account
+        Fn = top_load_tab(a.ld, g, a.G, i, j);
+        a.F[n - S * g.nz] = Fn;
       }
+      if (!is_dir(g, a.dir, i, j, k))
+        rr = Fn - gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
       a.r[n] = rr;
       v[0] += rr * rr * __ldcg(a.dinv + n);
       v[1] += rr * rr;
@@ -2071,6 +2160,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
         v[0] += __ldcg(a.s_e + e) * a.dt * a.vol8 * us;
       }
     });
+    tr.mark(TR_END_ELEMS);
     if (a.energy) {
       for (int n = gtid; n < S; n += gstride) v[1] += a.dt * __ldcg(a.F + n);
       for_dirichlet(g, a.dir, vg, [&](int n, int i, int j, int k) {
@@ -2084,18 +2174,20 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
               int e = ie + g.nx * (je + g.ny * ke);
               double se = __ldcg(a.s_e + e), kk = __ldcg(a.k_e + e);
               int la = (i - ie) + 2 * (j - je) + 4 * (k - ke);
-              double acc = 0.0;
+              double am = 0.0, ak = 0.0;  // row la of M^ u and of K^ T
 #pragma unroll
               for (int b = 0; b < 8; ++b) {
                 int nb = (ie + (b & 1)) + g.nnx * (je + ((b >> 1) & 1)) + S * (ke + (b >> 2));
-                acc += se * a.Mhat[la * 8 + b] * __ldcg(a.u + nb) + kk * a.Khat[la * 8 + b] * __ldcg(a.T_out + nb);
+                am = fma(a.Mhat[la * 8 + b], __ldcg(a.u + nb), am);
+                ak = fma(a.Khat[la * 8 + b], __ldcg(a.T_out + nb), ak);
               }
-              R_n += acc;
+              R_n += se * am + kk * ak;
             }
         if (k == g.nz) R_n -= __ldcg(a.F + (n - S * g.nz));
         v[2] += a.dt * R_n;
       });
     }
+    tr.mark(TR_END_DIR);
     block_reduce_store<3>(v, a.red + RS_ES * a.red_stride, a.red_stride, vg);
     double te[3];
     if (!grid_sync_total<3>(a.bar, vg, a.red + RS_ES * a.red_stride, a.red_stride, te)) return;

@@ -254,7 +254,8 @@ def tl_box_step_noalloc(desc, T_in_ptr, T_out_ptr, state_ptr, stream=None):
 TRACE_MARKS = {0: "start", 1: "phase0", 2: "rhs", 3: "resid", 4: "cg_pass", 5: "outer_init",
                6: "outer_apply", 7: "outer_end", 8: "update", 9: "end", 10: "cg_apply",
                11: "rr_value", 12: "breakdown_value", 13: "cg_update", 14: "cg_u_start", 15: "cg_u_end",
-               16: "cg_precond"}
+               16: "cg_precond", 17: "p0_elems", 18: "p0_dirichlet", 19: "p0_load", 20: "end_elems",
+               21: "end_dirichlet"}
 
 
 def tl_checkpoint_size(h):
