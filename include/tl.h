@@ -15,7 +15,7 @@
  *     tl_coarse_step(p, TL_CORRECT)   corrected T+ at t_n + Dt
  *
  * Every solve is one backward-Euler step of the heat equation Eq.
- * (thermalEqn) (Section 2.1, latent heat omitted) on a uniform mesh of
+ * (thermalEqn) (Section 2.1, latent heat optional) on a uniform mesh of
  * trilinear hexahedra, with conductivity and heat capacity evaluated at the
  * element-mean temperature of the step's start (lagged), a powder/solid/
  * melted element state, and a preconditioned conjugate gradient solve
@@ -119,6 +119,23 @@ typedef struct {
    * these mass-dominated steps for one extra pass per iteration; 0 = the
    * default, the same as 2 */
   int precond;
+  /* latent heat (Eq. thermalEqn's chi rho d f_pc / dt term) as an apparent
+   * heat capacity: rho c(T) becomes rho (c(T) + latent f_pc'(T)) with the
+   * sigmoid f_pc(T) = (1 + tanh(pc_sharpness (T - Tm))) / 2,
+   * Tm = (T_solidus + T_liquidus) / 2, so f_pc' = (pc_sharpness / 2)
+   * (1 - tanh^2(pc_sharpness (T - Tm))) (Eq. 2dPhaseChange of Section 5.1
+   * read as this derivative).  latent = 0 [J/kg]: no latent heat.  Both
+   * levels use it.  Requires latent >= 0 and, when latent > 0,
+   * pc_sharpness > 0 [1/K] and T_liquidus >= T_solidus [K]. */
+  double latent, T_solidus, T_liquidus, pc_sharpness;
+  /* Picard iterations per backward-Euler step (the nonlinear step with the
+   * coefficients evaluated at the new temperature): 0 or 1 = coefficients
+   * lagged at the step's start (one solve); K > 1 = K solves per step, solve
+   * k taking its coefficients from the element means of solve k-1's result
+   * (states stay those of the step's start; only the last solve updates the
+   * states and the energy account).  At most 50; not available in batches
+   * nor with coupling_sweeps > 1. */
+  int picard_iters;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
   /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks
    * must be 16-byte aligned (else tl_create_problem returns TL_EINVAL) */

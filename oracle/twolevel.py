@@ -2,11 +2,19 @@
 
 Test infrastructure only (see the package docstring).
 
-Problem (Section 2.1, Eq. thermalEqn, without latent heat): plate
-[0,Lx]x[0,Ly]x[0,Lz], Dirichlet T_bottom on z = 0, adiabatic elsewhere, a
-laser flux on the top surface z = Lz.  Material: rho constant,
-c(T) = c0 + c1 (T - Tref), k(T) = k0 + k1 (T - Tref); powder elements use
-powder_factor * k.
+Problem (Section 2.1, Eq. thermalEqn): plate [0,Lx]x[0,Ly]x[0,Lz],
+Dirichlet T_bottom on z = 0, adiabatic elsewhere, a laser flux on the top
+surface z = Lz.  Material: rho constant, c(T) = c0 + c1 (T - Tref),
+k(T) = k0 + k1 (T - Tref); powder elements use powder_factor * k.  Latent
+heat (latent = chi > 0): f_pc(T) = (1 + tanh(S (T - Tm))) / 2 with
+Tm = (T_solidus + T_liquidus) / 2 and S = pc_sharpness (Eq. 2dPhaseChange of
+Section 5.1 prints its derivative (S/2)(1 - tanh^2(S (T - Tm))) with the
+argument garbled).  Backward Euler applied to the term chi rho d f_pc/dt
+gives chi rho (f_pc(T^{n+1}) - f_pc(T^n)) / dt; per element it enters the
+heat capacity as the secant chi (f_pc(Tb) - f_pc(Tb0)) / (Tb - Tb0) of the
+element means Tb (of the temperature the coefficients are taken at) and Tb0
+(of the step's start), the derivative f_pc' at the midpoint when
+|S (Tb - Tb0)| < 1e-3.
 
 Two levels (Section 3, Eqs. localProblem and globalPbmAlternate):
   global (coarse) mesh of NXc x NYc x NZc hexes over the plate;
@@ -44,7 +52,14 @@ One macro step t_n -> t_n + Dt (Algorithm 1), this oracle's reading:
 
 Coefficients are lagged: each backward-Euler step evaluates rho c_e and k_e
 at the element mean of the step's starting temperature and the element's
-state at that time.  State rule after every step: element mean T_e of the
+state at that time (with latent heat: the derivative f_pc'(Tb0)).  With
+picard_iters = K > 1 each step is K solves from the same starting
+temperature T^n, solve j taking its coefficients from the temperature T*_j:
+T*_0 = T^n, T*_{j+1} = T*_j + (T_j - T*_j) / 2 for the result T_j of solve j
+(Picard iteration of the nonlinear backward-Euler step, relaxed by 1/2: the
+plain iteration falls into a two-cycle on the latent-heat peak); the states
+stay those of the step's start, and the last solve's coefficients enter the
+energy account.  State rule after every step: element mean T_e of the
 new temperature; MELTED if T_e > T_melt; else POWDER if it was POWDER; else
 SOLID.  Initially an element is POWDER iff its centroid lies within
 powder_depth of the top surface, else SOLID.  The fine states live in a
@@ -115,10 +130,36 @@ class Material:
         self.Tref = cfg["Tref"]
         self.powder_factor = cfg["powder_factor"]
         self.T_melt = cfg["T_melt"]
+        self.latent = float(cfg.get("latent", 0.0))
+        self.Tm = 0.5 * (float(cfg.get("T_solidus", 0.0)) + float(cfg.get("T_liquidus", 0.0)))
+        self.S = float(cfg.get("pc_sharpness", 0.0))
 
-    def coefficients(self, Tbar, state):
-        """(rho c_e, k_e) at element-mean temperature Tbar and state."""
-        rc = self.rho * (self.c0 + self.c1 * (Tbar - self.Tref))
+    def fpc(self, T):
+        """The phase-change sigmoid f_pc(T) = (1 + tanh(S (T - Tm))) / 2."""
+        return 0.5 * (1.0 + np.tanh(self.S * (T - self.Tm)))
+
+    def fpc_prime(self, T):
+        """d f_pc / dT = (S/2)(1 - tanh^2(S (T - Tm)))."""
+        th = np.tanh(self.S * (T - self.Tm))
+        return 0.5 * self.S * (1.0 - th * th)
+
+    def fpc_secant(self, Tb, Tb0):
+        """(f_pc(Tb) - f_pc(Tb0)) / (Tb - Tb0); f_pc' at the midpoint when
+        |S (Tb - Tb0)| < 1e-3."""
+        d = Tb - Tb0
+        near = np.abs(self.S * d) < 1e-3
+        quot = (self.fpc(Tb) - self.fpc(Tb0)) / np.where(near, 1.0, d)
+        return np.where(near, self.fpc_prime(0.5 * (Tb + Tb0)), quot)
+
+    def coefficients(self, Tbar, state, Tbar0=None):
+        """(rho c_e, k_e) at element-mean temperature Tbar and state; Tbar0 =
+        the element means at the step's start (default Tbar) for the latent
+        heat's secant."""
+        if self.latent:
+            lat = self.fpc_secant(Tbar, Tbar if Tbar0 is None else Tbar0)
+            rc = self.rho * (self.c0 + self.c1 * (Tbar - self.Tref) + self.latent * lat)
+        else:
+            rc = self.rho * (self.c0 + self.c1 * (Tbar - self.Tref))
         k = self.k0 + self.k1 * (Tbar - self.Tref)
         k = np.where(state == POWDER, self.powder_factor * k, k)
         return rc, k
@@ -145,6 +186,22 @@ def be_step(mesh, T, s_e, k_e, F, dir_idx, g):
     b = S @ T + F
     Tn = fem.solve_dirichlet(A, b, dir_idx, g)
     return Tn
+
+
+def be_picard(mesh, T, coeffs, dt, F, dir_idx, g, iters):
+    """Backward-Euler step from T with relaxed Picard iterations: solve j (of
+    K = max(1, iters)) takes (rho c_e, k_e) = coeffs(element means of T*_j,
+    element means of T), T*_0 = T, T*_{j+1} = T*_j + (T_j - T*_j) / 2 for the
+    result T_j of solve j.  Returns (T', rho c_e, k_e) of the last solve."""
+    Tb0 = mesh.element_mean(T)
+    Ts = T
+    K = max(1, int(iters))
+    for j in range(K):
+        rc, k = coeffs(mesh.element_mean(Ts), Tb0)
+        Tn = be_step(mesh, T, rc / dt, k, F, dir_idx, g)
+        if j + 1 < K:
+            Ts = Ts + 0.5 * (Tn - Ts)
+    return Tn, rc, k
 
 
 def energy_terms(mesh, T, Tn, s_e, k_e, F, dir_idx, dt):
@@ -178,15 +235,15 @@ class SingleLevel:
     def step(self):
         cfg, mesh = self.cfg, self.mesh
         t = (self.nstep + 1) * self.dt
-        Tbar = mesh.element_mean(self.T)
-        rc, k = self.mat.coefficients(Tbar, self.state)
         pos = self.path.position(t)
         if pos is None:
             F = np.zeros(mesh.nnode)
         else:
             F = fem.gaussian_surface_load(mesh, pos[0], pos[1], cfg["P"], cfg["eta"], cfg["radius"])
         g = np.full(len(self.dir_idx), float(cfg["T_bottom"]))
-        Tn = be_step(mesh, self.T, rc / self.dt, k, F, self.dir_idx, g)
+        st = self.state
+        Tn, _, _ = be_picard(mesh, self.T, lambda Tb, Tb0: self.mat.coefficients(Tb, st, Tb0), self.dt, F,
+                             self.dir_idx, g, cfg.get("picard_iters", 1))
         self.state = self.mat.update_state(mesh.element_mean(Tn), self.state)
         self.T = Tn
         self.nstep += 1
@@ -372,16 +429,15 @@ class TwoLevel:
         self.origin = new
         return True
 
-    def _coarse_coefficients(self):
-        Tbar = self.coarse.element_mean(self.Tc)
-        return self.mat.coefficients(Tbar, self.state_c)
+    def _coarse_coefficients(self, Tbar, Tbar0):
+        return self.mat.coefficients(Tbar, self.state_c, Tbar0)
 
     def predict(self):
         self.move_patch()
-        rc, k = self._coarse_coefficients()
         F = self.coarse_load(self.n)
         g = np.full(len(self.coarse_bottom), float(self.cfg["T_bottom"]))
-        self.Tc_pred = be_step(self.coarse, self.Tc, rc / self.Dt, k, F, self.coarse_bottom, g)
+        self.Tc_pred, _, _ = be_picard(self.coarse, self.Tc, self._coarse_coefficients, self.Dt, F,
+                                       self.coarse_bottom, g, self.cfg.get("picard_iters", 1))
         self._I_now = None
         self._I_pred = None
 
@@ -400,11 +456,10 @@ class TwoLevel:
         g[on_bottom] = c["T_bottom"]
         st = self.fine_state()
         st_flat = st.reshape(-1)
-        Tbar = mesh.element_mean(self.Tf)
-        rc, k = self.mat.coefficients(Tbar, st_flat)
         t = (self.n * self.m + i + 1) * self.dt
         F = self.fine_load(mesh, t)
-        Tn = be_step(mesh, self.Tf, rc / self.dt, k, F, idx, g)
+        Tn, rc, k = be_picard(mesh, self.Tf, lambda Tb, Tb0: self.mat.coefficients(Tb, st_flat, Tb0), self.dt, F,
+                              idx, g, c.get("picard_iters", 1))
         if i == self.m - 1:  # start of the last micro step: what a coupling re-solve starts from
             self._last_start = (self.Tf.copy(), st.copy())
         if self.track_energy:
@@ -467,11 +522,11 @@ class TwoLevel:
         nx, ny, _ = self.nf
         inj_vals = self.Tf[fi + (nx + 1) * (fj + (ny + 1) * fk)]
         inj_idx = self.coarse.node_id(I, J, K)
-        rc, k = self._coarse_coefficients()
         F = self.coarse_load(self.n)
         dir_idx = np.concatenate([self.coarse_bottom, inj_idx])
         g = np.concatenate([np.full(len(self.coarse_bottom), float(c["T_bottom"])), inj_vals])
-        Tn = be_step(self.coarse, self.Tc, rc / self.Dt, k, F, dir_idx, g)
+        Tn, rc, k = be_picard(self.coarse, self.Tc, self._coarse_coefficients, self.Dt, F, dir_idx, g,
+                              c.get("picard_iters", 1))
         e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt) if self.track_energy else None
         return Tn, self.mat.update_state(self.coarse.element_mean(Tn), self.state_c), e
 

@@ -63,6 +63,7 @@ struct Level {
   double* T3 = nullptr;   // iterated coupling (coarse): the corrected fields of two consecutive sweeps
   double* T3b = nullptr;
   uint8_t* state_snap = nullptr;  // iterated coupling: states before the superseded solve (fine: patch window)
+  double* Tp = nullptr;           // Picard iterations: the coefficient temperature between solves
   unsigned long long* trace = nullptr;  // phase timestamps of the level's last solve
   uint8_t* state = nullptr;
   int st_sx = 0, st_sy = 0, st_sz = 0;
@@ -294,6 +295,7 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
     }
     if ((s = alloc_n(p, &L.state_snap, ne)) != TL_OK) return s;
   }
+  if (p->cfg.picard_iters > 1 && (s = alloc_n(p, &L.Tp, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.trace, 2 * TRACE_CAP)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.state, (size_t)L.st_sx * L.st_sy * L.st_sz)) != TL_OK) return s;
   return TL_OK;
@@ -435,7 +437,8 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.G = L.G;
   a.state = L.state;
   const tl_config& c = p->cfg;
-  a.mat = Material{c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref, c.powder_factor, c.T_melt};
+  a.mat = Material{c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref, c.powder_factor, c.T_melt,
+                   c.latent, c.pc_sharpness, 0.5 * (c.T_solidus + c.T_liquidus)};
   a.tol = c.tol;
   a.max_iter = c.max_iter;
   std::memcpy(a.Mc, L.Mc, sizeof a.Mc);
@@ -461,6 +464,27 @@ tl_status launch_solve(tl_problem* p, const Level& L, SolveArgs& a) {
                                               STAGE_BYTES, p->stream);
   p->launches++;
   return cuda_status(e);
+}
+
+// One backward-Euler step as picard_iters solves: every solve starts from
+// T_in; solve j takes its coefficients at the temperature T*_j (T*_0 = T_in,
+// then L.Tp), and every solve but the last writes only
+// T*_{j+1} = T*_j + (T_j - T*_j) / 2 into L.Tp, without touching T_out, the
+// states or the energy account.
+tl_status launch_picard(tl_problem* p, const Level& L, SolveArgs& a) {
+  const int K = std::max(1, p->cfg.picard_iters);
+  if (K == 1) return launch_solve(p, L, a);
+  const int upd = a.update_state, en = a.energy;
+  for (int j = 0; j < K; ++j) {
+    const bool last = j + 1 == K;
+    a.T_coef = j == 0 ? nullptr : L.Tp;
+    a.T_relax = last ? nullptr : L.Tp;
+    a.update_state = last ? upd : 0;
+    a.energy = last ? en : 0;
+    const tl_status s = launch_solve(p, L, a);
+    if (s != TL_OK) return s;
+  }
+  return TL_OK;
 }
 
 int fine_dir_faces(const tl_problem* p) {
@@ -526,7 +550,7 @@ void build_coarse_args(tl_problem* p, bool correct, bool fused_inject, SolveArgs
 tl_status coarse_solve(tl_problem* p, bool correct) {
   SolveArgs a{};
   build_coarse_args(p, correct, false, a);
-  return launch_solve(p, p->C, a);
+  return launch_picard(p, p->C, a);
 }
 
 // Arguments of fine micro step i of the current macro step.
@@ -564,7 +588,7 @@ void build_fine_args(tl_problem* p, int i, SolveArgs& a) {
 tl_status fine_solve(tl_problem* p, int i) {
   SolveArgs a{};
   build_fine_args(p, i, a);
-  return launch_solve(p, p->Fi, a);
+  return launch_picard(p, p->Fi, a);
 }
 
 tl_status validate(const tl_config* c) {
@@ -583,6 +607,10 @@ tl_status validate(const tl_config* c) {
   if (c->precision == TL_FP32_REFINED && !(c->tol_inner > 0 && c->tol_inner < 1)) return TL_EINVAL;
   if (c->inner_tiles < 0 || c->inner_tiles > 2) return TL_EINVAL;
   if (c->coupling_sweeps > 1 && !(c->coupling_tol > 0)) return TL_EINVAL;
+  if (c->picard_iters < 0 || c->picard_iters > 50) return TL_EINVAL;
+  if (c->picard_iters > 1 && c->coupling_sweeps > 1) return TL_EINVAL;
+  if (!(c->latent >= 0)) return TL_EINVAL;
+  if (c->latent > 0 && (!(c->pc_sharpness > 0) || !(c->T_liquidus >= c->T_solidus))) return TL_EINVAL;
   if (c->precond < 0 || c->precond > 2) return TL_EINVAL;
   if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
   for (int j = 0; j < c->ntracks; ++j) {
@@ -1256,6 +1284,7 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
 tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out) {
   if (!b || !p || macro_steps < 0 || !id_out) return TL_EINVAL;
   if (p->cfg.coupling_sweeps > 1) return TL_EINVAL;  // batched sequences use the one-pass correction
+  if (p->cfg.picard_iters > 1) return TL_EINVAL;     // ... and one solve per step
   if (p->phase != NEED_PREDICT) return TL_ESTATE;  // join only between macro steps
   int active = 0;
   for (const auto& j : b->jobs) active += j.active ? 1 : 0;

@@ -28,7 +28,25 @@ enum Status : int {
 
 struct Material {
   double rho, c0, c1, k0, k1, Tref, powder_factor, T_melt;
+  double chi, S, Tm;  // latent heat [J/kg] (0: none), sigmoid sharpness [1/K], centre [K]
 };
+
+// Latent heat per element (the phase-change term of Eq. thermalEqn under
+// backward Euler, chi rho (f_pc(T^{k+1}) - f_pc(T^k)) / dt): the secant
+// (f_pc(Tb) - f_pc(Tb0)) / (Tb - Tb0) of the sigmoid
+// f_pc(T) = (1 + tanh(S (T - Tm))) / 2 between the element means Tb (where the
+// coefficients are taken) and Tb0 (the step's start); its derivative
+// (S/2)(1 - tanh^2(S (T - Tm))) at the midpoint when |S (Tb - Tb0)| < 1e-3.
+__device__ inline double fpc_secant(const Material& m, double Tb, double Tb0) {
+  const double d = Tb - Tb0;
+  if (fabs(m.S * d) < 1e-3) {
+    const double th = tanh(m.S * (0.5 * (Tb + Tb0) - m.Tm));
+    return 0.5 * m.S * (1.0 - th * th);
+  }
+  const double f1 = 0.5 * (1.0 + tanh(m.S * (Tb - m.Tm)));
+  const double f0 = 0.5 * (1.0 + tanh(m.S * (Tb0 - m.Tm)));
+  return (f1 - f0) / d;
+}
 
 struct Grid3 {
   int nx, ny, nz;     // elements

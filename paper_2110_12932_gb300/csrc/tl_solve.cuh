@@ -181,28 +181,6 @@ struct LoadSpec {
   double rect[MAXRECT][5];  // x0, x1, y0, y1, q
 };
 
-// int hat_i(x) exp(-alpha^2 (x-c)^2) dx over the mesh's extent (hat of node i
-// of n+1 nodes, spacing h, origin o), in closed form with erf / exp.
-__device__ inline double hat_gauss(int i, int n, double h, double o, double c, double alpha) {
-  const double sp = 0.88622692545275801365;  // sqrt(pi)/2
-  double G = 0.0;
-  if (i > 0) {  // element [x_{i-1}, x_i]; node i carries (x - a)/h
-    double a = o + h * (i - 1), b = o + h * i;
-    double E0 = sp / alpha * (erf(alpha * (b - c)) - erf(alpha * (a - c)));
-    double E1 = (exp(-(alpha * (a - c)) * (alpha * (a - c))) - exp(-(alpha * (b - c)) * (alpha * (b - c)))) /
-                (2.0 * alpha * alpha);
-    G += (E1 + (c - a) * E0) / h;
-  }
-  if (i < n) {  // element [x_i, x_{i+1}]; node i carries (b - x)/h
-    double a = o + h * i, b = o + h * (i + 1);
-    double E0 = sp / alpha * (erf(alpha * (b - c)) - erf(alpha * (a - c)));
-    double E1 = (exp(-(alpha * (a - c)) * (alpha * (a - c))) - exp(-(alpha * (b - c)) * (alpha * (b - c)))) /
-                (2.0 * alpha * alpha);
-    G += ((b - c) * E0 - E1) / h;
-  }
-  return G;
-}
-
 // int_{x0}^{x1} hat_i(x) dx (interval clipped to the mesh).
 __device__ inline double hat_box(int i, int n, double h, double o, double x0, double x1) {
   x0 = fmax(x0, o);
@@ -228,8 +206,8 @@ __device__ inline double hat_box(int i, int n, double h, double o, double x0, do
 //  Gaussian: entry p < w = nnx + nny holds erf(alpha (x_p - c)) and entry
 //   w + p exp(-(alpha (x_p - c))^2), x_p the position of x node p (p < nnx)
 //   or of y node p - nnx; after the next grid barrier entry 2w + p gets the
-//   1D hat integral of that node from them (hat_gauss_tab, the same
-//   expressions as hat_gauss), and F is formed after the barrier after that;
+//   1D hat integral of that node from them (hat_gauss_tab), and F is formed
+//   after the barrier after that;
 //  rectangles: entry f w + idx holds the box factor of x or y node idx.
 __device__ inline int load_factors(const LoadSpec& L) { return L.kind == 1 ? 1 : (L.kind == 2 ? L.nrect : 0); }
 
@@ -254,8 +232,9 @@ __device__ inline double load_table_entry(const LoadSpec& L, const Grid3& g, int
              : hat_box(i, g.ny, g.hy, L.oy, L.rect[f][2], L.rect[f][3]);
 }
 
-// hat_gauss from the tabulated erf (ef) and exp (ex) values at the node
-// positions of that direction.
+// int hat_i(x) exp(-alpha^2 (x-c)^2) dx over the mesh's extent (hat of node i
+// of n+1 nodes, spacing h, origin o), in closed form from the tabulated
+// erf (ef) and exp (ex) values at the node positions of that direction.
 __device__ inline double hat_gauss_tab(int i, int n, double h, double o, double c, double alpha, const double* ef,
                                        const double* ex) {
   const double sp = 0.88622692545275801365;  // sqrt(pi)/2
@@ -294,23 +273,6 @@ __device__ inline double top_load_tab(const LoadSpec& L, const Grid3& g, const d
   double F = 0.0;
   for (int f = 0; f < nf; ++f) F += L.rect[f][4] * __ldcg(G + f * w + i) * __ldcg(G + f * w + g.nnx + j);
   return F;
-}
-
-__device__ inline double top_load(const LoadSpec& L, const Grid3& g, int i, int j) {
-  if (L.kind == 1) {
-    return L.amp * hat_gauss(i, g.nx, g.hx, L.ox, L.xc, L.alpha) *
-           hat_gauss(j, g.ny, g.hy, L.oy, L.yc, L.alpha);
-  }
-  if (L.kind == 2) {
-    double F = 0.0;
-    for (int a = 0; a < L.nrect; ++a) {
-      double hx = hat_box(i, g.nx, g.hx, L.ox, L.rect[a][0], L.rect[a][1]);
-      double hy = hat_box(j, g.ny, g.hy, L.oy, L.rect[a][2], L.rect[a][3]);
-      F += L.rect[a][4] * hx * hy;
-    }
-    return F;
-  }
-  return 0.0;
 }
 
 // Counters written by block 0 at the end of each solve (index: 0 coarse, 1 fine).
@@ -358,6 +320,12 @@ struct SolveArgs {
   Tiling t;
   const double* T_in;
   double* T_out;
+  // Picard iterations of the nonlinear step: the coefficients are taken at
+  // T_coef (null: T_in); with T_relax set the solve writes only
+  // T_relax = Tc + (T_in + u - Tc) / 2 (Tc the coefficient temperature), not
+  // T_out (T_relax may equal T_coef)
+  const double* T_coef;
+  double* T_relax;
   double* u;     // increment T^{k+1} - T^k (Dirichlet entries prescribed)
   double* r;     // FP64 residual
   double* r2;    // its second buffer (CG pass parity)
@@ -1855,10 +1823,17 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     }
   }
   const double inv_dt = 1.0 / a.dt;  // once per thread: an FP64 division is costly here
+  const double* Tcoef = a.T_coef ? a.T_coef : a.T_in;
   for_elems(g, vg, [&](int e, int ie, int je, int ke) {
-    const double Tb = elem_mean(a.T_in, g, ie, je, ke);
+    const double Tb = elem_mean(Tcoef, g, ie, je, ke);
     const uint8_t st = a.state[(ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox];
-    const double rc = a.mat.rho * (a.mat.c0 + a.mat.c1 * (Tb - a.mat.Tref));
+    double rc;
+    if (a.mat.chi != 0.0) {
+      const double Tb0 = a.T_coef ? elem_mean(a.T_in, g, ie, je, ke) : Tb;
+      rc = a.mat.rho * (a.mat.c0 + a.mat.c1 * (Tb - a.mat.Tref) + a.mat.chi * fpc_secant(a.mat, Tb, Tb0));
+    } else {
+      rc = a.mat.rho * (a.mat.c0 + a.mat.c1 * (Tb - a.mat.Tref));
+    }
     double k = a.mat.k0 + a.mat.k1 * (Tb - a.mat.Tref);
     if (st == POWDER) k = a.mat.powder_factor * k;
     const double se = rc * inv_dt;
@@ -2134,7 +2109,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
 
   // ---- phase 3: update, states, energy -------------------------------------
   tr.mark(TR_UPDATE);
-  for (int n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
+  if (a.T_relax) {  // an intermediate Picard solve: only the next coefficient temperature
+    for (int n = gtid; n < nn; n += gstride) {
+      const double ts = __ldcg(Tcoef + n);
+      a.T_relax[n] = ts + 0.5 * (__ldcg(a.T_in + n) + __ldcg(a.u + n) - ts);
+    }
+  } else {
+    for (int n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
+  }
   if (a.update_state || a.energy) {
     if (!grid_sync(a.bar, vg)) return;
     double v[3] = {0.0, 0.0, 0.0};

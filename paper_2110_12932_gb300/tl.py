@@ -47,6 +47,8 @@ class tl_config(C.Structure):
         ("precision", C.c_int), ("tol", C.c_double), ("tol_inner", C.c_double),
         ("max_iter", C.c_int), ("inner_tiles", C.c_int),
         ("coupling_sweeps", C.c_int), ("coupling_tol", C.c_double), ("precond", C.c_int),
+        ("latent", C.c_double), ("T_solidus", C.c_double), ("T_liquidus", C.c_double),
+        ("pc_sharpness", C.c_double), ("picard_iters", C.c_int),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]

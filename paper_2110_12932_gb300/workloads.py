@@ -32,11 +32,16 @@ MATERIAL = dict(
     powder_depth=50e-6,  # m, top layer that starts as powder
     powder_factor=0.01,  # k_powder = powder_factor * k_solid
     T_melt=1900.0,       # K, powder consolidates above this element-mean T
+    latent=0.0,          # J/kg, latent heat of fusion (0: off; Ti64 ~ 2.86e5)
+    T_solidus=1878.0,    # K, phase-change sigmoid centred at (T_solidus + T_liquidus) / 2
+    T_liquidus=1923.0,   # K
+    pc_sharpness=0.05,   # 1/K, sigmoid sharpness S
 )
 PROCESS = dict(P=195.0, eta=0.4, radius=50e-6)
 THERMAL = dict(T0=293.0, T_bottom=293.0)
 SOLVER = dict(precision=0, tol=1e-12, tol_inner=1e-5, max_iter=2000, inner_tiles=0,
-              coupling_sweeps=1, coupling_tol=1e-10, precond=0, coarse_source=0, bc_weight_literal=0, energy=1)
+              coupling_sweeps=1, coupling_tol=1e-10, precond=0, coarse_source=0, bc_weight_literal=0, energy=1,
+              picard_iters=1)
 
 
 def raster_tracks(x_start, x_end, y_center, n_tracks, hatch, speed):

@@ -80,6 +80,8 @@ def _einval(lib, **over):
     dict(tracks=[(0.0, 0.0, 1e-3, 0.0, 0.0)]),           # zero speed
     dict(coarse_source=2), dict(precision=7), dict(inner_tiles=3), dict(inner_tiles=-1),
     dict(precond=3), dict(precond=-1), dict(coupling_sweeps=2, coupling_tol=0.0),
+    dict(picard_iters=51), dict(picard_iters=-1), dict(picard_iters=2, coupling_sweeps=2),
+    dict(latent=-1.0), dict(latent=2.86e5, pc_sharpness=0.0), dict(latent=2.86e5, T_liquidus=1800.0),
 ])
 def test_invalid_config_is_rejected_on_host(lib, over):
     assert _einval(lib, **over) == tl.TL_EINVAL

@@ -326,8 +326,9 @@ def test_coupled_correction_multitrack_first_macro_step():
     prob.close()
 
 
-def test_coupled_problems_stay_out_of_batches():
-    cfg = workloads.workload("single_track_tiny", coupling_sweeps=3)
+@pytest.mark.parametrize("over", [dict(coupling_sweeps=3), dict(picard_iters=3, latent=2.86e5)])
+def test_coupled_and_picard_problems_stay_out_of_batches(over):
+    cfg = workloads.workload("single_track_tiny", **over)
     p = tl.Problem(cfg)
     b = tl.Batch(launches_per_round=2, max_jobs=2)
     with pytest.raises(tl.TLError):
@@ -371,3 +372,43 @@ def test_preconditioners_agree_and_tensor_needs_fewer_iterations():
     (a, sa, st1), (b, sb, st2) = out
     assert rel(b, a) <= 1e-10 and np.array_equal(sa, sb)
     assert st2["cg_iters_fine"] * 2 < st1["cg_iters_fine"]
+
+
+# ---- latent heat and Picard iterations of the nonlinear step ------------------
+
+@pytest.mark.parametrize("picard", [1, 4])
+def test_latent_heat_picard_against_oracle(picard):
+    cfg = workloads.workload("single_track_tiny", latent=2.86e5, picard_iters=picard)
+    prob, ref, errs = run_both(cfg, 16, check_every=4)
+    st = prob.stats()
+    assert st["solves_fine"] == 16 * cfg["m"] * picard and st["solves_coarse"] == 16 * 2 * picard
+    for lvl in ("fine", "coarse"):  # the energy account of the last solve of every step
+        for k in ("stored", "laser", "flux"):
+            o = ref.energy[f"{lvl}_{k}"]
+            assert abs(st[f"energy_{lvl}_{k}"] - o) <= 1e-8 * max(abs(o), abs(ref.energy[f"{lvl}_laser"])), (lvl, k)
+    prob.close()
+
+
+def test_latent_heat_picard_refined_against_oracle():
+    cfg = workloads.workload("single_track_tiny", latent=2.86e5, picard_iters=4, precision=tl.TL_FP32_REFINED,
+                             tol=1e-10, tol_inner=1e-5)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    prob.macro_steps(12)
+    ref.run(12)
+    Tf, _ = prob.temperature(tl.TL_FINE)
+    Tc, _ = prob.temperature(tl.TL_COARSE)
+    assert rel(Tf, ref.Tf) <= REFINED_TOL and rel(Tc, ref.Tc) <= REFINED_TOL
+    assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+    prob.close()
+
+
+def test_zero_latent_and_one_picard_iteration_is_the_plain_step():
+    base = tl.Problem(workloads.workload("single_track_tiny"))
+    same = tl.Problem(workloads.workload("single_track_tiny", latent=0.0, picard_iters=0))
+    base.macro_steps(4)
+    same.macro_steps(4)
+    assert np.array_equal(base.temperature(tl.TL_FINE)[0], same.temperature(tl.TL_FINE)[0])
+    assert np.array_equal(base.temperature(tl.TL_COARSE)[0], same.temperature(tl.TL_COARSE)[0])
+    base.close()
+    same.close()

@@ -251,3 +251,81 @@ def test_coupling_energy_account_counts_final_solves():
     for lvl in ("fine", "coarse"):
         tot = sum(e["stored"] for l2, e in o.step_energy if l2 == lvl)
         assert abs(tot - o.energy[f"{lvl}_stored"]) <= 1e-9 * abs(tot)
+
+
+# ---- latent heat (Eq. thermalEqn's phase-change term) and Picard iterations --
+
+def _latent_material(**over):
+    return TL.Material(W.workload("single_track_tiny", latent=2.86e5, **over))
+
+
+def test_phase_change_sigmoid_derivative_and_integral():
+    """f_pc' is the derivative of f_pc (central differences) and integrates to
+    the sigmoid's full rise, 1 (a wrong factor of S/2 or a missing T fails)."""
+    from scipy.integrate import quad
+    mat = _latent_material()
+    T = np.linspace(mat.Tm - 300.0, mat.Tm + 300.0, 61)
+    h = 1e-3
+    fd = (mat.fpc(T + h) - mat.fpc(T - h)) / (2 * h)
+    assert np.max(np.abs(mat.fpc_prime(T) - fd)) <= 1e-6 * np.max(fd)
+    total, _ = quad(lambda x: float(mat.fpc_prime(x)), mat.Tm - 1500.0, mat.Tm + 1500.0, points=[mat.Tm], limit=200)
+    assert abs(total - 1.0) <= 1e-10
+    assert abs(mat.fpc(mat.Tm) - 0.5) <= 1e-15 and mat.fpc(mat.Tm - 2000.0) < 1e-15
+
+
+def test_phase_change_secant():
+    """The secant is the difference quotient of f_pc, the derivative in the
+    limit; the two branches meet at the switch |S dT| = 1e-3."""
+    mat = _latent_material()
+    a = np.array([1800.0, 1890.0, 1900.5, 1950.0])
+    b = a + 37.0
+    assert np.allclose(mat.fpc_secant(b, a), (mat.fpc(b) - mat.fpc(a)) / 37.0, rtol=1e-13, atol=0)
+    assert np.allclose(mat.fpc_secant(a, a), mat.fpc_prime(a), rtol=1e-15, atol=0)
+    d = 1e-3 / mat.S
+    below = mat.fpc_secant(a + d * (1 - 1e-9), a)
+    above = mat.fpc_secant(a + d * (1 + 1e-9), a)
+    assert np.allclose(below, above, rtol=1e-6, atol=0)
+
+
+def test_picard_reaches_the_nonlinear_backward_euler_step():
+    """With enough Picard iterations the step satisfies the nonlinear
+    backward-Euler equation with its coefficients (latent secant, c(T), k(T))
+    taken at its own result; one lagged solve does not."""
+    dt = 50e-6
+    res = {}
+    for K in (1, 30):
+        cfg = W.workload("single_track_tiny", latent=2.86e5, picard_iters=K)
+        sl = TL.SingleLevel(cfg, 16, 8, 4, dt)
+        for _ in range(3):
+            sl.step()
+        T0, st = sl.T.copy(), sl.state.copy()
+        sl.step()
+        mesh = sl.mesh
+        rc, k = sl.mat.coefficients(mesh.element_mean(sl.T), st, mesh.element_mean(T0))
+        A = mesh.assemble(rc / dt, k)
+        S = mesh.assemble(rc / dt, np.zeros_like(k))
+        pos = sl.path.position(4 * dt)
+        F = fem.gaussian_surface_load(mesh, pos[0], pos[1], cfg["P"], cfg["eta"], cfg["radius"])
+        free = np.setdiff1d(np.arange(mesh.nnode), sl.dir_idx)
+        res[K] = np.linalg.norm((A @ sl.T - S @ T0 - F)[free]) / np.linalg.norm(F)
+    assert res[30] <= 1e-9
+    assert res[1] >= 1e-3
+
+
+def test_latent_heat_energy_identity_every_solve():
+    """Each solve's stored heat (with the latent secant) equals the laser input
+    plus the Dirichlet flux, with Picard iterations on both levels."""
+    cfg = W.workload("single_track_tiny", latent=2.86e5, picard_iters=3)
+    ref = TL.TwoLevel(cfg, energy=True).run(3)
+    assert len(ref.step_energy) == 3 * (cfg["m"] + 1)
+    for _, e in ref.step_energy:
+        scale = max(abs(e["stored"]), abs(e["laser"]), 1e-30)
+        assert abs(e["stored"] - e["laser"] - e["flux"]) <= 1e-10 * scale
+
+
+def test_latent_heat_changes_the_solution_and_zero_latent_does_not():
+    base = TL.TwoLevel(W.workload("single_track_tiny"), energy=False).run(2)
+    zero = TL.TwoLevel(W.workload("single_track_tiny", latent=0.0, picard_iters=1), energy=False).run(2)
+    lat = TL.TwoLevel(W.workload("single_track_tiny", latent=2.86e5, picard_iters=3), energy=False).run(2)
+    assert np.array_equal(base.Tf, zero.Tf) and np.array_equal(base.Tc, zero.Tc)
+    assert np.max(np.abs(lat.Tf - base.Tf)) > 1.0
