@@ -152,7 +152,7 @@ typedef struct {
   int64_t macro_steps, substeps;
   int64_t cg_iters_fine, cg_iters_coarse;    /* all inner CG iterations        */
   int64_t outer_iters_fine, outer_iters_coarse; /* defect-correction sweeps (refined) */
-  int64_t solves_fine, solves_coarse;
+  int64_t solves_fine, solves_coarse;       /* solves run (picard_iters per step) */
   int32_t max_iters_fine, max_iters_coarse;  /* largest per-solve inner count  */
   int32_t origin[3];                         /* patch origin, coarse node index */
   int64_t patch_moves;

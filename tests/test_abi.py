@@ -96,3 +96,13 @@ def test_null_arguments(lib):
     lib.tl_destroy_problem(None)
     for s in (0, -1, -2, -3, -4, -5, -6):
         assert tl.tl_status_string(s) != "unknown status"
+
+
+def test_trace_mark_names_cover_the_kernel_marks():
+    """Every phase marker the solve kernel records has a name in the binding."""
+    with open(os.path.join(ROOT, "paper_2110_12932_gb300", "csrc", "tl_solve.cuh")) as f:
+        src = f.read()
+    body = src[src.index("enum TraceMark"):]
+    body = body[:body.index("};")]
+    values = {int(v) for v in re.findall(r"TR_[A-Z0-9_]+\s*=\s*(\d+)", body)}
+    assert values and values == set(tl.TRACE_MARKS)
