@@ -104,6 +104,37 @@ class BoxMesh:
         return A
 
 
+def top_face_matrix(mesh, h_f):
+    """CSR matrix sum_f h_f int_f phi_a phi_b dA over the top faces (z = top,
+    one per top-layer element, x fastest then y): the exact surface mass of
+    the bilinear face hats, M1x (x) M1y per face (local face node
+    a = ax + 2 ay), times the face's transfer coefficient h_f [W/(m^2 K)]."""
+    Mx, _ = line_matrices(mesh.hx)
+    My, _ = line_matrices(mesh.hy)
+    Mf = np.kron(My, Mx)
+    je, ie = np.meshgrid(np.arange(mesh.ny), np.arange(mesh.nx), indexing="ij")
+    ie, je = ie.ravel(), je.ravel()
+    conn = np.stack([mesh.node_id(ie + ax, je + ay, mesh.nz) for ay in (0, 1) for ax in (0, 1)], axis=1)
+    h_f = np.broadcast_to(np.asarray(h_f, dtype=np.float64), (len(ie),))
+    data = h_f[:, None, None] * Mf[None]
+    rows = np.repeat(conn[:, :, None], 4, axis=2)
+    cols = np.repeat(conn[:, None, :], 4, axis=1)
+    H = sp.coo_matrix((data.ravel(), (rows.ravel(), cols.ravel())), shape=(mesh.nnode, mesh.nnode)).tocsr()
+    H.sum_duplicates()
+    return H
+
+
+def top_face_mean(mesh, T):
+    """Mean of the four nodal values of every top face (x fastest, then y)."""
+    je, ie = np.meshgrid(np.arange(mesh.ny), np.arange(mesh.nx), indexing="ij")
+    ie, je = ie.ravel(), je.ravel()
+    s = T[mesh.node_id(ie, je, mesh.nz)].copy()
+    s = s + T[mesh.node_id(ie + 1, je, mesh.nz)]
+    s = s + T[mesh.node_id(ie, je + 1, mesh.nz)]
+    s = s + T[mesh.node_id(ie + 1, je + 1, mesh.nz)]
+    return s * 0.25
+
+
 def solve_spd(A, b):
     """Solve the SPD system A x = b: SuperLU for small systems, CG to a
     relative residual of 1e-14 for large ones."""

@@ -3,8 +3,10 @@
 Test infrastructure only (see the package docstring).
 
 Problem (Section 2.1, Eq. thermalEqn): plate [0,Lx]x[0,Ly]x[0,Lz],
-Dirichlet T_bottom on z = 0, adiabatic elsewhere, a laser flux on the top
-surface z = Lz.  Material: rho constant, c(T) = c0 + c1 (T - Tref),
+Dirichlet T_bottom on z = 0, adiabatic sides, a laser flux on the top
+surface z = Lz, which also loses heat (Section 3.1; off by default): by
+convection h_conv (T - T_amb) on both levels and by radiation
+sigma eps (T^4 - T_amb^4) on the local level only (see Surface).  Material: rho constant, c(T) = c0 + c1 (T - Tref),
 k(T) = k0 + k1 (T - Tref); powder elements use powder_factor * k.  Latent
 heat (latent = chi > 0): f_pc(T) = (1 + tanh(S (T - Tm))) / 2 with
 Tm = (T_solidus + T_liquidus) / 2 and S = pc_sharpness (Eq. 2dPhaseChange of
@@ -171,6 +173,38 @@ class Material:
         return new
 
 
+# Stefan-Boltzmann constant (CODATA 2018); Section 3.1 prints 5.87e-8.
+SIGMA_SB = 5.670374419e-8
+
+
+class Surface:
+    """Heat loss through the top surface (Section 3.1): convection
+    h_conv (T - T_amb) on both levels, plus radiation
+    sigma eps (T^4 - T_amb^4) on the local (fine) level.  Backward Euler with
+    the radiation written as h_rad(T*) (T - T_amb),
+    h_rad = sigma eps (T*^2 + T_amb^2)(T* + T_amb), per top face at the face
+    mean of the coefficient temperature T* (exact at a Picard fixed point)."""
+
+    def __init__(self, cfg, radiation):
+        self.h = float(cfg.get("h_conv", 0.0))
+        self.eps = float(cfg.get("emissivity", 0.0)) if radiation else 0.0
+        self.T_amb = float(cfg.get("T_amb", 293.0))
+        self.sigma = float(cfg.get("sigma_sb", SIGMA_SB))
+
+    def active(self):
+        return self.h != 0.0 or self.eps != 0.0
+
+    def coefficient(self, Tf):
+        """Transfer coefficient per face at face-mean temperatures Tf."""
+        if self.eps == 0.0:
+            return np.full(np.shape(Tf), self.h)
+        Ta = self.T_amb
+        return self.h + self.sigma * self.eps * (Tf * Tf + Ta * Ta) * (Tf + Ta)
+
+    def matrix(self, mesh, Ts):
+        return fem.top_face_matrix(mesh, self.coefficient(fem.top_face_mean(mesh, Ts)))
+
+
 def initial_state(mesh, Lz, powder_depth):
     """POWDER iff the element centroid is within powder_depth of the top."""
     _, _, ke = mesh.elem_ijk
@@ -178,42 +212,56 @@ def initial_state(mesh, Lz, powder_depth):
     return np.where(Lz - zc < powder_depth, POWDER, SOLID).astype(np.uint8)
 
 
-def be_step(mesh, T, s_e, k_e, F, dir_idx, g):
-    """One backward-Euler step (S + K) T' = S T + F with T'[dir_idx] = g,
-    S = sum_e s_e Mhat (s_e = rho c_e / dt), K = sum_e k_e Khat; returns T'."""
+def be_step(mesh, T, s_e, k_e, F, dir_idx, g, H=None, T_amb=0.0):
+    """One backward-Euler step (S + K + H) T' = S T + F + H T_amb with
+    T'[dir_idx] = g, S = sum_e s_e Mhat (s_e = rho c_e / dt),
+    K = sum_e k_e Khat, H the top-surface transfer matrix (none: adiabatic
+    top); returns T'."""
     A = mesh.assemble(s_e, k_e)
     S = mesh.assemble(s_e, np.zeros_like(k_e))
     b = S @ T + F
+    if H is not None:
+        A = A + H
+        b = b + H @ np.full(mesh.nnode, float(T_amb))
     Tn = fem.solve_dirichlet(A, b, dir_idx, g)
     return Tn
 
 
-def be_picard(mesh, T, coeffs, dt, F, dir_idx, g, iters):
+def be_picard(mesh, T, coeffs, dt, F, dir_idx, g, iters, surface=None):
     """Backward-Euler step from T with relaxed Picard iterations: solve j (of
     K = max(1, iters)) takes (rho c_e, k_e) = coeffs(element means of T*_j,
-    element means of T), T*_0 = T, T*_{j+1} = T*_j + (T_j - T*_j) / 2 for the
-    result T_j of solve j.  Returns (T', rho c_e, k_e) of the last solve."""
+    element means of T) and the top-surface matrix of T*_j (surface, if
+    active), T*_0 = T, T*_{j+1} = T*_j + (T_j - T*_j) / 2 for the result T_j
+    of solve j.  Returns (T', rho c_e, k_e, H) of the last solve."""
     Tb0 = mesh.element_mean(T)
     Ts = T
     K = max(1, int(iters))
+    on = surface is not None and surface.active()
     for j in range(K):
         rc, k = coeffs(mesh.element_mean(Ts), Tb0)
-        Tn = be_step(mesh, T, rc / dt, k, F, dir_idx, g)
+        H = surface.matrix(mesh, Ts) if on else None
+        Tn = be_step(mesh, T, rc / dt, k, F, dir_idx, g, H, surface.T_amb if on else 0.0)
         if j + 1 < K:
             Ts = Ts + 0.5 * (Tn - Ts)
-    return Tn, rc, k
+    return Tn, rc, k, H
 
 
-def energy_terms(mesh, T, Tn, s_e, k_e, F, dir_idx, dt):
-    """Energy bookkeeping of one step (J): stored heat, laser input and the
-    heat entering through the Dirichlet rows (their reactions)."""
+def energy_terms(mesh, T, Tn, s_e, k_e, F, dir_idx, dt, H=None, T_amb=0.0):
+    """Energy bookkeeping of one step (J): stored heat, laser input, the heat
+    entering through the Dirichlet rows (their reactions) and the heat lost
+    through the top surface; stored = laser + flux - loss."""
     S = mesh.assemble(s_e, np.zeros_like(k_e))
     K = mesh.assemble(np.zeros_like(s_e), k_e)
     u = Tn - T
     Su = S @ u
     R = Su + K @ Tn - F
+    loss = 0.0
+    if H is not None:
+        q = H @ (Tn - T_amb)
+        R = R + q
+        loss = dt * float(q.sum())
     return dict(stored=dt * float(Su.sum()), laser=dt * float(F.sum()),
-                flux=dt * float(R[dir_idx].sum()))
+                flux=dt * float(R[dir_idx].sum()), loss=loss)
 
 
 class SingleLevel:
@@ -230,6 +278,7 @@ class SingleLevel:
         self.state = initial_state(self.mesh, cfg["Lz"], cfg["powder_depth"])
         _, _, k = self.mesh.node_ijk()
         self.dir_idx = np.flatnonzero(k == 0)
+        self.surface = Surface(cfg, radiation=True)
         self.nstep = 0
 
     def step(self):
@@ -242,8 +291,8 @@ class SingleLevel:
             F = fem.gaussian_surface_load(mesh, pos[0], pos[1], cfg["P"], cfg["eta"], cfg["radius"])
         g = np.full(len(self.dir_idx), float(cfg["T_bottom"]))
         st = self.state
-        Tn, _, _ = be_picard(mesh, self.T, lambda Tb, Tb0: self.mat.coefficients(Tb, st, Tb0), self.dt, F,
-                             self.dir_idx, g, cfg.get("picard_iters", 1))
+        Tn, _, _, _ = be_picard(mesh, self.T, lambda Tb, Tb0: self.mat.coefficients(Tb, st, Tb0), self.dt, F,
+                                self.dir_idx, g, cfg.get("picard_iters", 1), self.surface)
         self.state = self.mat.update_state(mesh.element_mean(Tn), self.state)
         self.T = Tn
         self.nstep += 1
@@ -281,8 +330,10 @@ class TwoLevel:
         _, _, kc = self.coarse.node_ijk()
         self.coarse_bottom = np.flatnonzero(kc == 0)
         self.n = 0
-        self.energy = dict(fine_stored=0.0, fine_laser=0.0, fine_flux=0.0,
-                           coarse_stored=0.0, coarse_laser=0.0, coarse_flux=0.0)
+        self.energy = dict(fine_stored=0.0, fine_laser=0.0, fine_flux=0.0, fine_loss=0.0,
+                           coarse_stored=0.0, coarse_laser=0.0, coarse_flux=0.0, coarse_loss=0.0)
+        self.surf_f = Surface(cfg, radiation=True)    # local domain: convection + radiation
+        self.surf_c = Surface(cfg, radiation=False)   # global domain: convection
         self.step_energy = []          # per-solve energy terms (fine and coarse)
         self.origin = self._origin_for(0, None)
         self.Tf = self._interp_fine(self.Tc, self.origin)
@@ -436,8 +487,8 @@ class TwoLevel:
         self.move_patch()
         F = self.coarse_load(self.n)
         g = np.full(len(self.coarse_bottom), float(self.cfg["T_bottom"]))
-        self.Tc_pred, _, _ = be_picard(self.coarse, self.Tc, self._coarse_coefficients, self.Dt, F,
-                                       self.coarse_bottom, g, self.cfg.get("picard_iters", 1))
+        self.Tc_pred, _, _, _ = be_picard(self.coarse, self.Tc, self._coarse_coefficients, self.Dt, F,
+                                          self.coarse_bottom, g, self.cfg.get("picard_iters", 1), self.surf_c)
         self._I_now = None
         self._I_pred = None
 
@@ -458,12 +509,12 @@ class TwoLevel:
         st_flat = st.reshape(-1)
         t = (self.n * self.m + i + 1) * self.dt
         F = self.fine_load(mesh, t)
-        Tn, rc, k = be_picard(mesh, self.Tf, lambda Tb, Tb0: self.mat.coefficients(Tb, st_flat, Tb0), self.dt, F,
-                              idx, g, c.get("picard_iters", 1))
+        Tn, rc, k, H = be_picard(mesh, self.Tf, lambda Tb, Tb0: self.mat.coefficients(Tb, st_flat, Tb0), self.dt,
+                                 F, idx, g, c.get("picard_iters", 1), self.surf_f)
         if i == self.m - 1:  # start of the last micro step: what a coupling re-solve starts from
             self._last_start = (self.Tf.copy(), st.copy())
         if self.track_energy:
-            e = energy_terms(mesh, self.Tf, Tn, rc / self.dt, k, F, idx, self.dt)
+            e = energy_terms(mesh, self.Tf, Tn, rc / self.dt, k, F, idx, self.dt, H, self.surf_f.T_amb)
             self._add_energy("fine", e)
             self._last_fine_e = e
         new_state = self.mat.update_state(mesh.element_mean(Tn), st_flat)
@@ -471,7 +522,7 @@ class TwoLevel:
         self.Tf = Tn
 
     def _add_energy(self, level, e, sign=1.0):
-        for key in ("stored", "laser", "flux"):
+        for key in ("stored", "laser", "flux", "loss"):
             self.energy[f"{level}_{key}"] += sign * e[key]
         if sign > 0:
             self.step_energy.append((level, e))
@@ -525,9 +576,10 @@ class TwoLevel:
         F = self.coarse_load(self.n)
         dir_idx = np.concatenate([self.coarse_bottom, inj_idx])
         g = np.concatenate([np.full(len(self.coarse_bottom), float(c["T_bottom"])), inj_vals])
-        Tn, rc, k = be_picard(self.coarse, self.Tc, self._coarse_coefficients, self.Dt, F, dir_idx, g,
-                              c.get("picard_iters", 1))
-        e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt) if self.track_energy else None
+        Tn, rc, k, H = be_picard(self.coarse, self.Tc, self._coarse_coefficients, self.Dt, F, dir_idx, g,
+                                 c.get("picard_iters", 1), self.surf_c)
+        e = (energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F, dir_idx, self.Dt, H, self.surf_c.T_amb)
+             if self.track_energy else None)
         return Tn, self.mat.update_state(self.coarse.element_mean(Tn), self.state_c), e
 
     def macro_step(self):

@@ -170,6 +170,8 @@ def tl_status_string(status):
 def make_config(cfg, stream=None):
     """tl_config from a workload dict (keys = tl_config fields + tracks).
     Returns (config, keep-alive objects)."""
+    if cfg.get("h_conv", 0.0) or cfg.get("emissivity", 0.0):
+        raise NotImplementedError("top-surface convection / radiation is not in the CUDA path")
     c = tl_config()
     for name, _ in tl_config._fields_:
         if name in ("path", "ntracks", "stream", "alloc", "free", "alloc_ctx"):

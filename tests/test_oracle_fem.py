@@ -155,3 +155,28 @@ def test_dense_brute_force_solve():
     x_dense = np.linalg.solve(Ad, bd)
     x = fem.solve_dirichlet(mesh.assemble(s, k), b, dir_idx, g)
     assert np.allclose(x, x_dense, rtol=1e-12, atol=1e-12)
+
+
+def test_top_face_matrix_against_quadrature():
+    """The top-surface transfer matrix equals 2 x 2 Gauss quadrature of the
+    products of bilinear face hats, face by face, with per-face coefficients."""
+    mesh = fem.BoxMesh(3, 2, 2, 0.1, 0.2, 0.3, origin=(0.5, -0.25, 1.0))
+    rng = np.random.default_rng(7)
+    h_f = rng.uniform(1.0, 5.0, mesh.nx * mesh.ny)
+    H = fem.top_face_matrix(mesh, h_f).toarray()
+    ref = np.zeros((mesh.nnode, mesh.nnode))
+    gp = np.array([0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)])
+    f = 0
+    for je in range(mesh.ny):
+        for ie in range(mesh.nx):
+            nodes = [mesh.node_id(ie + ax, je + ay, mesh.nz) for ay in (0, 1) for ax in (0, 1)]
+            for u in gp:
+                for v in gp:
+                    phi = np.array([(1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v])
+                    w = 0.25 * mesh.hx * mesh.hy
+                    for a in range(4):
+                        for b in range(4):
+                            ref[nodes[a], nodes[b]] += h_f[f] * w * phi[a] * phi[b]
+            f += 1
+    assert np.allclose(H, ref, rtol=1e-13, atol=1e-16)
+    assert abs(H.sum() - np.sum(h_f) * mesh.hx * mesh.hy) <= 1e-13 * H.sum()

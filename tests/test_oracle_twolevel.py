@@ -329,3 +329,53 @@ def test_latent_heat_changes_the_solution_and_zero_latent_does_not():
     lat = TL.TwoLevel(W.workload("single_track_tiny", latent=2.86e5, picard_iters=3), energy=False).run(2)
     assert np.array_equal(base.Tf, zero.Tf) and np.array_equal(base.Tc, zero.Tc)
     assert np.max(np.abs(lat.Tf - base.Tf)) > 1.0
+
+
+# ---- top-surface heat loss: convection and radiation (Section 3.1) ---------
+
+def _steady_cfg(**over):
+    base = dict(tracks=[], powder_depth=0.0, c1=0.0, k1=0.0, T0=1500.0, T_bottom=1500.0, T_amb=293.0)
+    base.update(over)
+    return W.workload("single_track_tiny", **base)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.6])
+def test_steady_profile_with_surface_losses(eps):
+    """Constant k, Dirichlet bottom, top losing h (T - T_amb) + sigma eps
+    (T^4 - T_amb^4): the steady field is linear in z, T_top the root of
+    k (T_top - T_b) / Lz + q(T_top) = 0 (found here by a bracketing root
+    finder), and Q1 elements reproduce it exactly; one huge time step with
+    Picard iterations reaches it.  A wrong sign, scale or T_amb term fails."""
+    from scipy.optimize import brentq
+    cfg = _steady_cfg(h_conv=4.0e4, emissivity=eps, picard_iters=40 if eps else 1)
+    sl = TL.SingleLevel(cfg, 4, 2, 8, 1e9)
+    sl.step()
+    k, Lz, Tb, Ta = cfg["k0"], cfg["Lz"], cfg["T_bottom"], cfg["T_amb"]
+    sigma = TL.SIGMA_SB
+
+    def residual(Tt):
+        return k * (Tt - Tb) / Lz + cfg["h_conv"] * (Tt - Ta) + sigma * eps * (Tt ** 4 - Ta ** 4)
+
+    Tt = brentq(residual, Ta, Tb, xtol=1e-14, rtol=1e-15)
+    _, _, z = sl.mesh.node_xyz()
+    expect = Tb + (Tt - Tb) * z / Lz
+    assert Tt < Tb - 10.0
+    assert np.max(np.abs(sl.T - expect)) <= 1e-8 * Tb
+
+
+def test_surface_loss_energy_identity_every_solve():
+    """stored = laser + Dirichlet flux - surface loss for every solve, with
+    convection on both levels and radiation on the local one."""
+    cfg = W.workload("single_track_tiny", h_conv=50.0, emissivity=0.5, T_amb=293.0, picard_iters=3)
+    ref = TL.TwoLevel(cfg, energy=True).run(3)
+    assert ref.energy["fine_loss"] > 0 and ref.energy["coarse_loss"] != 0
+    for _, e in ref.step_energy:
+        scale = max(abs(e["stored"]), abs(e["laser"]), abs(e["loss"]), 1e-30)
+        assert abs(e["stored"] - e["laser"] - e["flux"] + e["loss"]) <= 1e-10 * scale
+
+
+def test_surface_off_is_the_plain_step():
+    base = TL.TwoLevel(W.workload("single_track_tiny"), energy=True).run(2)
+    off = TL.TwoLevel(W.workload("single_track_tiny", h_conv=0.0, emissivity=0.0), energy=True).run(2)
+    assert np.array_equal(base.Tf, off.Tf) and np.array_equal(base.Tc, off.Tc)
+    assert off.energy["fine_loss"] == 0.0 and off.energy["coarse_loss"] == 0.0
