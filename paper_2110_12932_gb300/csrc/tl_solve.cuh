@@ -680,7 +680,6 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
   const Grid3 g = a.g;
   const Tiling t = a.t;
   const int nn = g.nnx * g.nny * g.nnz;
-  const int ne = g.nx * g.ny * g.nz;
   const int ntiles = t.ntx * t.nty * t.ntz;
   R alpha = R(0), beta = R(0), gamma = R(0);
   int it = 0;
@@ -1308,7 +1307,6 @@ __device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
                     R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
   R* s_scal = red_scalars<R>();  // broadcast of the step scalars
   const Grid3 g = a.g;
-  const int nn = g.nnx * g.nny * g.nnz;
   const int ntiles = t.ntx * t.nty * t.ntz;
   R alpha = R(0), beta = R(0), gamma = R(0);
   int it = 0;
