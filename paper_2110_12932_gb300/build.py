@@ -1,8 +1,9 @@
 """Compile the CUDA library ``libtl.so`` in-tree for sm_103a (GB300).
 
 The library has two translation units (csrc/tl_api.cu, the two-level path,
-and csrc/tl_noalloc.cu, the allocation-free single step); it links the CUDA runtime statically, so the only run-time dependency
-is the driver.
+and csrc/tl_noalloc.cu, the allocation-free single step); it links the CUDA
+runtime statically, so the only run-time dependency is the NVIDIA driver's
+libcuda.
 """
 from __future__ import annotations
 
