@@ -106,3 +106,11 @@ def test_trace_mark_names_cover_the_kernel_marks():
     body = body[:body.index("};")]
     values = {int(v) for v in re.findall(r"TR_[A-Z0-9_]+\s*=\s*(\d+)", body)}
     assert values and values == set(tl.TRACE_MARKS)
+
+
+@pytest.mark.parametrize("over", [dict(h_conv=10.0), dict(emissivity=0.4)])
+def test_surface_losses_are_refused_by_the_binding(over):
+    """Top-surface losses exist in the oracle only; the binding must not pass
+    such a configuration to the CUDA path, which would ignore it."""
+    with pytest.raises(NotImplementedError):
+        tl.make_config(workloads.workload("single_track_tiny", **over))
