@@ -261,7 +261,9 @@ typedef struct tl_batch tl_batch;
 tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl_batch** out);
 
 /* Add a problem for macro_steps more macro steps; *id_out gets its job id.
- * Errors: TL_ESTATE (not between macro steps), TL_ENOMEM (batch full). */
+ * Errors: TL_ESTATE (not between macro steps), TL_ENOMEM (batch full),
+ * TL_EINVAL (a problem with coupling_sweeps > 1 or picard_iters > 1: batched
+ * sequences run one solve per step and the one-pass correction). */
 tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out);
 
 /* Enqueue one round (asynchronous after a synchronisation with the previous
