@@ -19,7 +19,12 @@ beyond that.
 
 Pins (tests/test_oracle_*.py): element matrices against Gauss quadrature;
 laser and box loads against adaptive quadrature and the erf closed form;
-the closed-form discrete eigenmode decay; the discrete energy identity; the
-patch-covers-domain identity; the r = m = 1 identity; brute-force dense
-solves on tiny meshes; patch-motion copy/interpolation exactness.
+the closed-form discrete eigenmode decay and the second-order convergence of
+the oracle's own eigenmode solutions to the continuum decay; the discrete
+energy identity; the patch-covers-domain identity; the r = m = 1 identity;
+brute-force dense solves on tiny meshes; patch-motion copy/interpolation
+exactness; the coarse box source's total power and first moments against the
+swept rectangles (track turns included); the injection set against the
+coarse nodes at free fine nodes; the CG branch of the sparse solver against a
+direct solve; the saw-tooth of the multirate scheme's error (Section 5.1).
 """
