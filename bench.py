@@ -476,7 +476,7 @@ def run_batch(args):
                 "data": "synthetic",
                 "config": {"workload": f"batch_jobs({args.jobs}, seed 20211025)", "jobs": len(jobs),
                            "fine_dof_substeps": total_work, "precision": "fp32_refined", "tol": 1e-10,
-                           "launches_per_round": args.launches_per_round, "graph_mode": info["graph_mode"],
+                           "launches_per_round": args.launches_per_round,
                            "inner_tiles": args.inner_tiles,
                            "step": "one batched cooperative launch (each job's next solve)"},
                 "gpu_launches": launches, "clocks": clk, "wall_s": wall,

@@ -136,6 +136,18 @@ typedef struct {
    * states and the energy account).  At most 50; not available in batches
    * nor with coupling_sweeps > 1. */
   int picard_iters;
+  /* heat loss through the top surface (Section 3.1): convection
+   * h_conv (T - T_amb) [W/(m^2 K)] on the top of both levels, radiation
+   * sigma_SB emissivity (T^4 - T_amb^4) on the top of the fine patch (the
+   * local domain); h_conv = emissivity = 0: adiabatic top.  Requires
+   * h_conv >= 0, 0 <= emissivity <= 1, T_amb > 0 [K] when either is on. */
+  double h_conv, emissivity, T_amb;
+  /* time limit [s] of every device-side grid barrier wait; 0 = 1 s, at most
+   * 60 s.  A wait that runs out ends the launch at that barrier in every
+   * block (no block passes a barrier that another left), records
+   * TL_ETIMEOUT and leaves the problem's fields and states as the last
+   * complete solve left them. */
+  double barrier_timeout;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
   /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks
    * must be 16-byte aligned (else tl_create_problem returns TL_EINVAL) */
@@ -272,12 +284,13 @@ tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out)
 tl_status tl_batch_round(tl_batch* b, int* active_out);
 
 /* Synchronise and report (and remove from the batch) up to cap jobs that
- * finished their macro steps; their problems return to their own streams. */
+ * finished their macro steps or whose solve failed in a round (a failed job
+ * leaves at once; tl_sync on its problem returns the failure); their problems
+ * return to their own streams. */
 tl_status tl_batch_poll(tl_batch* b, int* ids, int cap, int* n_out);
 
-/* Active jobs, launches (rounds) so far, graph mode (always 0: a round is a
- * single launch). */
-tl_status tl_batch_info(const tl_batch* b, int* active, long long* launches, int* graph_mode);
+/* Active jobs and launches (rounds) so far; either pointer may be NULL. */
+tl_status tl_batch_info(const tl_batch* b, int* active, long long* launches);
 
 void tl_batch_destroy(tl_batch* b);
 

@@ -66,6 +66,7 @@ struct Level {
   double* Tp = nullptr;           // Picard iterations: the coefficient temperature between solves
   unsigned long long* trace = nullptr;  // phase timestamps of the level's last solve
   uint8_t* state = nullptr;
+  uint8_t* st_new = nullptr;  // new element states of a solve until its commit
   int st_sx = 0, st_sy = 0, st_sz = 0;
   double Mc[8], Kc[8], Md = 0, Kd = 0, vol8 = 0, Mhat[64], Khat[64];
 };
@@ -298,6 +299,7 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
   if (p->cfg.picard_iters > 1 && (s = alloc_n(p, &L.Tp, nn)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.trace, 2 * TRACE_CAP)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.state, (size_t)L.st_sx * L.st_sy * L.st_sz)) != TL_OK) return s;
+  if ((s = alloc_n(p, &L.st_new, ne)) != TL_OK) return s;
   return TL_OK;
 }
 
@@ -392,6 +394,13 @@ LoadSpec box_load(const tl_problem* p, int n) {
   return ld;
 }
 
+// Time limit of the device barriers' waits: barrier_timeout seconds, 1 s by default.
+unsigned long long barrier_limit_ns(const tl_config& c) {
+  if (!(c.barrier_timeout > 0)) return BAR_DEFAULT_LIMIT_NS;
+  const double ns = c.barrier_timeout * 1e9;
+  return ns < 1.0 ? 1ull : (ns > 6e10 ? 60000000000ull : (unsigned long long)ns);
+}
+
 void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.g = L.g;
   a.t = L.t;
@@ -436,6 +445,7 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.F = L.F;
   a.G = L.G;
   a.state = L.state;
+  a.st_new = L.st_new;
   const tl_config& c = p->cfg;
   a.mat = Material{c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref, c.powder_factor, c.T_melt,
                    c.latent, c.pc_sharpness, 0.5 * (c.T_solidus + c.T_liquidus)};
@@ -450,7 +460,7 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.vol8 = L.vol8;
   std::memcpy(a.Mhat, L.Mhat, sizeof a.Mhat);
   std::memcpy(a.Khat, L.Khat, sizeof a.Khat);
-  a.bar = Barrier{p->bar, p->bar + BAR_GEN, p->status};
+  a.bar = Barrier{reinterpret_cast<unsigned long long*>(p->bar), p->status, barrier_limit_ns(c)};
   a.red = p->red;
   a.red32 = p->red32;
   a.red_stride = p->red_stride;
@@ -613,6 +623,10 @@ tl_status validate(const tl_config* c) {
   if (c->latent > 0 && (!(c->pc_sharpness > 0) || !(c->T_liquidus >= c->T_solidus))) return TL_EINVAL;
   if (c->precond < 0 || c->precond > 2) return TL_EINVAL;
   if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
+  if (!(c->barrier_timeout >= 0) || c->barrier_timeout > 60.0) return TL_EINVAL;
+  if (!(c->h_conv >= 0) || !(c->emissivity >= 0) || c->emissivity > 1.0) return TL_EINVAL;
+  if ((c->h_conv > 0 || c->emissivity > 0) && !(c->T_amb > 0)) return TL_EINVAL;
+  if (c->h_conv > 0 || c->emissivity > 0) return TL_EINVAL;  // top-surface losses: oracle only so far
   for (int j = 0; j < c->ntracks; ++j) {
     const tl_track& k = c->path[j];
     if (!(k.speed > 0)) return TL_EINVAL;
@@ -832,8 +846,9 @@ struct tl_batch {
   SolveArgs* d_args = nullptr; // R x cap job arguments
   BatchTable* h_tab = nullptr; // pinned staging of the same
   SolveArgs* h_args = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int graph_state = 0;         // rounds are single launches; no graph
+  int* d_st = nullptr;         // per launch slot: the job's status word at the end of the round
+  int* h_st = nullptr;         // pinned copy
+  std::vector<int> round_ids;  // job id of each launch slot of the last round
   long long launches = 0, rounds = 0;
 };
 
@@ -1081,8 +1096,44 @@ struct CkptHeader {
   int32_t dims[12];   // NXc NYc NZc, fine nx ny nz, map sx sy sz, r, m, precision
   int32_t n, oi, oj, ok;
   int64_t patch_moves, coupling_resolves;
+  uint64_t cfg_hash;  // config_hash: every value that fixes the results, the scan path, the build
 };
 constexpr uint64_t CKPT_MAGIC = 0x746c636b70743031ull;  // "tlckpt01"
+constexpr uint32_t CKPT_VERSION = 2;
+
+// 64-bit FNV-1a over the values of the configuration that fix a run's results
+// (geometry, material, process, solver and coupling settings, the tracks) and
+// an identifier of this library build; the stream, the allocator and the
+// barrier time limit are left out.
+static uint64_t config_hash(const tl_problem* p) {
+  uint64_t h = 1469598103934665603ull;
+  auto add = [&](const void* v, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(v);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  const tl_config& c = p->cfg;
+  const double d[] = {c.Lx, c.Ly, c.Lz, c.dt_coarse, c.T0, c.T_bottom, c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref,
+                      c.powder_depth, c.powder_factor, c.T_melt, c.P, c.eta, c.radius, c.tol, c.tol_inner,
+                      c.coupling_tol, c.latent, c.T_solidus, c.T_liquidus, c.pc_sharpness, c.h_conv,
+                      c.emissivity, c.T_amb};
+  const int32_t i[] = {c.NXc, c.NYc, c.NZc, c.pNXc, c.pNYc, c.pNZc, c.r, c.m, c.coarse_source,
+                       c.bc_weight_literal, c.energy, (int32_t)c.precision, c.max_iter, c.inner_tiles,
+                       c.coupling_sweeps, c.precond, c.picard_iters, (int32_t)p->tracks.size()};
+  add(d, sizeof d);
+  add(i, sizeof i);
+  for (const tl_track& k : p->tracks) {
+    const double t[5] = {k.x0, k.y0, k.x1, k.y1, k.speed};
+    add(t, sizeof t);
+  }
+  static const char build[] = __DATE__ " " __TIME__;
+  const uint64_t sizes[2] = {sizeof(SolveArgs), sizeof(DevStats)};
+  add(build, sizeof build - 1);
+  add(sizes, sizeof sizes);
+  return h;
+}
 
 static void ckpt_dims(const tl_problem* p, int32_t (&d)[12]) {
   const Level &C = p->C, &F = p->Fi;
@@ -1124,7 +1175,8 @@ tl_status tl_checkpoint_save(const tl_problem* p, void* host_out, size_t bytes) 
   unsigned char* b = static_cast<unsigned char*>(host_out);
   CkptHeader h{};
   h.magic = CKPT_MAGIC;
-  h.version = 1;
+  h.version = CKPT_VERSION;
+  h.cfg_hash = config_hash(p);
   h.stats_bytes = (uint32_t)sizeof(DevStats);
   ckpt_dims(p, h.dims);
   h.n = p->n;
@@ -1153,8 +1205,8 @@ tl_status tl_checkpoint_load(tl_problem* p, const void* host_in, size_t bytes) {
   std::memcpy(&h, host_in, sizeof h);
   int32_t d[12];
   ckpt_dims(p, d);
-  if (h.magic != CKPT_MAGIC || h.version != 1 || h.stats_bytes != sizeof(DevStats) ||
-      std::memcmp(d, h.dims, sizeof d) != 0)
+  if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION || h.stats_bytes != sizeof(DevStats) ||
+      std::memcmp(d, h.dims, sizeof d) != 0 || h.cfg_hash != config_hash(p))
     return TL_EINVAL;
   if (h.n < 0 || h.oi < 0 || h.oj < 0 || h.oi + p->cfg.pNXc > p->cfg.NXc || h.oj + p->cfg.pNYc > p->cfg.NYc ||
       h.ok != p->ok)
@@ -1266,14 +1318,18 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
   const size_t targs = (size_t)b->R * b->cap * sizeof(SolveArgs), ttab = sizeof(BatchTable);
   e = cudaMalloc(&b->d_tab, ttab);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_args, targs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_st, BATCH_MAX * sizeof(int));
   if (e == cudaSuccess) e = cudaHostAlloc(&b->h_tab, ttab, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc(&b->h_args, targs, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&b->h_st, BATCH_MAX * sizeof(int), cudaHostAllocDefault);
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->d_tab);
     cudaFree(b->d_args);
+    cudaFree(b->d_st);
     cudaFreeHost(b->h_tab);
     cudaFreeHost(b->h_args);
+    cudaFreeHost(b->h_st);
     delete b;
     return e == cudaErrorMemoryAllocation ? TL_ENOMEM : TL_ECUDA;
   }
@@ -1313,6 +1369,19 @@ tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out)
 }
 
 namespace {
+
+// After the stream is synchronised: jobs whose solve failed in the last round
+// leave the batch (their problem keeps its status word, which tl_sync reports).
+void retire_failed(tl_batch* b) {
+  for (size_t q = 0; q < b->round_ids.size(); ++q) {
+    auto& j = b->jobs[b->round_ids[q]];
+    if (j.active && b->h_st[q] != 0) {
+      j.active = false;
+      b->finished.push_back(b->round_ids[q]);
+    }
+  }
+  b->round_ids.clear();
+}
 
 // Split the blocks of one launch over its jobs in proportion to their element
 // counts (at least one block each, at most the job's reduction width).
@@ -1356,6 +1425,7 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
   if (!b) return TL_EINVAL;
   cudaError_t e = cudaStreamSynchronize(b->stream);  // staging buffers free again
   if (e != cudaSuccess) return cuda_status(e);
+  retire_failed(b);
   BatchTable& tab = *b->h_tab;
   std::vector<long long> w;
   std::vector<int> capb;
@@ -1383,6 +1453,7 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
       ++ns;
     }
     tab.nsolves[nj] = ns;
+    b->round_ids.push_back((int)id);
     seen |= 1 << pmode_of(j.p->cfg);
     capb.push_back(j.p->red_stride);
     w.push_back(work);
@@ -1429,10 +1500,16 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
   if (e != cudaSuccess) return cuda_status(e);
   const BatchTable* tp = b->d_tab;
   const SolveArgs* ap = b->d_args;
-  void* kargs[] = {(void*)&tp, (void*)&ap};
+  int* sp = b->d_st;
+  void* kargs[] = {(void*)&tp, (void*)&ap, (void*)&sp};
   e = cudaLaunchCooperativeKernel(batch_kernel_for(mode), dim3(tab.first[nj]), dim3(NT), kargs, STAGE_BYTES,
                                   b->stream);
-  if (e != cudaSuccess) return cuda_status(e);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_st, b->d_st, (size_t)nj * sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e != cudaSuccess) {
+    b->round_ids.clear();
+    return cuda_status(e);
+  }
   b->launches++;
   b->rounds++;
   return TL_OK;
@@ -1442,6 +1519,7 @@ tl_status tl_batch_poll(tl_batch* b, int* ids, int cap, int* n_out) {
   if (!b || !n_out || (cap > 0 && !ids)) return TL_EINVAL;
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_status(e);
+  retire_failed(b);
   // jobs that just reached their target are retired here too
   for (size_t id = 0; id < b->jobs.size(); ++id) {
     auto& j = b->jobs[id];
@@ -1463,13 +1541,12 @@ tl_status tl_batch_poll(tl_batch* b, int* ids, int cap, int* n_out) {
   return TL_OK;
 }
 
-tl_status tl_batch_info(const tl_batch* b, int* active, long long* launches, int* graph_mode) {
+tl_status tl_batch_info(const tl_batch* b, int* active, long long* launches) {
   if (!b) return TL_EINVAL;
   int a = 0;
   for (const auto& j : b->jobs) a += j.active ? 1 : 0;
   if (active) *active = a;
   if (launches) *launches = b->launches;
-  if (graph_mode) *graph_mode = b->graph_state;
   return TL_OK;
 }
 
@@ -1478,11 +1555,12 @@ void tl_batch_destroy(tl_batch* b) {
   cudaStreamSynchronize(b->stream);
   for (auto& j : b->jobs)
     if (j.p) j.p->stream = j.saved_stream;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
   cudaFree(b->d_tab);
   cudaFree(b->d_args);
+  cudaFree(b->d_st);
   cudaFreeHost(b->h_tab);
   cudaFreeHost(b->h_args);
+  cudaFreeHost(b->h_st);
   delete b;
 }
 

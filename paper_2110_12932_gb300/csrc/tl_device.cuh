@@ -67,16 +67,22 @@ __host__ __device__ inline int split_lo(int n, int parts, int a) {
 }
 
 // ---------------------------------------------------------------------------
-// Time-limited grid barrier for cooperative (co-resident) launches.  Every
-// block arrives on one counter; the last arrival resets it and releases the
-// generation word.  (Measured on GB300 with 152 to 608 blocks: 2.2 - 2.4 us
-// per barrier, against 2.9 - 3.2 us with a two-level tree of 32-block groups;
-// the arrivals on one word do not queue noticeably at this block count.)
-// Every wait gives up after `limit_ns` of global time, records ST_TIMEOUT and
-// returns false; a block that sees an error recorded by another returns false
-// too, so that all blocks leave the kernel.
-// Word layout (BAR_WORDS unsigned ints, zero at creation): [0] counter,
-// [BAR_GEN] generation, [BAR_STATUS] status.
+// Time-limited grid barrier for cooperative (co-resident) launches.  One
+// 64-bit word holds the arrivals (low half) and the generation (high half):
+// every block arrives with one atomic add; the block whose add completes the
+// count releases the next generation with a second add that also clears the
+// count.  (Measured on GB300 with 152 to 608 blocks: 2.2 - 2.4 us per
+// barrier for the one-counter scheme, against 2.9 - 3.2 us with a two-level
+// tree of 32-block groups; the arrivals on one word do not queue noticeably
+// at this block count.)
+// A barrier either releases every block or none: a block whose wait exceeds
+// the time limit withdraws its arrival (compare-and-swap, possible only while
+// some block has not arrived, so the count can no longer complete), records
+// ST_TIMEOUT and returns false; a waiting block that sees ST_TIMEOUT returns
+// false too, so that all blocks leave the kernel at the same barrier and no
+// block runs a phase that another skipped.
+// Word layout (BAR_WORDS unsigned ints, zero at creation): [0..1] the 64-bit
+// arrival / generation word, [BAR_STATUS] the sticky status word.
 // ---------------------------------------------------------------------------
 // The block range a solve runs on: a whole cooperative grid, or one job's
 // slice of a batched grid.  bid is the block's index within the slice.
@@ -84,14 +90,14 @@ struct VGrid {
   int bid, nblk;
 };
 
-constexpr int BAR_GEN = 1;
 constexpr int BAR_STATUS = 2;
 constexpr int BAR_WORDS = 4;
+constexpr unsigned long long BAR_DEFAULT_LIMIT_NS = 1000000000ull;
 
 struct Barrier {
-  unsigned int* count;
-  unsigned int* gen;
-  int* status;  // sticky device status word
+  unsigned long long* word;  // arrivals | generation << 32
+  int* status;               // sticky device status word
+  unsigned long long limit_ns;  // time limit of every wait
 };
 
 __device__ inline unsigned long long global_ns() {
@@ -100,13 +106,13 @@ __device__ inline unsigned long long global_ns() {
   return t;
 }
 
-__device__ inline unsigned int ld_acquire_u32(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ inline unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ inline void st_release_u32(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ inline void atom_add_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ inline int ld_volatile_i32(const int* p) {
   return *(volatile const int*)p;
@@ -121,47 +127,65 @@ __device__ inline int* bar_ok_flag() {
 // 0 reads and writes it): every use of a barrier releases exactly one
 // generation, and none is released before every block has arrived, so the
 // copy read once by bar_begin stays exact, and the arrival path needs no read
-// of the generation word.
+// of the word.
 __device__ inline unsigned int* bar_gen_local() {
   __shared__ unsigned int gen;
   return &gen;
 }
 __device__ inline void bar_begin(const Barrier& b) {
-  if (threadIdx.x == 0) *bar_gen_local() = ld_acquire_u32(b.gen);
+  if (threadIdx.x == 0) *bar_gen_local() = (unsigned int)(ld_acquire_u64(b.word) >> 32);
   __syncthreads();
 }
 
-// Waits (thread 0) until the generation moves past g; false if the time limit
-// passed (recorded in the status word) or another block recorded a time-out.
-// The status word and the clock are looked at every 16th poll only.
-__device__ inline bool bar_wait(const Barrier& b, unsigned int g, unsigned long long limit_ns) {
+// Waits (thread 0) until generation g is released, or every block has arrived
+// at it; false if the time limit passed (the arrival is withdrawn and the
+// time-out recorded) or another block recorded a time-out.  The status word
+// and the clock are looked at every 16th poll, or at every poll under a limit
+// shorter than a millisecond.
+__device__ inline bool bar_wait(const Barrier& b, unsigned int g, int nblk) {
   const unsigned long long t0 = global_ns();
-  for (unsigned int poll = 1; ld_acquire_u32(b.gen) == g; ++poll) {
-    if ((poll & 15) == 0) {
+  const bool every = b.limit_ns < 1000000ull;
+  for (unsigned int poll = 1;; ++poll) {
+    unsigned long long w = ld_acquire_u64(b.word);
+    if ((unsigned int)(w >> 32) != g) return true;
+    if ((unsigned int)w == (unsigned int)nblk) {  // complete; the release is on its way
+      __threadfence();
+      return true;
+    }
+    if (every || (poll & 15) == 0) {
       if (ld_volatile_i32(b.status) == ST_TIMEOUT) return false;
-      if (global_ns() - t0 > limit_ns) {
+      if (global_ns() - t0 > b.limit_ns) {
+        for (;;) {  // withdraw the arrival while the count is incomplete
+          if ((unsigned int)(w >> 32) != g) return true;
+          if ((unsigned int)w == (unsigned int)nblk) {
+            __threadfence();
+            return true;
+          }
+          const unsigned long long prev = atomicCAS(b.word, w, w - 1ull);
+          if (prev == w) break;
+          w = prev;
+        }
         atomicExch(b.status, (int)ST_TIMEOUT);
         return false;
       }
     }
     __nanosleep(32);
   }
-  return true;
 }
 
-__device__ inline bool grid_sync(const Barrier& b, const VGrid& vg, unsigned long long limit_ns = 1000000000ull) {
+__device__ inline bool grid_sync(const Barrier& b, const VGrid& vg) {
   int* s_ok = bar_ok_flag();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int g = *bar_gen_local();
     __threadfence();  // release side: this block's writes
     bool ok = true;
-    if (atomicAdd(b.count, 1u) == (unsigned int)vg.nblk - 1u) {
+    const unsigned long long old = atomicAdd(b.word, 1ull);
+    if ((unsigned int)old == (unsigned int)vg.nblk - 1u) {
       __threadfence();  // acquire side: every block's arrival
-      atomicExch(b.count, 0u);
-      st_release_u32(b.gen, g + 1u);
+      atom_add_release_u64(b.word, (1ull << 32) - (unsigned long long)(unsigned int)vg.nblk);
     } else {
-      ok = bar_wait(b, g, limit_ns);
+      ok = bar_wait(b, g, vg.nblk);
     }
     *bar_gen_local() = g + 1u;
     *s_ok = ok;
@@ -407,9 +431,8 @@ __device__ inline void grid_total(const double* slots, int stride, double (&out)
 // slot values stored by block_reduce_store before the call).  Same time limit
 // and error behaviour as grid_sync; on false the totals are undefined.
 template <int NV, typename T>
-__device__ inline bool grid_sync_total(const Barrier& b, const VGrid& vg, const T* slots, int stride, T (&out)[NV],
-                                       unsigned long long limit_ns = 1000000000ull) {
-  if (!grid_sync(b, vg, limit_ns)) return false;
+__device__ inline bool grid_sync_total(const Barrier& b, const VGrid& vg, const T* slots, int stride, T (&out)[NV]) {
+  if (!grid_sync(b, vg)) return false;
   grid_total<NV>(slots, stride, out, vg);
   return true;
 }

@@ -34,12 +34,12 @@ constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign;
 // Worst case over all meshes with at most kMaxNodes nodes: 24 nodal FP64 arrays
 // (u, r x2, p x2, s x2, q x2, dinv and 2 x 7 exchange arrays), 10 per-element
 // values (s_e, k_e and 8 eigenvalues; at most as many elements as nodes), the
-// top-face load (at most half the nodes) and its 1D factor tables (nnx + nny
-// <= kMaxNodes / 4 + 2 per factor), the reduction slots, barrier / status
-// words and the counters.
+// new element states (one byte per element), the top-face load (at most half
+// the nodes) and its 1D factor tables (nnx + nny <= kMaxNodes / 4 + 2 per
+// factor), the reduction slots, barrier / status words and the counters.
 constexpr size_t kScratchBytes =
     24 * align_up(kMaxNodes * sizeof(double)) + 2 * align_up(kMaxNodes * sizeof(double)) +
-    align_up(8 * kMaxNodes * sizeof(double)) +
+    align_up(8 * kMaxNodes * sizeof(double)) + align_up(kMaxNodes) +
     align_up(kMaxNodes / 2 * sizeof(double)) + align_up((size_t)MAXRECT * (kMaxNodes / 4 + 2) * sizeof(double)) + align_up((size_t)RS_N * kMaxGrid * sizeof(double)) + align_up((size_t)RS_N * kMaxGrid * sizeof(float)) +
     align_up(BAR_WORDS * sizeof(unsigned int)) + align_up(sizeof(DevStats)) + 4 * kAlign;
 
@@ -193,15 +193,16 @@ extern "C" tl_status tl_box_step_noalloc(const tl_box_step_desc* d, const double
   a.s_e = c.take<double>(ne);
   a.k_e = c.take<double>(ne);
   a.lam = c.take<double>(8 * ne);
+  a.st_new = c.take<uint8_t>(ne);
   a.F = c.take<double>((size_t)(nnx * nny));
   a.G = c.take<double>((size_t)MAXRECT * (nnx + nny));
   a.red = c.take<double>((size_t)RS_N * kMaxGrid);
   a.red32 = c.take<float>((size_t)RS_N * kMaxGrid);
-  unsigned int* words = c.take<unsigned int>(BAR_WORDS);  // barrier counters, generation, status
+  unsigned int* words = c.take<unsigned int>(BAR_WORDS);  // barrier arrivals / generation, status
   a.stats = c.take<DevStats>(1);
   if (c.used > kScratchBytes) return TL_EINVAL;
   a.red_stride = kMaxGrid;
-  a.bar = Barrier{words, words + BAR_GEN, (int*)(words + BAR_STATUS)};
+  a.bar = Barrier{reinterpret_cast<unsigned long long*>(words), (int*)(words + BAR_STATUS), BAR_DEFAULT_LIMIT_NS};
 
   a.T_in = T_in;
   a.T_out = T_out;

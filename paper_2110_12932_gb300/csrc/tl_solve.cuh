@@ -357,6 +357,7 @@ struct SolveArgs {
   double* F;     // top-face load, (nx+1)(ny+1)
   double* G;     // load factor tables, MAXRECT (nnx + nny)
   uint8_t* state;
+  uint8_t* st_new;  // the new element states (one per element, patch order) until the commit
   int st_sx, st_sy, st_ox, st_oy;  // element (ie,je,ke) -> state[(ke st_sy + je + st_oy) st_sx + ie + st_ox]
   DirSpec dir;
   DirValues dv;
@@ -1778,6 +1779,18 @@ __device__ inline double elem_mean(const double* T, const Grid3& g, int ie, int 
   return s * 0.125;
 }
 
+// The same mean of T + u (node by node, the values T + u rounds to), in the
+// same order: equal to elem_mean of the stored sum.
+__device__ inline double elem_mean_sum(const double* T, const double* u, const Grid3& g, int ie, int je, int ke) {
+  const int S = g.nnx * g.nny;
+  const int n0 = ie + g.nnx * je + S * ke;
+  const int off[8] = {0, 1, g.nnx, g.nnx + 1, S, S + 1, S + g.nnx, S + g.nnx + 1};
+  double s = __ldcg(T + n0) + __ldcg(u + n0);
+#pragma unroll
+  for (int c = 1; c < 8; ++c) s += __ldcg(T + n0 + off[c]) + __ldcg(u + n0 + off[c]);
+  return s * 0.125;
+}
+
 // One backward-Euler solve on the block range vg (all of it or one job's slice).
 // PMODE: 0 plain FP64 solves only, 1 refined solves only, 2 either (chosen by
 // a.precision at run time).  Each kernel instantiates only the paths it runs,
@@ -2105,27 +2118,23 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     return;
   }
 
-  // ---- phase 3: update, states, energy -------------------------------------
+  // ---- phase 3: states and energy, then the commit ----------------------------
+  // Everything that outlives the launch (T_out or T_relax, the element states,
+  // the counters) is written after the solve's last grid barrier, which either
+  // releases every block or none: a launch that fails at any barrier leaves
+  // the problem's state as it was.  The new states and the energy terms are
+  // formed from T^k + u, the same values T_out receives.
   tr.mark(TR_UPDATE);
-  if (a.T_relax) {  // an intermediate Picard solve: only the next coefficient temperature
-    for (int n = gtid; n < nn; n += gstride) {
-      const double ts = __ldcg(Tcoef + n);
-      a.T_relax[n] = ts + 0.5 * (__ldcg(a.T_in + n) + __ldcg(a.u + n) - ts);
-    }
-  } else {
-    for (int n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
-  }
+  double te[3] = {0.0, 0.0, 0.0};
   if (a.update_state || a.energy) {
-    if (!grid_sync(a.bar, vg)) return;
     double v[3] = {0.0, 0.0, 0.0};
     for_elems(g, vg, [&](int e, int ie, int je, int ke) {
       if (a.update_state) {
-        const double Tb = elem_mean(a.T_out, g, ie, je, ke);
-        uint8_t* sp = a.state + (ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox;
-        uint8_t st = *sp;
+        const double Tb = elem_mean_sum(a.T_in, a.u, g, ie, je, ke);
+        const uint8_t st = a.state[(ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox];
         uint8_t ns = (st == POWDER) ? POWDER : SOLID;
         if (Tb > a.mat.T_melt) ns = MELTED;
-        *sp = ns;
+        a.st_new[e] = ns;
       }
       if (a.energy) {
         const int n0 = ie + g.nnx * je + S * ke;
@@ -2144,7 +2153,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     if (a.energy) {
       for (int n = gtid; n < S; n += gstride) v[1] += a.dt * __ldcg(a.F + n);
       for_dirichlet(g, a.dir, vg, [&](int n, int i, int j, int k) {
-        // reaction of a Dirichlet row: (S u + K T^{k+1})_n - F_n
+        // reaction of a Dirichlet row: (S u + K T^{k+1})_n - F_n, T^{k+1} = T^k + u
         double R_n = 0.0;
         for (int dz = -1; dz <= 0; ++dz)
           for (int dy = -1; dy <= 0; ++dy)
@@ -2154,12 +2163,13 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
               int e = ie + g.nx * (je + g.ny * ke);
               double se = __ldcg(a.s_e + e), kk = __ldcg(a.k_e + e);
               int la = (i - ie) + 2 * (j - je) + 4 * (k - ke);
-              double am = 0.0, ak = 0.0;  // row la of M^ u and of K^ T
+              double am = 0.0, ak = 0.0;  // row la of M^ u and of K^ T^{k+1}
 #pragma unroll
               for (int b = 0; b < 8; ++b) {
                 int nb = (ie + (b & 1)) + g.nnx * (je + ((b >> 1) & 1)) + S * (ke + (b >> 2));
-                am = fma(a.Mhat[la * 8 + b], __ldcg(a.u + nb), am);
-                ak = fma(a.Khat[la * 8 + b], __ldcg(a.T_out + nb), ak);
+                const double ub = __ldcg(a.u + nb);
+                am = fma(a.Mhat[la * 8 + b], ub, am);
+                ak = fma(a.Khat[la * 8 + b], __ldcg(a.T_in + nb) + ub, ak);
               }
               R_n += se * am + kk * ak;
             }
@@ -2169,21 +2179,31 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     }
     tr.mark(TR_END_DIR);
     block_reduce_store<3>(v, a.red + RS_ES * a.red_stride, a.red_stride, vg);
-    double te[3];
     if (!grid_sync_total<3>(a.bar, vg, a.red + RS_ES * a.red_stride, a.red_stride, te)) return;
-    if (vg.bid == 0) {
-      if (threadIdx.x == 0 && a.energy) {
-        a.stats->e_stored[lvl] += te[0];
-        a.stats->e_laser[lvl] += te[1];
-        a.stats->e_flux[lvl] += te[2];
-        a.stats->e_last[lvl][0] = te[0];
-        a.stats->e_last[lvl][1] = te[1];
-        a.stats->e_last[lvl][2] = te[2];
-      }
-    }
   }
+  // the commit: no barrier follows
+  if (a.T_relax) {  // an intermediate Picard solve: only the next coefficient temperature
+    for (int n = gtid; n < nn; n += gstride) {
+      const double ts = __ldcg(Tcoef + n);
+      a.T_relax[n] = ts + 0.5 * (__ldcg(a.T_in + n) + __ldcg(a.u + n) - ts);
+    }
+  } else {
+    for (int n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
+  }
+  if (a.update_state)
+    for_elems(g, vg, [&](int e, int ie, int je, int ke) {
+      a.state[(ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox] = __ldcg(a.st_new + e);
+    });
   tr.mark(TR_END);
   if (vg.bid == 0 && threadIdx.x == 0) {
+    if (a.energy) {
+      a.stats->e_stored[lvl] += te[0];
+      a.stats->e_laser[lvl] += te[1];
+      a.stats->e_flux[lvl] += te[2];
+      a.stats->e_last[lvl][0] = te[0];
+      a.stats->e_last[lvl][1] = te[1];
+      a.stats->e_last[lvl][2] = te[2];
+    }
     a.stats->iters[lvl] += it;
     a.stats->outer[lvl] += outer;
     a.stats->solves[lvl] += 1;
@@ -2205,7 +2225,9 @@ static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_kernel(const Solv
 // to back (job-local grid barrier in between), each with its own barrier
 // words, reduction slots and buffers, so jobs meet only at the launch's end.
 // The arguments of job j's s-th solve are jobs[j * per_job + s]; each is
-// copied to shared memory once per block.
+// copied to shared memory once per block.  At the end the job's first block
+// writes the job's status word into st_out[j] (nonzero: a solve failed and
+// the job's later solves were skipped).
 constexpr int BATCH_MAX = 512;
 struct BatchTable {
   int njobs, per_job;
@@ -2215,7 +2237,8 @@ struct BatchTable {
 
 template <int PMODE>
 static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_batch_kernel(const BatchTable* __restrict__ tab,
-                                                                  const SolveArgs* __restrict__ jobs) {
+                                                                  const SolveArgs* __restrict__ jobs,
+                                                                  int* __restrict__ st_out) {
   __shared__ SolveArgs s_args;
   __shared__ int s_job;
   if (threadIdx.x == 0) {
@@ -2241,10 +2264,11 @@ static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_batch_kernel(cons
     __syncthreads();
     solve_body<PMODE>(s_args, vg);
     if (sv + 1 < ns) {
-      if (!grid_sync(s_args.bar, vg)) return;  // the next solve reads this one's results
-      if (ld_volatile_i32(s_args.bar.status) != 0) return;
+      if (!grid_sync(s_args.bar, vg)) break;  // the next solve reads this one's results
+      if (ld_volatile_i32(s_args.bar.status) != 0) break;
     }
   }
+  if (vg.bid == 0 && threadIdx.x == 0) st_out[j] = ld_volatile_i32(s_args.bar.status);
 }
 
 // ---------------------------------------------------------------------------

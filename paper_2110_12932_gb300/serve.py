@@ -8,6 +8,9 @@ together with the native batched kernel (tl_batch_round: every job performs
 its next solves on its own slice of the grid).  Finished jobs leave the batch,
 free their memory and make room for waiting ones.
 
+A job whose solve fails (a CG cap, a barrier time-out) leaves the batch after
+the round in which it failed and is reported with its status.
+
 Latency per job = completion - arrival (queueing included); latency per coarse
 step = the wall time of a round divided by the macro steps a job completed in
 it, one sample per completed macro step.  The paper itself is serial; it notes
@@ -123,6 +126,7 @@ class Server:
             "coarse_step_latency_ms": {"p50": None if not step_lat else 1e3 * pct(step_lat, 50),
                                        "p99": None if not step_lat else 1e3 * pct(step_lat, 99)},
             "peak_admitted_bytes": peak_mem, "all_ok": all(d["status"] == 0 for d in done),
+            "failed": sum(d["status"] != 0 for d in done),
             "done": done,
         }
 

@@ -49,6 +49,8 @@ class tl_config(C.Structure):
         ("coupling_sweeps", C.c_int), ("coupling_tol", C.c_double), ("precond", C.c_int),
         ("latent", C.c_double), ("T_solidus", C.c_double), ("T_liquidus", C.c_double),
         ("pc_sharpness", C.c_double), ("picard_iters", C.c_int),
+        ("h_conv", C.c_double), ("emissivity", C.c_double), ("T_amb", C.c_double),
+        ("barrier_timeout", C.c_double),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
@@ -149,7 +151,7 @@ def load(path=LIB_PATH):
     lib.tl_batch_round.restype = C.c_int
     lib.tl_batch_poll.argtypes = [P, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
     lib.tl_batch_poll.restype = C.c_int
-    lib.tl_batch_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+    lib.tl_batch_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
     lib.tl_batch_info.restype = C.c_int
     lib.tl_batch_destroy.argtypes = [P]
     lib.tl_batch_destroy.restype = None
@@ -170,8 +172,6 @@ def tl_status_string(status):
 def make_config(cfg, stream=None):
     """tl_config from a workload dict (keys = tl_config fields + tracks).
     Returns (config, keep-alive objects)."""
-    if cfg.get("h_conv", 0.0) or cfg.get("emissivity", 0.0):
-        raise NotImplementedError("top-surface convection / radiation is not in the CUDA path")
     c = tl_config()
     for name, _ in tl_config._fields_:
         if name in ("path", "ntracks", "stream", "alloc", "free", "alloc_ctx"):
@@ -399,9 +399,9 @@ class Batch:
         return [self.jobs.pop(ids[i]) for i in range(n.value)]
 
     def info(self):
-        a, l, g = C.c_int(), C.c_longlong(), C.c_int()
-        _check(load().tl_batch_info(self.h, C.byref(a), C.byref(l), C.byref(g)), "tl_batch_info")
-        return {"active": a.value, "launches": l.value, "graph_mode": g.value}
+        a, l = C.c_int(), C.c_longlong()
+        _check(load().tl_batch_info(self.h, C.byref(a), C.byref(l)), "tl_batch_info")
+        return {"active": a.value, "launches": l.value}
 
     def run(self):
         """Rounds until every job finished; returns the problems in finishing order."""

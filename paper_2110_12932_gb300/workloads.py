@@ -39,6 +39,8 @@ MATERIAL = dict(
 )
 PROCESS = dict(P=195.0, eta=0.4, radius=50e-6)
 THERMAL = dict(T0=293.0, T_bottom=293.0)
+# top-surface losses (Section 3.1): off in every workload unless overridden
+SURFACE = dict(h_conv=0.0, emissivity=0.0, T_amb=293.0)
 SOLVER = dict(precision=0, tol=1e-12, tol_inner=1e-5, max_iter=2000, inner_tiles=0,
               coupling_sweeps=1, coupling_tol=1e-10, precond=0, coarse_source=0, bc_weight_literal=0, energy=1,
               picard_iters=1)
@@ -66,6 +68,7 @@ def _base(**kw):
     cfg.update(MATERIAL)
     cfg.update(PROCESS)
     cfg.update(THERMAL)
+    cfg.update(SURFACE)
     cfg.update(SOLVER)
     cfg.update(kw)
     return cfg

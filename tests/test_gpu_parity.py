@@ -119,6 +119,40 @@ def test_literal_bc_weight_and_laser_off_tail():
     run_both(cfg, 24, check_every=8)
 
 
+def test_alternating_tracks_whole_scan():
+    """Three alternating 1.03 mm tracks (hatch 100 um < the 500 um patch) on
+    the 2 x 1 x 0.5 mm plate with the box source on the coarse level, run to
+    past the end of the scan and compared after every macro step: the coarse
+    source split between two tracks in the macro steps that hold a turn
+    (the 26th and the 52nd; the scan ends in the 78th), the patch turning
+    round, and the patch returning over material the previous track
+    consolidated (the plate-wide fine state map)."""
+    cfg = workloads.workload("single_track_tiny", coarse_source=0,
+                             tracks=workloads.raster_tracks(0.5e-3, 1.53e-3, 0.5e-3, 3, 100e-6, 0.8))
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg)
+    revisited = 0
+    first_track = None
+    for n in range(82):
+        prob.macro_steps(1)
+        ref.run(1)
+        compare(prob, ref, f"macro {n + 1}")
+        if n + 1 == 25:  # the first track ends during the 26th step
+            first_track = ref.state_map == TL.MELTED
+        if n + 1 >= 32:  # back over the first track's melt, 100 um aside
+            o, r = ref.origin, ref.r
+            win = ref.fine_state()
+            revisited += int(np.count_nonzero(first_track[:, o[1] * r:o[1] * r + win.shape[1],
+                                                          o[0] * r:o[0] * r + win.shape[2]]))
+    assert revisited > 0
+    st = prob.stats()
+    assert st["patch_moves"] >= 10
+    s, l, f = (st[f"energy_coarse_{k}"] for k in ("stored", "laser", "flux"))
+    assert abs(s - l - f) <= 1e-9 * max(abs(s), abs(l))
+    assert abs(l - ref.energy["coarse_laser"]) <= 1e-9 * abs(l)
+    prob.close()
+
+
 def test_no_tracks_stays_at_initial_temperature():
     cfg = workloads.workload("single_track_tiny", tracks=[])
     prob = tl.Problem(cfg)

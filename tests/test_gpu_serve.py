@@ -59,3 +59,40 @@ def test_results_same_alone_and_in_the_mix():
 def test_fifo_reference_latencies():
     lat = serve.fifo_one_at_a_time([(0.0, None), (0.5, None), (0.6, None)], [1.0, 1.0, 1.0])
     assert lat == [1.0, 1.5, 2.4]
+
+
+def test_failing_job_is_evicted_and_the_others_are_undisturbed():
+    """One job cannot converge (max_iter = 1): its first failed solve ends its
+    work in that round, the next poll reports it with TL_ENOCONV long before
+    its scan would end, and every other job's result equals its run alone."""
+    jobs = _jobs()[:3]
+    bad = dict(jobs[0], max_iter=1, macro_steps=40, name="bad")
+    alone = []
+    for cfg in jobs:
+        p = tl.Problem(cfg)
+        p.macro_steps(cfg["macro_steps"])
+        alone.append(p.temperature(tl.TL_FINE)[0])
+        p.close()
+    arrivals = [(0.0, jobs[0]), (0.0, bad), (0.0, jobs[1]), (0.002, jobs[2])]
+    got, steps = {}, {}
+
+    def on_done(k, p, rec):
+        got[k] = p.temperature(tl.TL_FINE)[0]
+        steps[k] = rec["steps"]
+
+    srv = serve.Server(mem_cap_bytes=1e12, max_jobs=8, launches_per_round=4)
+    rep = srv.run(arrivals, on_done=on_done)
+    srv.close()
+    assert rep["jobs"] == 4 and not rep["all_ok"]
+    status = {d["key"]: d["status"] for d in rep["done"]}
+    assert status[1] == tl.TL_ENOCONV
+    assert all(status[k] == tl.TL_OK for k in (0, 2, 3))
+    assert rep["failed"] == 1
+    assert steps[1] < bad["macro_steps"]
+    order = [d["key"] for d in rep["done"]]
+    assert order.index(1) < order.index(0), "the failed job leaves before the healthy ones finish"
+    for k, idx in ((0, 0), (2, 1), (3, 2)):
+        cfg = jobs[idx]
+        tol = 1e-6 if cfg.get("precision", 0) == tl.TL_FP32_REFINED else 1e-9
+        rel = np.linalg.norm(got[k] - alone[idx]) / np.linalg.norm(alone[idx])
+        assert rel <= tol, (k, rel)
