@@ -1,17 +1,27 @@
 """Benchmark: fine DOF-substeps/s of the two-level LPBF heat solve on GB300.
 
-One step = one macro step of Algorithm 1 (predictor, m fine micro steps,
-restriction, correction) of the 10 x 5 x 2 mm multi-track workload (80x40x16
-coarse hexes, 65x65x33-node fine patch, m = 8); the default K = 500 steps is
-the first quarter of the 2000-step, 10-track scan.  Metric: fine DOF-substeps/s = fine patch nodes x micro steps
-solved / time.
+Default workload: the 20 x 10 x 4 mm plate of the precision form (160 x 80 x 32
+coarse hexahedra, 129 x 129 x 65-node fine patch, m = 8, alternating 18 mm
+tracks).  One step = one macro step of Algorithm 1 (predictor, m fine micro
+steps, restriction, correction).  Metric: fine DOF-substeps/s = fine patch
+nodes x micro steps solved / device time.
+
+The JSON line's headline is the precision form (FP32 inner CG, FP64 defect
+correction to 1e-10); beside it: the plain FP64 path on the same workload,
+both forms' error against the FP64 oracle's stored fields and against each
+other, the roofline of the dominant kernel (the refined fine micro step), a
+roofline probe on a 256 x 256 x 128-element patch whose working set exceeds
+L2, the batched form on 64 seeded jobs, and the served form under a Poisson
+stream at the nominal 20 jobs/s (for --duration seconds).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--mode full|plain|batch|serve|roofline]
 
-N > 1 (torchrun, one rank per GPU): N independent replicas of the workload,
-no collective on the data path (the patch solve does not shard); value = the
-work of all ranks / the slowest rank's time.  --impl reference times the FP64
-CPU oracle on a bounded sample of the same workload (rank 0 only).
+N > 1 (torchrun, one rank per GPU): N independent replicas of the plate, and
+batch / serve jobs dealt round-robin to the ranks; no collective on the data
+path; value = the work of all ranks / the slowest rank's time.  --impl
+reference times the FP64 CPU oracle on a bounded sample of the same workload
+(rank 0 only).
 """
 from __future__ import annotations
 
@@ -29,30 +39,49 @@ sys.path.insert(0, ROOT)
 
 from paper_2110_12932_gb300 import ranks, workloads  # noqa: E402
 
-WORKLOAD = "multitrack_10mm"
+WORKLOAD = "multitrack_20mm"
 METRIC = "fine DOF-substeps/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "multitrack_20mm_oracle.npz")
 FLOPS_APPLY_PER_ELEM = 65   # Hadamard-factored matrix-free apply, FP64 flops per element
 FLOPS_VEC_PER_NODE = 14     # PCG vector update, fused dots, p = z + beta p
-# dram__bytes_read.sum + dram__bytes_write.sum of one FP64 fine micro-step launch of
-# this workload, from the ncu capture summarised in
-# profiles/solve_kernel_fp64_multitrack_10mm.md (the patch is L2-resident)
-FINE_LAUNCH_DRAM_BYTES = 3.026432e6 + 1.040640e6
+HBM_NOMINAL_GBS = 8000.0
+HBM_FALLBACK_GBS = 6800.0   # the profiling recipe's fallback copy bandwidth
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+# Algorithmic bytes per fine node (elements ~ nodes; every array counted once
+# per pass that needs it; cache re-reads of neighbours and the exchange
+# partials on tile faces are not counted):
+#  FP32 inner CG iteration (tensor-preconditioned, three phases): update
+#   reads r, q, x, u, p, s, sq and writes p, s, r, x, v (48); preconditioner
+#   reads v, sq, r and writes u (16); apply reads u, s_e, k_e and writes q (16);
+#  FP64 CG iteration: update 10 FP64 + 2 FP32 arrays (88), preconditioner
+#   (24), apply with eight FP64 eigenvalues per element (80);
+#  per solve outside the CG: coefficients (read T, state; write s_e, k_e, the
+#   eight eigenvalues, u; the refined path also the FP32 s_e, k_e), diagonal
+#   and right-hand side (two applies), initial residual, states / energy and
+#   the commit T^{k+1} = T^k + u;
+#  per outer sweep of the refined path: FP32 copy of the scaled residual, the
+#   FP32 preconditioner's set-up, the FP64 apply of the correction and the
+#   FP64 update of u and r.
+B_ITER = {"fp32": 80, "fp64": 192}
+B_SOLVE = {"fp32": 305, "fp64": 293}
+B_OUTER = 160
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "roofline"],
-                    help="plain: the 10 mm multi-track plate (FP64 headline + precision form); "
-                         "batch: 64 uneven jobs in the batched FP32-refined form")
+    ap.add_argument("--mode", default="full", choices=["full", "plain", "batch", "serve", "roofline"],
+                    help="full: the plate in both precisions plus the roofline probe, the batch and the serve "
+                         "sub-objects; plain: the plate only; batch / serve / roofline: one of them alone")
     ap.add_argument("--jobs", type=int, default=64)
-    ap.add_argument("--rate", type=float, default=2.0, help="serve: arrivals per second")
-    ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
+    ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
     ap.add_argument("--mem-cap-gb", type=float, default=120.0)
     ap.add_argument("--launches-per-round", type=int, default=10)
     ap.add_argument("--coupling-sweeps", type=int, default=1,
@@ -61,9 +90,21 @@ def parse():
                     help="plain: latent heat of fusion [J/kg] (0 = none; Ti64-like 2.86e5)")
     ap.add_argument("--picard", type=int, default=1,
                     help="plain: Picard iterations per backward-Euler step (1 = coefficients lagged)")
+    ap.add_argument("--h-conv", type=float, default=0.0, help="plain: top-surface convection [W/(m^2 K)]")
+    ap.add_argument("--emissivity", type=float, default=0.0, help="plain: top-surface emissivity (fine level)")
     ap.add_argument("--inner-tiles", type=int, default=0, choices=[0, 1, 2],
                     help="batch / serve: tiling of the FP32 inner CG (0 by mesh size, 1 element tiles, 2 wide tiles)")
     return ap.parse_args()
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth of
+    MEASURED_PEAKS.json when present, else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 class ClockSampler:
@@ -130,6 +171,11 @@ sum_over_ranks = ranks.sum_over_ranks
 
 def fine_nodes(cfg):
     return workloads.fine_nodes(cfg)
+
+
+def fine_elems(cfg):
+    r = cfg["r"]
+    return (cfg["pNXc"] * r) * (cfg["pNYc"] * r) * (cfg["pNZc"] * r)
 
 
 def oracle_solves(o):
@@ -215,11 +261,17 @@ def run_reference(args):
     return 0
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one fine micro-step launch of
+# the headline form per workload, from the ncu captures summarised under
+# profiles/ (None: not captured for the kernel as it stands)
+FINE_LAUNCH_DRAM_BYTES = {}
+
+
 def l2_flush(buf):
     buf.fill_(1.0)
 
 
-def timed_run(tl, torch, cfg, K, sp, stream, flush, sample_every=50):
+def timed_run(tl, torch, cfg, K, sp, stream, flush, sample_every=5):
     """K macro steps of a fresh problem, each bracketed by CUDA events on the
     library's stream, L2 flushed between steps outside the events; every
     `sample_every`-th macro step also times each fine launch separately."""
@@ -260,149 +312,169 @@ def timed_run(tl, torch, cfg, K, sp, stream, flush, sample_every=50):
 
 
 def fine_flops(cfg, iters_per_launch):
-    r = cfg["r"]
-    ne = (cfg["pNXc"] * r) * (cfg["pNYc"] * r) * (cfg["pNZc"] * r)
-    nfn = fine_nodes(cfg)
+    ne, nfn = fine_elems(cfg), fine_nodes(cfg)
     return iters_per_launch * (FLOPS_APPLY_PER_ELEM * ne + FLOPS_VEC_PER_NODE * nfn) + 2 * FLOPS_APPLY_PER_ELEM * ne
 
 
-def run_ours(args):
+def fine_bytes(cfg, prec, iters, outer):
+    """Algorithmic bytes of one fine solve (see B_ITER / B_SOLVE / B_OUTER)."""
+    n = fine_nodes(cfg)
+    if prec == "fp32":
+        return n * (B_SOLVE["fp32"] + B_OUTER * outer + B_ITER["fp32"] * iters)
+    return n * (B_SOLVE["fp64"] + B_ITER["fp64"] * iters)
+
+
+def load_golden():
+    """The oracle's stored fields of the 20 mm plate (tests/golden), or None."""
     import numpy as np
-    import torch
+    if not os.path.exists(GOLDEN):
+        return None
+    z = np.load(GOLDEN)
+    T0 = float(z["T0"])
+    out = {}
+    for n in (int(v) for v in z["steps"]):
+        snap = {"origin": tuple(int(v) for v in z[f"s{n}_origin"])}
+        for lvl in ("fine", "coarse"):
+            T = np.full(int(z[f"s{n}_{lvl}_n"]), T0)
+            T[z[f"s{n}_{lvl}_idx"]] = z[f"s{n}_{lvl}_val"]
+            snap[lvl] = T
+        snap["fine_state"] = z[f"s{n}_fine_state"]
+        out[n] = snap
+    return out
 
-    from paper_2110_12932_gb300 import build as tlbuild
-    from paper_2110_12932_gb300 import tl
 
-    rank, ws, local = dist_setup(args.gpus)
-    tlbuild.build()
-    tl.load()
-    form = dict(coupling_sweeps=args.coupling_sweeps, latent=args.latent, picard_iters=args.picard)
-    cfg = workloads.workload(args.workload, precision=0, tol=1e-12, **form)
-    cfg_ref = workloads.workload(args.workload, precision=1, tol=1e-10, tol_inner=1e-5, **form)
-    stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
-    nfn = fine_nodes(cfg)
-    m = cfg["m"]
-    r = cfg["r"]
-    ne = (cfg["pNXc"] * r) * (cfg["pNYc"] * r) * (cfg["pNZc"] * r)
+def versus_oracle(tl, cfg, sp):
+    """Relative L2 of both levels and melt-mask agreement against the oracle's
+    stored fields after the last stored macro step (20 mm plate only)."""
+    import numpy as np
+    gold = load_golden()
+    if gold is None or cfg["name"] != "multitrack_20mm":
+        return None
+    n = max(gold)
+    g = gold[n]
+    p = tl.Problem(cfg, stream=sp)
+    p.macro_steps(n)
+    Tf, org = p.temperature(tl.TL_FINE)
+    Tc, _ = p.temperature(tl.TL_COARSE)
+    sf = p.state(tl.TL_FINE)
+    p.close()
+    return {"macro_steps": n, "origin_equal": tuple(org) == g["origin"],
+            "fine": float(np.linalg.norm(Tf - g["fine"]) / np.linalg.norm(g["fine"])),
+            "coarse": float(np.linalg.norm(Tc - g["coarse"]) / np.linalg.norm(g["coarse"])),
+            "melt_mask_agreement": float(np.mean((sf == tl.MELTED) == (g["fine_state"] == tl.MELTED))),
+            "states_equal": bool(np.array_equal(sf, g["fine_state"]))}
+
+
+def measure_plate(args, tl, torch, sp, stream, ws):
+    """Both precisions on the plate: device-timed K macro steps each, fine
+    launches sampled for the roofline, the error against each other and
+    against the stored oracle fields."""
+    import numpy as np
+    form = dict(coupling_sweeps=args.coupling_sweeps, latent=args.latent, picard_iters=args.picard,
+                h_conv=args.h_conv, emissivity=args.emissivity)
+    cfg64 = workloads.workload(args.workload, precision=0, tol=1e-12, **form)
+    cfg32 = workloads.workload(args.workload, precision=1, tol=1e-10, tol_inner=1e-5, **form)
+    nfn, m, K = fine_nodes(cfg64), cfg64["m"], args.steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    K = args.steps
-
-    # warm-up on throw-away problems
-    for c in (cfg, cfg_ref):
+    for c in (cfg64, cfg32):  # warm-up on throw-away problems
         wp = tl.Problem(c, stream=sp)
         for _ in range(args.warmup):
             wp.macro_steps(1)
         wp.close()
-
-    clocks = ClockSampler(local)
-    barrier(ws)
-    torch.cuda.synchronize()
-    clocks.start()
-    t_wall = time.perf_counter()
-    dev_ms, fine_ms, st, Tf64, Tc64, sf64 = timed_run(tl, torch, cfg, K, sp, stream, flush)
-    wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    barrier(ws)
-    dev_ms = max_over_ranks(dev_ms, ws)
-    work = sum_over_ranks(K * m * nfn, ws)
-    value = work / (dev_ms / 1e3)
-    fine_iters = st["cg_iters_fine"] / max(1, st["solves_fine"])
-    launch_s = statistics.mean(fine_ms) / 1e3
-    picard = max(1, args.picard)  # solves per fine micro step; fine_ms times the whole micro step
-    achieved = picard * fine_flops(cfg, fine_iters) / launch_s / 1e12
-    peak = FP64_PEAK_TFLOPS   # FP64 FMA: 2 DFMA/clk/SM = 4 flop/clk/SM at 2.07 GHz
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": FINE_LAUNCH_DRAM_BYTES,
-                "kernel": "tl::solve_kernel (FP64 fine micro step)",
-                "launch_ms": statistics.mean(fine_ms), "cg_iters_per_launch": fine_iters,
-                "flops_per_launch": picard * fine_flops(cfg, fine_iters),
-                "peak_note": "FP64 pipe, derived: 152 SMs x 4 flop/clk x 2.07 GHz; a DFMA loop measured 1.20 TFLOP/s. "
-                             "Counts the FP64 flops of the apply (65 per element) and of the vector work (14 per node) "
-                             "per CG iteration; the FP32 preconditioner filter is not counted"}
-
-    # ---- the precision form on the same workload (FP32 inner CG, FP64 defect correction)
-    barrier(ws)
-    dev_ms_r, fine_ms_r, st_r, Tf32, Tc32, sf32 = timed_run(tl, torch, cfg_ref, K, sp, stream, flush)
-    dev_ms_r = max_over_ranks(dev_ms_r, ws)
-    value_r = work / (dev_ms_r / 1e3)
-    refined = {
-        "value": value_r, "unit": "DOF-substeps/s", "ms_per_step": dev_ms_r / K, "speedup_vs_fp64": value_r / value,
-        "tol": cfg_ref["tol"], "tol_inner": cfg_ref["tol_inner"],
-        "rel_l2_vs_fp64": {"fine": float(np.linalg.norm(Tf32 - Tf64) / np.linalg.norm(Tf64)),
-                           "coarse": float(np.linalg.norm(Tc32 - Tc64) / np.linalg.norm(Tc64))},
-        "melt_mask_agreement": float(np.mean((sf32 == tl.MELTED) == (sf64 == tl.MELTED))),
-        "fine_launch_ms": statistics.mean(fine_ms_r),
-        "inner_iters_per_solve": st_r["cg_iters_fine"] / max(1, st_r["solves_fine"]),
-        "outer_iters_per_solve": st_r["outer_iters_fine"] / max(1, st_r["solves_fine"]),
-        "gpu_launches": int(sum_over_ranks(st_r["launches"], ws)),
+    out = {}
+    for prec, cfg in (("fp64", cfg64), ("fp32", cfg32)):
+        barrier(ws)
+        dev_ms, fine_ms, st, Tf, Tc, sf = timed_run(tl, torch, cfg, K, sp, stream, flush)
+        dev_ms = max_over_ranks(dev_ms, ws)
+        work = sum_over_ranks(K * m * nfn, ws)
+        solves = max(1, st["solves_fine"])
+        out[prec] = dict(value=work / (dev_ms / 1e3), ms_per_step=dev_ms / K, fine_ms=fine_ms, stats=st,
+                         Tf=Tf, Tc=Tc, sf=sf, iters=st["cg_iters_fine"] / solves,
+                         outer=st["outer_iters_fine"] / solves, work=work, dev_ms=dev_ms)
+    a, b = out["fp64"], out["fp32"]
+    accuracy = {
+        "vs_fp64_gpu_path": {"macro_steps": K,
+                             "fine": float(np.linalg.norm(b["Tf"] - a["Tf"]) / np.linalg.norm(a["Tf"])),
+                             "coarse": float(np.linalg.norm(b["Tc"] - a["Tc"]) / np.linalg.norm(a["Tc"])),
+                             "melt_mask_agreement": float(np.mean((b["sf"] == tl.MELTED) == (a["sf"] == tl.MELTED)))},
+        "fp32_refined_vs_oracle": versus_oracle(tl, cfg32, sp),
+        "fp64_vs_oracle": versus_oracle(tl, cfg64, sp),
     }
-
-    # ---- end to end through the public API: create, K steps, host read-back each step
-    torch.cuda.synchronize()
-    barrier(ws)
-    t0 = time.perf_counter()
-    p2 = tl.Problem(cfg, stream=sp)
-    host = None
-    for k in range(K):
-        p2.macro_steps(1)
-        host, _ = p2.temperature(tl.TL_FINE)
-    p2.close()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e = {"value": work / e2e_s, "unit": "DOF-substeps/s", "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": int(host.nbytes), "wall_s": e2e_s,
-           "note": "tl_create_problem + per step tl_macro_steps(1) + tl_get_temperature(fine) into a host buffer; "
-                   "step inputs (laser positions, weights) travel as launch parameters"}
-
-    launches = int(sum_over_ranks(st["launches"], ws))
-    if rank == 0:
-        cpu = None
-        if not args.no_cpu_baseline and ws == 1:
-            cpu = cpu_baseline(cfg)
-        line = {"metric": METRIC, "value": value, "unit": "DOF-substeps/s", "n_gpus": ws, "steps": K,
-                "warmup": args.warmup, "ms_per_step": dev_ms / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": cfg["name"], "fine_nodes": nfn, "fine_elements": ne,
-                           "coarse_nodes": (cfg["NXc"] + 1) * (cfg["NYc"] + 1) * (cfg["NZc"] + 1),
-                           "m": m, "r": r, "tol": cfg["tol"], "precision": "fp64",
-                           "coupling_sweeps": args.coupling_sweeps, "latent": args.latent,
-                           "picard_iters": args.picard,
-                           "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                           "l2": "flushed (256 MB write) between timed macro steps, outside the events"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "wall_s": wall,
-                "coupling_resolves_per_step": st.get("coupling_resolves", 0) / max(1, K),
-                "cg_iters": {"fine_per_solve": fine_iters,
-                             "coarse_per_solve": st["cg_iters_coarse"] / max(1, st["solves_coarse"])},
-                "fp32_refined": refined}
-        print(json.dumps(line), flush=True)
-    ranks.finish(ws)
-    return 0
+    return cfg64, cfg32, out, accuracy
 
 
-def run_batch(args):
+def measure_probe(tl, torch):
+    """A 256 x 256 x 128-element fine patch (8.5M nodes, working set above L2;
+    32 x 32 x 16 coarse elements refined 8x on a 40 x 40 x 20 plate): one micro
+    step in each precision, per-phase times of the CG iterations from the
+    device phase tracer (block 0's view: a phase ends when the grid barrier
+    after it is passed)."""
+    peak, src = hbm_peak()
+    base = workloads.workload("multitrack_10mm", Lx=5e-3, Ly=5e-3, Lz=2.5e-3, NXc=40, NYc=40, NZc=20,
+                              pNXc=32, pNYc=32, pNZc=16, r=8, m=8,
+                              tracks=[(1e-3, 2.5e-3, 4e-3, 2.5e-3, 0.8)])
+    nn = fine_nodes(base)
+    ne = fine_elems(base)
+    out = {}
+    names = {v: k for k, v in tl.TRACE_MARKS.items()}
+    for prec in ("fp32", "fp64"):
+        cfg = dict(base, precision=1 if prec == "fp32" else 0, tol=1e-10 if prec == "fp32" else 1e-12)
+        p = tl.Problem(cfg)
+        p.macro_steps(1)           # warm-up macro step
+        p.predict()
+        p.fine_substeps(1)
+        torch.cuda.synchronize()
+        ev = [e for e in p.trace(tl.TL_FINE) if e[0] not in (names["rr_value"], names["breakdown_value"])]
+        p.close()
+        launch = (ev[-1][1] - ev[0][1]) / 1e9
+        ends = [b for (mk, b) in ev if mk == names["cg_pass"]]
+        t = statistics.median([(y - x) / 1e9 for x, y in zip(ends, ends[1:])]) if len(ends) > 1 else float("nan")
+        seg = {}
+        for (m0, a), (m1, b) in zip(ev, ev[1:]):
+            seg.setdefault((m0, m1), []).append((b - a) / 1e9)
+
+        def med(a, b):
+            return statistics.median(seg[(names[a], names[b])])
+
+        tu = med("cg_pass", "cg_u_start") + med("cg_u_start", "cg_u_end") + med("cg_u_end", "cg_update")
+        tp = med("cg_update", "cg_precond")
+        ta = med("cg_precond", "cg_apply") + med("cg_apply", "cg_pass")
+        per = {"fp32": (48, 16, 16), "fp64": (88, 24, 80)}[prec]
+        bu, bp, ba = (x * nn for x in per)
+
+        def phase(us, byt):
+            g = byt / us / 1e9
+            return {"us": 1e6 * us, "bytes": byt, "GBps": g, "frac_of_hbm": g / peak,
+                    "frac_of_8TBps": g / HBM_NOMINAL_GBS}
+
+        o = {"launch_ms": 1e3 * launch, "cg_iterations": len(ends), "iteration_us": 1e6 * t,
+             "update_phase": phase(tu, bu), "precond_phase": phase(tp, bp), "apply_phase": phase(ta, ba),
+             "bytes_per_iteration": bu + bp + ba, "GBps": (bu + bp + ba) / t / 1e9,
+             "frac_of_hbm": (bu + bp + ba) / t / 1e9 / peak,
+             "frac_of_8TBps": (bu + bp + ba) / t / 1e9 / HBM_NOMINAL_GBS}
+        if prec == "fp64":
+            fa = FLOPS_APPLY_PER_ELEM * ne + 2 * nn
+            o["apply_phase"].update({"fp64_flops": fa, "TFLOPs": fa / ta / 1e12,
+                                     "frac_of_fp64_peak": fa / ta / 1e12 / FP64_PEAK_TFLOPS})
+        out[prec] = o
+    return {"fine_nodes": nn, "fine_elements": ne, "hbm_peak_GBps": peak, "hbm_peak_source": src,
+            "scheme": "tensor-preconditioned CG, three phases per iteration (update, preconditioner, apply); "
+                      "FP32 apply on wide tiles, FP64 apply on element tiles",
+            "bytes_per_node": {"fp32": {"update": 48, "precond": 16, "apply": 16},
+                               "fp64": {"update": 88, "precond": 24, "apply": 80}},
+            "results": out}
+
+
+def measure_batch(args, tl, torch, sp, stream, rank, ws):
     """64 independent seeded jobs (2-8 mm plates, 32^3 ... 96x96x48 fine
     patches, r = m in {4, 8}) advanced together in the batched FP32-refined
     form until every job finished its scan; compared with the same jobs run
     one at a time on the plain FP64 path (a timed sample of each job's first
     macro steps, extrapolated to its full scan)."""
-    import torch
-
-    from paper_2110_12932_gb300 import build as tlbuild
-    from paper_2110_12932_gb300 import tl
-
-    rank, ws, local = dist_setup(args.gpus)
-    tlbuild.build()
-    tl.load()
-    stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
-    # jobs are dealt round-robin to the ranks (no exchange between them)
     jobs = ranks.deal(workloads.batch_jobs(args.jobs), rank, ws)
     for j in jobs:
         j.update(precision=1, tol=1e-10, tol_inner=1e-5, inner_tiles=args.inner_tiles)
     work = sum(fine_nodes(j) * j["m"] * j["macro_steps"] for j in jobs)
-
-    # warm-up: one short batch
     wb = tl.Batch(launches_per_round=args.launches_per_round, max_jobs=len(jobs), stream=sp)
     wps = [tl.Problem(j, stream=sp) for j in jobs[:8]]
     for p in wps:
@@ -411,35 +483,21 @@ def run_batch(args):
     wb.close()
     for p in wps:
         p.close()
-
     probs = [tl.Problem(j, stream=sp) for j in jobs]
     batch = tl.Batch(launches_per_round=args.launches_per_round, max_jobs=len(jobs), stream=sp)
     for p, j in zip(probs, jobs):
         batch.add(p, j["macro_steps"])
-    clocks = ClockSampler(local)
     barrier(ws)
     torch.cuda.synchronize()
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     e0.record(stream)
-    rounds = []
     while batch.jobs:
-        ra, rb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ra.record(stream)
-        act = batch.round()
-        rb.record(stream)
-        rounds.append((act, ra, rb))
+        batch.round()
         batch.poll()
     e1.record(stream)
     torch.cuda.synchronize()
-    by_active = {}
-    for act, ra, rb in rounds:
-        k = "1" if act <= 1 else ("2-8" if act <= 8 else ("9-32" if act <= 32 else "33+"))
-        c, ms = by_active.get(k, (0, 0.0))
-        by_active[k] = (c + 1, ms + ra.elapsed_time(rb))
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
     dev_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws)
     info = batch.info()
     stats = [p.stats() for p in probs]
@@ -448,49 +506,34 @@ def run_batch(args):
     for p in probs:
         p.close()
     total_work = sum_over_ranks(work, ws)
-    launches = int(sum_over_ranks(info["launches"], ws))
-    # plain FP64 one at a time: time each job's first macro steps alone
     sample_steps = 3
-    alone_s = 0.0
-    alone_work = 0
+    alone_s, alone_work = 0.0, 0
     for j in jobs:
         c = dict(j, precision=0, tol=1e-12)
         p = tl.Problem(c, stream=sp)
-        p.macro_steps(1)  # warm
+        p.macro_steps(1)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(sample_steps):
-            p.predict()
-            p.fine_substeps(c["m"])
-            p.restrict()
-            p.correct()
+        p.macro_steps(sample_steps)
         b.record(stream)
         torch.cuda.synchronize()
         alone_s += a.elapsed_time(b) / 1e3 * (j["macro_steps"] / sample_steps)
         alone_work += fine_nodes(j) * j["m"] * j["macro_steps"]
         p.close()
-    if rank == 0:
-        line = {"metric": METRIC, "value": total_work / dev_s, "unit": "DOF-substeps/s", "n_gpus": ws,
-                "steps": info["launches"], "warmup": 1, "ms_per_step": 1e3 * dev_s / max(1, info["launches"]),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-                "data": "synthetic",
-                "config": {"workload": f"batch_jobs({args.jobs}, seed 20211025)", "jobs": len(jobs),
-                           "fine_dof_substeps": total_work, "precision": "fp32_refined", "tol": 1e-10,
-                           "launches_per_round": args.launches_per_round,
-                           "inner_tiles": args.inner_tiles,
-                           "step": "one batched cooperative launch (each job's next solve)"},
-                "gpu_launches": launches, "clocks": clk, "wall_s": wall,
-                "all_ok": all(s == 0 for s in status),
-                "rounds_by_active_jobs": {k: {"rounds": c, "ms": ms} for k, (c, ms) in by_active.items()},
-                "cg_iters_fine_per_solve": sum(s["cg_iters_fine"] for s in stats) / max(1, sum(s["solves_fine"] for s in stats)),
-                "plain_fp64_one_at_a_time": {
-                    "value": alone_work / alone_s, "unit": "DOF-substeps/s",
-                    "sample": f"first {sample_steps} macro steps of each job alone (after 1 warm-up), FP64 tol 1e-12, "
-                              "extrapolated linearly to each job's scan"},
-                "speedup_vs_plain_fp64": (total_work / dev_s) / (alone_work / alone_s)}
-        print(json.dumps(line), flush=True)
-    ranks.finish(ws)
-    return 0
+    alone_s = max_over_ranks(alone_s, ws)
+    alone_work = sum_over_ranks(alone_work, ws)
+    return {"value": total_work / dev_s, "unit": "DOF-substeps/s",
+            "workload": f"batch_jobs({args.jobs}, seed 20211025)", "jobs": args.jobs,
+            "fine_dof_substeps": total_work, "precision": "fp32_refined", "tol": 1e-10,
+            "device_s": dev_s, "wall_s": wall, "rounds": info["launches"],
+            "launches_per_round": args.launches_per_round, "all_ok": all(s == 0 for s in status),
+            "cg_iters_fine_per_solve": sum(s["cg_iters_fine"] for s in stats)
+            / max(1, sum(s["solves_fine"] for s in stats)),
+            "plain_fp64_one_at_a_time": {
+                "value": alone_work / alone_s, "unit": "DOF-substeps/s",
+                "sample": f"first {sample_steps} macro steps of each job alone (after 1 warm-up), FP64 tol 1e-12, "
+                          "extrapolated linearly to each job's scan"},
+            "speedup_vs_plain_fp64": (total_work / dev_s) / (alone_work / alone_s)}
 
 
 def fp64_service_estimate(tl, torch, cfg, sp, stream, sample_steps=2):
@@ -508,23 +551,16 @@ def fp64_service_estimate(tl, torch, cfg, sp, stream, sample_steps=2):
     return a.elapsed_time(b) / 1e3 * c["macro_steps"] / sample_steps
 
 
-def run_serve(args):
+def measure_serve(args, tl, torch, sp, stream, rank, ws):
     """Poisson stream of jobs (batch_jobs shapes plus 10 % of the 20 mm plate
-    truncated to 200 macro steps), admitted by free slots and a device-memory
-    budget, served by continuous batching; compared with serving the same
-    arrivals one job at a time, first come first served, on the plain FP64
-    path (service times from timed samples)."""
+    truncated to 200 macro steps) at args.rate jobs/s for args.duration s,
+    admitted by free slots and a device-memory budget, served by continuous
+    batching; compared with serving the same arrivals one job at a time, first
+    come first served, on the plain FP64 path (service times from timed
+    samples)."""
     import numpy as np
-    import torch
 
-    from paper_2110_12932_gb300 import build as tlbuild
-    from paper_2110_12932_gb300 import serve, tl
-
-    rank, ws, local = dist_setup(args.gpus)
-    tlbuild.build()
-    tl.load()
-    stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
+    from paper_2110_12932_gb300 import serve
     arrivals = ranks.deal(workloads.serving_arrivals(args.rate, args.duration), rank, ws)
     for _, c in arrivals:
         c["inner_tiles"] = args.inner_tiles
@@ -535,16 +571,11 @@ def run_serve(args):
     for c in wt:  # warm-up
         c["macro_steps"] = 1
     srv.run([(0.0, c) for c in wt])
-    clocks = ClockSampler(local)
     barrier(ws)
     torch.cuda.synchronize()
-    clocks.start()
     rep = srv.run(arrivals)
-    clk = clocks.stop()
     srv.close()
-    # one at a time on the plain FP64 path: service time per distinct shape
-    cache = {}
-    service = []
+    cache, service = {}, []
     for _, c in arrivals:
         key = (c["name"].startswith("serve_large"), c["NXc"], c["NYc"], c["NZc"], c["pNXc"], c["pNYc"],
                c["pNZc"], c["r"], c["macro_steps"])
@@ -553,123 +584,134 @@ def run_serve(args):
         service.append(cache[key])
     fifo = serve.fifo_one_at_a_time(arrivals, service)
     value = ranks.aggregate_rate(rep["fine_dof_substeps"], rep["busy_s"], ws)
+    last_arrival = max((t for t, _ in arrivals), default=0.0)
+    return {"value": value, "unit": "DOF-substeps/s", "workload": "serving_arrivals",
+            "rate_per_s": args.rate, "duration_s": args.duration, "jobs": len(arrivals),
+            "large_jobs": sum(c["name"].startswith("serve_large") for _, c in arrivals),
+            "mem_cap_gb": args.mem_cap_gb, "precision": "fp32_refined", "tol": 1e-10,
+            "offered_dof_substeps": work,
+            "offered_rate": work / max(last_arrival, 1e-9), "served_rate": value,
+            "job_latency_s": rep["job_latency_s"], "coarse_step_latency_ms": rep["coarse_step_latency_ms"],
+            "wall_s": rep["wall_s"], "busy_s": rep["busy_s"], "rounds": rep["rounds"],
+            "peak_admitted_gb": rep["peak_admitted_bytes"] / 1e9, "all_ok": rep["all_ok"],
+            "plain_fp64_one_at_a_time": {
+                "throughput": work / sum(service),
+                "job_latency_s": {"p50": float(np.percentile(fifo, 50)), "p99": float(np.percentile(fifo, 99))},
+                "sample": "service time per job shape from its first 2 macro steps alone (FP64, tol 1e-12), "
+                          "extrapolated; first come first served"}}
+
+
+def _setup(args):
+    import torch
+
+    from paper_2110_12932_gb300 import build as tlbuild
+    from paper_2110_12932_gb300 import tl
+    rank, ws, local = dist_setup(args.gpus)
+    tlbuild.build()
+    tl.load()
+    stream = torch.cuda.current_stream()
+    return torch, tl, rank, ws, local, stream, stream.cuda_stream
+
+
+def run_ours(args):
+    torch, tl, rank, ws, local, stream, sp = _setup(args)
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    cfg64, cfg32, out, accuracy = measure_plate(args, tl, torch, sp, stream, ws)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    a, b = out["fp64"], out["fp32"]
+    nfn, ne, m, K = fine_nodes(cfg32), fine_elems(cfg32), cfg32["m"], args.steps
+    picard = max(1, args.picard)  # solves per fine micro step; fine_ms times the whole micro step
+    peak, src = hbm_peak()
+    launch_s = statistics.mean(b["fine_ms"]) / 1e3
+    byt = picard * fine_bytes(cfg32, "fp32", b["iters"], b["outer"])
+    achieved = byt / launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": FINE_LAUNCH_DRAM_BYTES.get(args.workload), "peak_source": src,
+                "frac_of_8TBps": achieved / HBM_NOMINAL_GBS,
+                "kernel": "tl::solve_kernel<1> (precision-form fine micro step)",
+                "launch_ms": 1e3 * launch_s, "bytes_per_launch": byt,
+                "inner_iters_per_solve": b["iters"], "outer_sweeps_per_solve": b["outer"],
+                "bytes_note": f"fine nodes x ({B_SOLVE['fp32']} + {B_OUTER} x outer sweeps + {B_ITER['fp32']} x "
+                              "inner CG iterations) algorithmic bytes per solve"}
+    launch64 = statistics.mean(a["fine_ms"]) / 1e3
+    fl64 = picard * fine_flops(cfg64, a["iters"])
+    fp64 = {"value": a["value"], "unit": "DOF-substeps/s", "ms_per_step": a["ms_per_step"], "tol": 1e-12,
+            "fine_launch_ms": 1e3 * launch64, "cg_iters_per_solve": a["iters"],
+            "coarse_cg_iters_per_solve": a["stats"]["cg_iters_coarse"] / max(1, a["stats"]["solves_coarse"]),
+            "gpu_launches": int(sum_over_ranks(a["stats"]["launches"], ws)),
+            "roofline": {"bound": "alu", "achieved": fl64 / launch64 / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": fl64 / launch64 / 1e12 / FP64_PEAK_TFLOPS,
+                         "kernel": "tl::solve_kernel<0> (FP64 fine micro step)",
+                         "hbm_GBps": picard * fine_bytes(cfg64, "fp64", a["iters"], 0) / launch64 / 1e9,
+                         "peak_note": "FP64 pipe, derived: 152 SMs x 4 flop/clk x 2.07 GHz (a DFMA loop measured "
+                                      "1.20 TFLOP/s); FP64 flops of the apply (65 per element) and the vector "
+                                      "work (14 per node) per CG iteration"}}
+    # end to end through the public API: create, K steps, host read-back each step
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    p2 = tl.Problem(cfg32, stream=sp)
+    host = None
+    for _ in range(K):
+        p2.macro_steps(1)
+        host, _ = p2.temperature(tl.TL_FINE)
+    p2.close()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": b["work"] / e2e_s, "unit": "DOF-substeps/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": int(host.nbytes), "wall_s": e2e_s,
+           "note": "tl_create_problem + per step tl_macro_steps(1) + tl_get_temperature(fine) into a host buffer; "
+                   "step inputs (laser positions, weights) travel as launch parameters"}
+    extra = {}
+    if args.mode == "full":
+        extra["roofline_probe"] = measure_probe(tl, torch)
+        extra["batch"] = measure_batch(args, tl, torch, sp, stream, rank, ws)
+        extra["serve"] = measure_serve(args, tl, torch, sp, stream, rank, ws)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "DOF-substeps/s", "n_gpus": ws,
-                "steps": rep["rounds"], "warmup": 1, "ms_per_step": 1e3 * rep["busy_s"] / max(1, rep["rounds"]),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-                "data": "synthetic",
-                "config": {"workload": "serving_arrivals", "rate_per_s": args.rate, "duration_s": args.duration,
-                           "jobs": len(arrivals), "large_jobs": sum(c["name"].startswith("serve_large")
-                                                                  for _, c in arrivals),
-                           "mem_cap_gb": args.mem_cap_gb, "precision": "fp32_refined", "tol": 1e-10,
-                           "step": "one batch round", "offered_dof_substeps": work},
-                "job_latency_s": rep["job_latency_s"], "coarse_step_latency_ms": rep["coarse_step_latency_ms"],
-                "wall_s": rep["wall_s"], "busy_s": rep["busy_s"], "peak_admitted_gb": rep["peak_admitted_bytes"] / 1e9,
-                "all_ok": rep["all_ok"], "clocks": clk,
-                "plain_fp64_one_at_a_time": {
-                    "throughput": work / sum(service),
-                    "job_latency_s": {"p50": float(np.percentile(fifo, 50)), "p99": float(np.percentile(fifo, 99))},
-                    "sample": "service time per job shape from its first 2 macro steps alone (FP64, tol 1e-12), "
-                              "extrapolated; first come first served"}}
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            cpu = cpu_baseline(cfg64)
+        line = {"metric": METRIC, "value": b["value"], "unit": "DOF-substeps/s", "n_gpus": ws, "steps": K,
+                "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": cfg32["name"], "fine_nodes": nfn, "fine_elements": ne,
+                           "coarse_nodes": (cfg32["NXc"] + 1) * (cfg32["NYc"] + 1) * (cfg32["NZc"] + 1),
+                           "m": m, "r": cfg32["r"], "precision": "fp32_refined", "tol": 1e-10, "tol_inner": 1e-5,
+                           "coupling_sweeps": args.coupling_sweeps, "latent": args.latent,
+                           "picard_iters": args.picard, "h_conv": args.h_conv, "emissivity": args.emissivity,
+                           "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                           "l2": "flushed (256 MB write) between timed macro steps, outside the events"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum_over_ranks(b["stats"]["launches"], ws)),
+                "clocks": clk, "wall_s": wall,
+                "cg_iters": {"fine_inner_per_solve": b["iters"], "fine_outer_per_solve": b["outer"],
+                             "coarse_inner_per_solve": b["stats"]["cg_iters_coarse"]
+                             / max(1, b["stats"]["solves_coarse"])},
+                "fp64": fp64, "speedup_vs_fp64": b["value"] / a["value"], "accuracy": accuracy}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     ranks.finish(ws)
     return 0
 
 
-# Algorithmic bytes per node of one CG iteration of the default form (the
-# tensor-preconditioned CG, three phases; elements ~ nodes):
-#  update: reads r, q, x, u, p, s (solve precision) and sq (FP32), writes
-#   p, s, r, x (solve precision) and v (FP32); exchange partials on tile faces
-#   are not counted;
-#  preconditioner: reads v and sq (FP32) and r, writes u (solve precision);
-#   the v halo comes from L2 and is not counted;
-#  apply: FP32 on wide tiles reads u and two element coefficients and writes
-#   the partial q; FP64 on element tiles reads u and eight FP64 eigenvalues
-#   per element and writes q.
-UPDATE_BYTES = {"fp32": 12 * 4, "fp64": 10 * 8 + 2 * 4}
-PRECOND_BYTES = {"fp32": 4 * 4, "fp64": 2 * 4 + 2 * 8}
-APPLY_BYTES = {"fp32": 4 * 4, "fp64": 2 * 8 + 8 * 8}
-# FP64 flops of the FP64 form's phases (the FP32 preconditioner filter runs on
-# the FP32 pipe and is not counted): update 5 FMA per node, <r,u> 1 FMA per
-# node, apply FLOPS_APPLY_PER_ELEM per element plus <w,u>.
-UPDATE_FLOPS_FP64 = 10
-PRECOND_FLOPS_FP64 = 2
-HBM_GBS = 6688.8  # measured copy bandwidth of this GB300 (read + write bytes)
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-
-
-def run_roofline(args):
-    """A 256 x 256 x 128-element fine patch (8.5M nodes; 32 x 32 x 16 coarse
-    elements refined 8x, plate 40 x 40 x 20 coarse): one micro step in each
-    precision, per-phase times of the CG iterations from the device phase
-    tracer (block 0's view: a phase ends when the grid barrier after it is
-    passed)."""
-    import torch
-
-    from paper_2110_12932_gb300 import build as tlbuild
-    from paper_2110_12932_gb300 import tl
-
-    tlbuild.build()
-    tl.load()
-    base = workloads.workload("multitrack_10mm", Lx=5e-3, Ly=5e-3, Lz=2.5e-3, NXc=40, NYc=40, NZc=20,
-                              pNXc=32, pNYc=32, pNZc=16, r=8, m=8,
-                              tracks=[(1e-3, 2.5e-3, 4e-3, 2.5e-3, 0.8)])
-    nn = fine_nodes(base)
-    ne = 256 * 256 * 128
-    out = {}
-    names = {v: k for k, v in tl.TRACE_MARKS.items()}
-    for prec in ("fp32", "fp64"):
-        cfg = dict(base, precision=1 if prec == "fp32" else 0, tol=1e-10 if prec == "fp32" else 1e-12)
-        p = tl.Problem(cfg)
-        p.macro_steps(1)           # warm-up macro step
-        p.predict()
-        p.fine_substeps(1)
-        torch.cuda.synchronize()
-        ev = [e for e in p.trace(tl.TL_FINE) if e[0] not in (names["rr_value"], names["breakdown_value"])]
-        p.close()
-        launch = (ev[-1][1] - ev[0][1]) / 1e9
-        ends = [b for (m, b) in ev if m == names["cg_pass"]]
-        t = statistics.median([(y - x) / 1e9 for x, y in zip(ends, ends[1:])]) if len(ends) > 1 else float("nan")
-        seg = {}
-        for (m0, a), (m1, b) in zip(ev, ev[1:]):
-            seg.setdefault((m0, m1), []).append((b - a) / 1e9)
-
-        def med(a, b):
-            return statistics.median(seg[(names[a], names[b])])
-
-        tu = med("cg_pass", "cg_u_start") + med("cg_u_start", "cg_u_end") + med("cg_u_end", "cg_update")
-        tp = med("cg_update", "cg_precond")
-        ta = med("cg_precond", "cg_apply") + med("cg_apply", "cg_pass")
-        bu, bp, ba = UPDATE_BYTES[prec] * nn, PRECOND_BYTES[prec] * nn, APPLY_BYTES[prec] * nn
-
-        def phase(us, byt):
-            return {"us": 1e6 * us, "bytes": byt, "GBps": byt / us / 1e9, "frac_of_measured_hbm": byt / us / 1e9 / HBM_GBS}
-
-        o = {"launch_ms": 1e3 * launch, "cg_iterations": len(ends), "iteration_us": 1e6 * t,
-             "scheme": "tensor-preconditioned CG, three phases; apply on "
-                       + ("wide tiles" if prec == "fp32" else "element tiles"),
-             "update_phase": dict(phase(tu, bu), block0_share_us=1e6 * med("cg_u_start", "cg_u_end"),
-                                  reduce_and_barrier_us=1e6 * med("cg_u_end", "cg_update")),
-             "precond_phase": phase(tp, bp),
-             "apply_phase": phase(ta, ba),
-             "bytes_per_iteration": bu + bp + ba, "GBps": (bu + bp + ba) / t / 1e9,
-             "frac_of_measured_hbm": (bu + bp + ba) / t / 1e9 / HBM_GBS}
-        if prec == "fp64":
-            fa = FLOPS_APPLY_PER_ELEM * ne + 2 * nn
-            o["apply_phase"].update({"fp64_flops": fa, "TFLOPs": fa / ta / 1e12,
-                                     "frac_of_fp64_peak": fa / ta / 1e12 / FP64_PEAK_TFLOPS})
-            fi = fa + (UPDATE_FLOPS_FP64 + PRECOND_FLOPS_FP64) * nn
-            o.update({"fp64_flops_per_iteration": fi, "TFLOPs": fi / t / 1e12,
-                      "frac_of_fp64_peak": fi / t / 1e12 / FP64_PEAK_TFLOPS})
-        out[prec] = o
-    line = {"metric": "CG iteration throughput (update, preconditioner, matrix-free apply)", "mode": "roofline",
-            "config": {"fine_nodes": nn, "fine_elements": ne,
-                       "bytes_per_node": {"update": UPDATE_BYTES, "precond": PRECOND_BYTES, "apply": APPLY_BYTES},
-                       "fp64_flops": {"apply_per_element": FLOPS_APPLY_PER_ELEM, "update_per_node": UPDATE_FLOPS_FP64,
-                                      "precond_per_node": PRECOND_FLOPS_FP64},
-                       "hbm_peak_GBps": HBM_GBS, "fp64_peak_TFLOPs": FP64_PEAK_TFLOPS},
-            "results": out}
-    print(json.dumps(line), flush=True)
+def _single(args, what):
+    torch, tl, rank, ws, local, stream, sp = _setup(args)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if what == "batch":
+        res = measure_batch(args, tl, torch, sp, stream, rank, ws)
+    elif what == "serve":
+        res = measure_serve(args, tl, torch, sp, stream, rank, ws)
+    else:
+        res = measure_probe(tl, torch)
+    clk = clocks.stop()
+    if rank == 0:
+        print(json.dumps({"mode": what, "clocks": clk, **res}), flush=True)
+    ranks.finish(ws)
     return 0
 
 
@@ -677,12 +719,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.mode == "batch":
-        return run_batch(args)
-    if args.mode == "serve":
-        return run_serve(args)
-    if args.mode == "roofline":
-        return run_roofline(args)
+    if args.mode in ("batch", "serve", "roofline"):
+        return _single(args, args.mode)
     return run_ours(args)
 
 
