@@ -139,8 +139,14 @@ typedef struct {
   /* heat loss through the top surface (Section 3.1): convection
    * h_conv (T - T_amb) [W/(m^2 K)] on the top of both levels, radiation
    * sigma_SB emissivity (T^4 - T_amb^4) on the top of the fine patch (the
-   * local domain); h_conv = emissivity = 0: adiabatic top.  Requires
-   * h_conv >= 0, 0 <= emissivity <= 1, T_amb > 0 [K] when either is on. */
+   * local domain); h_conv = emissivity = 0: adiabatic top.  Backward Euler
+   * with the radiation written as h_rad (T - T_amb),
+   * h_rad = sigma_SB emissivity (T*^2 + T_amb^2)(T* + T_amb) per top face at
+   * the face mean of the temperature the coefficients are taken at (T^k, or
+   * the Picard iterate: exact at the fixed point); the consistent surface
+   * mass of the bilinear face hats.  Requires h_conv >= 0,
+   * 0 <= emissivity <= 1, T_amb > 0 [K] when either is on, and the tensor
+   * preconditioner (precond 0 or 2). */
   double h_conv, emissivity, T_amb;
   /* time limit [s] of every device-side grid barrier wait; 0 = 1 s, at most
    * 60 s.  A wait that runs out ends the launch at that barrier in every
@@ -158,8 +164,9 @@ typedef struct {
 
 /* Counters and energy account (J) since creation.  stored = sum_e rho c_e
  * int_e (T^{k+1} - T^k), laser = dt sum_i F_i, flux = dt * (sum of the
- * Dirichlet-row reactions); per solve stored = laser + flux up to the solver
- * tolerance (discrete energy identity). */
+ * Dirichlet-row reactions), loss = dt * (heat through the top surface,
+ * int_top h (T^{k+1} - T_amb)); per solve stored = laser + flux - loss up to
+ * the solver tolerance (discrete energy identity). */
 typedef struct {
   int64_t macro_steps, substeps;
   int64_t cg_iters_fine, cg_iters_coarse;    /* all inner CG iterations        */
@@ -173,6 +180,7 @@ typedef struct {
   double energy_coarse_stored, energy_coarse_laser, energy_coarse_flux;
   double time;                               /* simulated time t_n [s]         */
   int64_t coupling_resolves;                 /* extra corrections of the iterated coupling */
+  double energy_fine_loss, energy_coarse_loss;  /* top-surface losses (0 with an adiabatic top) */
 } tl_stats;
 
 /* Validate *cfg, allocate and initialise (T = T0 on both levels, states by

@@ -67,6 +67,8 @@ struct Level {
   unsigned long long* trace = nullptr;  // phase timestamps of the level's last solve
   uint8_t* state = nullptr;
   uint8_t* st_new = nullptr;  // new element states of a solve until its commit
+  double* hf = nullptr;       // top-surface losses: transfer coefficient per top face
+  float* hf32 = nullptr;
   int st_sx = 0, st_sy = 0, st_sz = 0;
   double Mc[8], Kc[8], Md = 0, Kd = 0, vol8 = 0, Mhat[64], Khat[64];
 };
@@ -248,6 +250,11 @@ bool use_wide(const tl_config& c, const Grid3& g, int blocks) {
   return (long long)g.nx * g.ny * g.nz >= WIDE_MIN_ELEMS_PER_BLOCK * std::max(1, blocks);
 }
 
+// Stefan-Boltzmann constant (CODATA 2018) [W/(m^2 K^4)].
+constexpr double SIGMA_SB = 5.670374419e-8;
+
+bool surface_on(const tl_config& c) { return c.h_conv > 0 || c.emissivity > 0; }
+
 tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
   const size_t nn = (size_t)L.g.nnx * L.g.nny * L.g.nnz;
   const size_t ne = (size_t)L.g.nx * L.g.ny * L.g.nz;
@@ -300,6 +307,11 @@ tl_status alloc_level(tl_problem* p, Level& L, bool coarse) {
   if ((s = alloc_n(p, &L.trace, 2 * TRACE_CAP)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.state, (size_t)L.st_sx * L.st_sy * L.st_sz)) != TL_OK) return s;
   if ((s = alloc_n(p, &L.st_new, ne)) != TL_OK) return s;
+  if (surface_on(p->cfg)) {
+    const size_t nf = (size_t)L.g.nx * L.g.ny;
+    if ((s = alloc_n(p, &L.hf, nf)) != TL_OK) return s;
+    if (p->cfg.precision == TL_FP32_REFINED && (s = alloc_n(p, &L.hf32, nf)) != TL_OK) return s;
+  }
   return TL_OK;
 }
 
@@ -447,6 +459,18 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.state = L.state;
   a.st_new = L.st_new;
   const tl_config& c = p->cfg;
+  // top-surface losses (Section 3.1): convection on both levels, radiation on
+  // the local (fine) level only
+  a.surf = surface_on(c) ? 1 : 0;
+  a.h_conv = c.h_conv;
+  a.rad = &L == &p->Fi ? SIGMA_SB * c.emissivity : 0.0;
+  a.T_amb = c.T_amb;
+  a.hf = L.hf;
+  a.hf32 = L.hf32;
+  a.Mfx[0] = L.g.hx / 3.0;
+  a.Mfx[1] = L.g.hx / 6.0;
+  a.Mfy[0] = L.g.hy / 3.0;
+  a.Mfy[1] = L.g.hy / 6.0;
   a.mat = Material{c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref, c.powder_factor, c.T_melt,
                    c.latent, c.pc_sharpness, 0.5 * (c.T_solidus + c.T_liquidus)};
   a.tol = c.tol;
@@ -626,7 +650,9 @@ tl_status validate(const tl_config* c) {
   if (!(c->barrier_timeout >= 0) || c->barrier_timeout > 60.0) return TL_EINVAL;
   if (!(c->h_conv >= 0) || !(c->emissivity >= 0) || c->emissivity > 1.0) return TL_EINVAL;
   if ((c->h_conv > 0 || c->emissivity > 0) && !(c->T_amb > 0)) return TL_EINVAL;
-  if (c->h_conv > 0 || c->emissivity > 0) return TL_EINVAL;  // top-surface losses: oracle only so far
+  // the surface term rides on the apply of the stored CG direction, which the
+  // Jacobi forms (fused update) do not keep
+  if ((c->h_conv > 0 || c->emissivity > 0) && c->precond == 1) return TL_EINVAL;
   for (int j = 0; j < c->ntracks; ++j) {
     const tl_track& k = c->path[j];
     if (!(k.speed > 0)) return TL_EINVAL;
@@ -1265,6 +1291,8 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out) {
   out->energy_fine_stored = d.e_stored[1];
   out->energy_fine_laser = d.e_laser[1];
   out->energy_fine_flux = d.e_flux[1];
+  out->energy_fine_loss = d.e_loss[1];
+  out->energy_coarse_loss = d.e_loss[0];
   out->time = p->n * p->cfg.dt_coarse;
   out->coupling_resolves = p->coupling_resolves;
   return TL_OK;

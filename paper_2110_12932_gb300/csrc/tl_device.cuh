@@ -80,7 +80,8 @@ __host__ __device__ inline int split_lo(int n, int parts, int a) {
 // some block has not arrived, so the count can no longer complete), records
 // ST_TIMEOUT and returns false; a waiting block that sees ST_TIMEOUT returns
 // false too, so that all blocks leave the kernel at the same barrier and no
-// block runs a phase that another skipped.
+// block runs a phase that another skipped.  Once the count is complete no
+// block gives up: the release follows.
 // Word layout (BAR_WORDS unsigned ints, zero at creation): [0..1] the 64-bit
 // arrival / generation word, [BAR_STATUS] the sticky status word.
 // ---------------------------------------------------------------------------
@@ -137,10 +138,13 @@ __device__ inline void bar_begin(const Barrier& b) {
   __syncthreads();
 }
 
-// Waits (thread 0) until generation g is released, or every block has arrived
-// at it; false if the time limit passed (the arrival is withdrawn and the
-// time-out recorded) or another block recorded a time-out.  The status word
-// and the clock are looked at every 16th poll, or at every poll under a limit
+// Waits (thread 0) until generation g is released; false if the time limit
+// passed (the arrival is withdrawn and the time-out recorded) or another block
+// recorded a time-out.  A block passes only once the generation has moved:
+// every arrival at the next barrier then comes after this release in the
+// word's order, so its count starts from zero.  Once every block has arrived
+// the release is on its way and the wait never gives up.  The status word and
+// the clock are looked at every 16th poll, or at every poll under a limit
 // shorter than a millisecond.
 __device__ inline bool bar_wait(const Barrier& b, unsigned int g, int nblk) {
   const unsigned long long t0 = global_ns();
@@ -148,25 +152,19 @@ __device__ inline bool bar_wait(const Barrier& b, unsigned int g, int nblk) {
   for (unsigned int poll = 1;; ++poll) {
     unsigned long long w = ld_acquire_u64(b.word);
     if ((unsigned int)(w >> 32) != g) return true;
-    if ((unsigned int)w == (unsigned int)nblk) {  // complete; the release is on its way
-      __threadfence();
-      return true;
-    }
-    if (every || (poll & 15) == 0) {
+    if ((every || (poll & 15) == 0) && (unsigned int)w != (unsigned int)nblk) {
       if (ld_volatile_i32(b.status) == ST_TIMEOUT) return false;
       if (global_ns() - t0 > b.limit_ns) {
         for (;;) {  // withdraw the arrival while the count is incomplete
           if ((unsigned int)(w >> 32) != g) return true;
-          if ((unsigned int)w == (unsigned int)nblk) {
-            __threadfence();
-            return true;
-          }
+          if ((unsigned int)w == (unsigned int)nblk) break;  // complete: wait for the release
           const unsigned long long prev = atomicCAS(b.word, w, w - 1ull);
-          if (prev == w) break;
+          if (prev == w) {
+            atomicExch(b.status, (int)ST_TIMEOUT);
+            return false;
+          }
           w = prev;
         }
-        atomicExch(b.status, (int)ST_TIMEOUT);
-        return false;
       }
     }
     __nanosleep(32);

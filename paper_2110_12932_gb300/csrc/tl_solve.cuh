@@ -277,10 +277,10 @@ __device__ inline double top_load_tab(const LoadSpec& L, const Grid3& g, const d
 
 // Counters written by block 0 at the end of each solve (index: 0 coarse, 1 fine).
 struct DevStats {
-  double e_stored[2], e_laser[2], e_flux[2];
+  double e_stored[2], e_laser[2], e_flux[2], e_loss[2];
   long long iters[2], solves[2], outer[2];
   int max_iters[2], last_iters[2];
-  double e_last[2][3];  // the last solve's stored / laser / flux terms per level (for rollback)
+  double e_last[2][4];  // the last solve's stored / laser / flux / loss terms per level (for rollback)
 };
 
 // Converts eight Hadamard factors (index = x mode + 2 y mode + 4 z mode) to
@@ -372,6 +372,15 @@ struct SolveArgs {
   int energy, update_state, level;
   double Mc[8], Kc[8], Md, Kd, vol8;  // Mc, Kc: eigenvalue factors in pair form (to_pair_form)
   double Mhat[64], Khat[64];
+  // heat loss through the top surface (Section 3.1): h_f (T - T_amb) per top
+  // face f with h_f = h_conv + rad (T*_f^2 + T_amb^2)(T*_f + T_amb), T*_f the
+  // face mean of the coefficient temperature (rad = sigma_SB emissivity on the
+  // fine level, 0 on the coarse one); hf / hf32 hold h_f (nx ny, x fastest)
+  int surf;        // 0: adiabatic top
+  double h_conv, rad, T_amb;
+  double* hf;
+  float* hf32;
+  double Mfx[2], Mfy[2];  // 1D mass entries of the face hats: same node h/3, other node h/6
   Barrier bar;
   double* red;   // reduction slots [RS_N][red_stride]
   float* red32;  // FP32 reduction slots of the refined path's inner CG
@@ -615,6 +624,79 @@ __device__ inline void store_partial(R* prim, R* X, int nn, int n, int slot, R v
   *dst = v;
 }
 
+// Element box of a tile: [ie0, ie0 + ex) x [je0, je0 + ey), and whether its
+// element layers reach the plate top.
+struct TileBox {
+  int ie0, je0, ex, ey;
+  bool top;
+};
+__device__ inline TileBox tile_box(const Grid3& g, const Tiling& t, int tile) {
+  const int txy = t.ntx * t.nty;
+  const int tiz = tile / txy, trem = tile - tiz * txy;
+  const int tiy = trem / t.ntx, tix = trem - tiy * t.ntx;
+  const int ie0 = tix * t.ex, je0 = tiy * t.ey;
+  return TileBox{ie0, je0, min(t.ex, g.nx - ie0), min(t.ey, g.ny - je0), min(tiz * t.ez + t.ez, g.nz) == g.nz};
+}
+
+// Top-surface transfer term of one tile (the Robin condition of Section 3.1):
+// for every node of the tile's window on the plate's top layer, the tile's
+// share sum over its top faces f next to the node of
+// h_f sum_b Mf[a, b] x_b, Mf = M1x (x) M1y the consistent surface mass of the
+// bilinear face hats, added to the partial the tile's apply emitted for that
+// node (own or exchange slot, as the apply chose).  Returns the share of
+// <x, H x>.  Called after the tile's apply with all threads of the block.
+template <typename R, typename XT, typename HT>
+__device__ R surface_partials(const Grid3& g, const TileBox& b, const XT* x, const HT* hf, const double (&mfx)[2],
+                              const double (&mfy)[2], R* q, R* X) {
+  const int wx = b.ex + 1, nwin = wx * (b.ey + 1);
+  const int nn = g.nnx * g.nny * g.nnz;
+  const int top = g.nnx * g.nny * g.nz;
+  const R mx[2] = {(R)mfx[0], (R)mfx[1]}, my[2] = {(R)mfy[0], (R)mfy[1]};
+  R vd = R(0);
+  for (int w = threadIdx.x; w < nwin; w += blockDim.x) {
+    const int wj = w / wx, wi = w - wj * wx;
+    const int i = b.ie0 + wi, j = b.je0 + wj;
+    R acc = R(0);
+    for (int je = max(j - 1, b.je0); je <= min(j, b.je0 + b.ey - 1); ++je)
+      for (int ie = max(i - 1, b.ie0); ie <= min(i, b.ie0 + b.ex - 1); ++ie) {
+        R sf = R(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int bx = c & 1, by = c >> 1;
+          const R wgt = mx[ie + bx == i ? 0 : 1] * my[je + by == j ? 0 : 1];
+          sf = fma(wgt, (R)__ldcg(x + top + (ie + bx) + g.nnx * (je + by)), sf);
+        }
+        acc = fma((R)__ldcg(hf + ie + g.nx * je), sf, acc);
+      }
+    const int n = top + i + g.nnx * j;
+    const int slot = ((wi == b.ex && b.ie0 + b.ex < g.nx) ? 1 : 0) | ((wj == b.ey && b.je0 + b.ey < g.ny) ? 2 : 0);
+    store_partial(q, X, nn, n, slot, acc, true);
+    vd = fma((R)__ldcg(x + n), acc, vd);
+  }
+  __syncthreads();
+  return vd;
+}
+
+// Row of the surface operator at top node (i, j) applied to v - shift (all
+// faces next to the node), in FP64.
+__device__ inline double surface_row(const Grid3& g, const double* hf, const double (&mfx)[2], const double (&mfy)[2],
+                                     int i, int j, const double* T, const double* u, double shift) {
+  const int top = g.nnx * g.nny * g.nz;
+  double acc = 0.0;
+  for (int je = max(j - 1, 0); je <= min(j, g.ny - 1); ++je)
+    for (int ie = max(i - 1, 0); ie <= min(i, g.nx - 1); ++ie) {
+      double sf = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        const int bx = c & 1, by = c >> 1;
+        const int nb = top + (ie + bx) + g.nnx * (je + by);
+        const double v = (u ? __ldcg(T + nb) + __ldcg(u + nb) : __ldcg(T + nb)) - shift;
+        sf = fma(mfx[ie + bx == i ? 0 : 1] * mfy[je + by == j ? 0 : 1], v, sf);
+      }
+      acc = fma(__ldcg(hf + ie + g.nx * je), sf, acc);
+    }
+  return acc;
+}
+
 // Grid-wide loop over node rows (j, k): each warp takes whole rows, its lanes
 // walk i, so the only division is one per row.  body(n, i, j, k, row_low_faces).
 template <class Body>
@@ -646,7 +728,8 @@ __device__ inline void for_elems(const Grid3& g, const VGrid& vg, Body body) {
   }
 }
 
-enum RedSlot { RS_RZ0 = 0, RS_BB = 1, RS_PQ = 2, RS_RZ = 3, RS_RR = 4, RS_ES = 5, RS_EL = 6, RS_EF = 7, RS_N = 8 };
+enum RedSlot { RS_RZ0 = 0, RS_BB = 1, RS_PQ = 2, RS_RZ = 3, RS_RR = 4, RS_ES = 5, RS_EL = 6, RS_EF = 7, RS_EX = 8,
+               RS_N = 9 };
 
 // Buffers of one preconditioned CG on the free nodes.  Arrays that a tile
 // reads on its whole window while owners update them are double-buffered by
@@ -1857,6 +1940,22 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       a.sk32[ne + e] = (float)k;
     }
   });
+  if (a.surf) {  // transfer coefficient per top face at the face mean of the coefficient temperature
+    const int top = S * g.nz;
+    for (int f = gtid; f < g.nx * g.ny; f += gstride) {
+      const int je = f / g.nx, ie = f - je * g.nx;
+      const int n0 = top + ie + g.nnx * je;
+      double tf = __ldcg(Tcoef + n0);
+      tf += __ldcg(Tcoef + n0 + 1);
+      tf += __ldcg(Tcoef + n0 + g.nnx);
+      tf += __ldcg(Tcoef + n0 + g.nnx + 1);
+      tf *= 0.25;
+      const double ta = a.T_amb;
+      const double h = a.h_conv + a.rad * (tf * tf + ta * ta) * (tf + ta);
+      a.hf[f] = h;
+      if (refined) a.hf32[f] = (float)h;
+    }
+  }
   tr.mark(TR_P0_ELEMS);
   // increments: 0 on free nodes, g - T^k on Dirichlet nodes (disjoint writes)
   for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool, bool) {
@@ -1901,6 +2000,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
             int e = ie + g.nx * (je + g.ny * ke);
             d += __ldcg(a.s_e + e) * a.Md + __ldcg(a.k_e + e) * a.Kd;
           }
+      if (a.surf && k == g.nz)
+        for (int je = max(j - 1, 0); je <= min(j, g.ny - 1); ++je)
+          for (int ie = max(i - 1, 0); ie <= min(i, g.nx - 1); ++ie)
+            d += __ldcg(a.hf + ie + g.nx * je) * a.Mfx[0] * a.Mfy[0];
       di = 1.0 / d;
     }
     a.dinv[n] = di;
@@ -1922,10 +2025,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     const FinishArray<double, double> fin;
     auto no_lam_fetch = [](int, double*) {};
     for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
+      const TileBox tb = tile_box(g, t, tile);
       apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.u}, fin, no_lam_fetch,
                                       lam_full, emit1);
+      if (a.surf && tb.top) surface_partials<double>(g, tb, a.u, a.hf, a.Mfx, a.Mfy, a.q, a.X);
       apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.T_in}, fin,
                                       no_lam_fetch, lam_k, emit2);
+      // the surface term of T^k too: its ambient part enters the load below
+      if (a.surf && tb.top) surface_partials<double>(g, tb, a.T_in, a.hf, a.Mfx, a.Mfy, a.q, a.X);
     }
   }
   if (!grid_sync(a.bar, vg)) return;
@@ -1935,12 +2042,19 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool ly, bool lz) {
       double rr = 0.0;
       double Fn = 0.0;
+      double Fa = 0.0;  // ambient part of the surface term: T_amb sum_f h_f int_f phi_n dA
       if (k == g.nz) {  // the top-face load, kept for the energy account
         Fn = top_load_tab(a.ld, g, a.G, i, j);
         a.F[n - S * g.nz] = Fn;
+        if (a.surf) {
+          double hs = 0.0;
+          for (int je = max(j - 1, 0); je <= min(j, g.ny - 1); ++je)
+            for (int ie = max(i - 1, 0); ie <= min(i, g.nx - 1); ++ie) hs += __ldcg(a.hf + ie + g.nx * je);
+          Fa = a.T_amb * hs * (0.25 * g.hx * g.hy);
+        }
       }
       if (!is_dir(g, a.dir, i, j, k))
-        rr = Fn - gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
+        rr = (Fn + Fa) - gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
       a.r[n] = rr;
       v[0] += rr * rr * __ldcg(a.dinv + n);
       v[1] += rr * rr;
@@ -1977,6 +2091,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
         };
         apply_tile<double, false, 1, 1>(g, t, tile, sm64, stage64, StageArray<double, double>{c3.u},
                                         FinishArray<double, double>{}, no_fetch64, lam64, emit);
+        if (a.surf) {
+          const TileBox tb = tile_box(g, t, tile);
+          if (tb.top) vd += surface_partials<double>(g, tb, c3.u, a.hf, a.Mfx, a.Mfy, c3.q, c3.X);
+        }
         return vd;
       };
       res = pcg3<double>(a, vg, t, c3, apply_z, stage64, thresh, a.max_iter, a.red, &it, tr);
@@ -2042,7 +2160,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
           cf.kp[m] = kcf[m];
         }
         auto apply_z = [&](int tile) {
-          return apply_wide_partials(g, a.tw, tile, smw, stage32, c3.u, a.sk32, cf, c3.q, c3.X);
+          float vd = apply_wide_partials(g, a.tw, tile, smw, stage32, c3.u, a.sk32, cf, c3.q, c3.X);
+          if (a.surf) {
+            const TileBox tb = tile_box(g, a.tw, tile);
+            if (tb.top) vd += surface_partials<float>(g, tb, c3.u, a.hf32, a.Mfx, a.Mfy, c3.q, c3.X);
+          }
+          return vd;
         };
         res = pcg3<float>(a, vg, a.tw, c3, apply_z, stage32, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
       } else {
@@ -2055,6 +2178,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
           // staging slots: 0 the window value, 1 and 2 the element data
           apply_tile<float, true, 3, 1>(g, t, tile, sm32, stage32, StageArray<float, float>{c3.u},
                                         FinishArray<float, float>{}, fetch32, lam32, emit);
+          if (a.surf) {
+            const TileBox tb = tile_box(g, t, tile);
+            if (tb.top) vd += surface_partials<float>(g, tb, c3.u, a.hf32, a.Mfx, a.Mfy, c3.q, c3.X);
+          }
           return vd;
         };
         res = pcg3<float>(a, vg, t, c3, apply_z, stage32, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
@@ -2086,9 +2213,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     };
     auto no_lam_fetch = [](int, double*) {};
     auto emit = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, false); };
-    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk)
+    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
       apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, float>{a.d32},
                                       FinishArray<double, float>{}, no_lam_fetch, lam_full, emit);
+      if (a.surf) {
+        const TileBox tb = tile_box(g, t, tile);
+        if (tb.top) surface_partials<double>(g, tb, a.d32, a.hf, a.Mfx, a.Mfy, a.q, a.X);
+      }
+    }
     if (!grid_sync(a.bar, vg)) return;
     tr.mark(TR_OUTER_APPLY);
     double v[1] = {0.0};
@@ -2125,9 +2257,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   // the problem's state as it was.  The new states and the energy terms are
   // formed from T^k + u, the same values T_out receives.
   tr.mark(TR_UPDATE);
-  double te[3] = {0.0, 0.0, 0.0};
+  double te[3] = {0.0, 0.0, 0.0}, tloss[1] = {0.0};
   if (a.update_state || a.energy) {
-    double v[3] = {0.0, 0.0, 0.0};
+    double v[3] = {0.0, 0.0, 0.0}, vl[1] = {0.0};
     for_elems(g, vg, [&](int e, int ie, int je, int ke) {
       if (a.update_state) {
         const double Tb = elem_mean_sum(a.T_in, a.u, g, ie, je, ke);
@@ -2152,6 +2284,18 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     tr.mark(TR_END_ELEMS);
     if (a.energy) {
       for (int n = gtid; n < S; n += gstride) v[1] += a.dt * __ldcg(a.F + n);
+      if (a.surf) {  // heat lost through the top: dt 1^T H (T^{k+1} - T_amb), face by face
+        const int top = S * g.nz;
+        for (int f = gtid; f < g.nx * g.ny; f += gstride) {
+          const int je = f / g.nx, ie = f - je * g.nx;
+          const int n0 = top + ie + g.nnx * je;
+          const int off[4] = {0, 1, g.nnx, g.nnx + 1};
+          double sv = 0.0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) sv += __ldcg(a.T_in + n0 + off[c]) + __ldcg(a.u + n0 + off[c]) - a.T_amb;
+          vl[0] += a.dt * __ldcg(a.hf + f) * (0.25 * g.hx * g.hy) * sv;
+        }
+      }
       for_dirichlet(g, a.dir, vg, [&](int n, int i, int j, int k) {
         // reaction of a Dirichlet row: (S u + K T^{k+1})_n - F_n, T^{k+1} = T^k + u
         double R_n = 0.0;
@@ -2173,13 +2317,18 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
               }
               R_n += se * am + kk * ak;
             }
-        if (k == g.nz) R_n -= __ldcg(a.F + (n - S * g.nz));
+        if (k == g.nz) {
+          R_n -= __ldcg(a.F + (n - S * g.nz));
+          if (a.surf) R_n += surface_row(g, a.hf, a.Mfx, a.Mfy, i, j, a.T_in, a.u, a.T_amb);
+        }
         v[2] += a.dt * R_n;
       });
     }
     tr.mark(TR_END_DIR);
     block_reduce_store<3>(v, a.red + RS_ES * a.red_stride, a.red_stride, vg);
+    if (a.surf) block_reduce_store<1>(vl, a.red + RS_EX * a.red_stride, a.red_stride, vg);
     if (!grid_sync_total<3>(a.bar, vg, a.red + RS_ES * a.red_stride, a.red_stride, te)) return;
+    if (a.surf) grid_total<1>(a.red + RS_EX * a.red_stride, a.red_stride, tloss, vg);
   }
   // the commit: no barrier follows
   if (a.T_relax) {  // an intermediate Picard solve: only the next coefficient temperature
@@ -2200,9 +2349,11 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       a.stats->e_stored[lvl] += te[0];
       a.stats->e_laser[lvl] += te[1];
       a.stats->e_flux[lvl] += te[2];
+      a.stats->e_loss[lvl] += tloss[0];
       a.stats->e_last[lvl][0] = te[0];
       a.stats->e_last[lvl][1] = te[1];
       a.stats->e_last[lvl][2] = te[2];
+      a.stats->e_last[lvl][3] = tloss[0];
     }
     a.stats->iters[lvl] += it;
     a.stats->outer[lvl] += outer;
@@ -2318,6 +2469,7 @@ __global__ void energy_rollback_kernel(DevStats* s, int lvl) {
     s->e_stored[lvl] -= s->e_last[lvl][0];
     s->e_laser[lvl] -= s->e_last[lvl][1];
     s->e_flux[lvl] -= s->e_last[lvl][2];
+    s->e_loss[lvl] -= s->e_last[lvl][3];
   }
 }
 

@@ -72,6 +72,7 @@ class tl_stats(C.Structure):
         ("energy_coarse_flux", C.c_double),
         ("time", C.c_double),
         ("coupling_resolves", C.c_int64),
+        ("energy_fine_loss", C.c_double), ("energy_coarse_loss", C.c_double),
     ]
 
 

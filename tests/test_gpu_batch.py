@@ -109,3 +109,36 @@ def test_batch_admits_and_retires_between_rounds():
     for p in (a, b, c, ref):
         p.close()
     batch.close()
+
+
+def test_many_small_slices_keep_every_barrier():
+    """48 small jobs share each launch (slices of a few blocks, short phases):
+    a barrier that let a block into its next phase early, or lost an arrival,
+    would end in a time-out (a nonzero status) or a wrong field.  Every job
+    must finish with status 0 and equal its solo run."""
+    base = workloads.workload("single_track_tiny")
+    jobs = []
+    for k in range(48):
+        c = dict(base, macro_steps=6 + k % 5, P=120.0 + 3.0 * k)
+        if k % 3 == 1:
+            c.update(precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5)
+        if k % 4 == 2:
+            c.update(pNXc=3, pNYc=2, pNZc=1, r=2, m=2)
+        jobs.append(c)
+    probs = [tl.Problem(c) for c in jobs]
+    b = tl.Batch(launches_per_round=10, max_jobs=64)
+    for p, c in zip(probs, jobs):
+        b.add(p, c["macro_steps"])
+    b.run()
+    b.close()
+    for k, (p, c) in enumerate(zip(probs, jobs)):
+        assert p.sync() == tl.TL_OK, k
+        got = p.temperature(tl.TL_FINE)[0]
+        p.close()
+        if k % 6 == 0 or k % 6 == 1:  # a sample of solo runs
+            q = tl.Problem(c)
+            q.macro_steps(c["macro_steps"])
+            want = q.temperature(tl.TL_FINE)[0]
+            q.close()
+            tol = 1e-6 if c.get("precision", 0) == tl.TL_FP32_REFINED else 1e-9
+            assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), k

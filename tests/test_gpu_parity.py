@@ -446,3 +446,80 @@ def test_zero_latent_and_one_picard_iteration_is_the_plain_step():
     assert np.array_equal(base.temperature(tl.TL_COARSE)[0], same.temperature(tl.TL_COARSE)[0])
     base.close()
     same.close()
+
+
+# ---- top-surface convection and radiation (Section 3.1) ---------------------
+# Coefficients far above the physical ones (h ~ 10 W/(m^2 K)) so that the term
+# moves the solution well beyond the parity tolerance.
+
+SURFACE_CASES = [
+    dict(h_conv=2e5),
+    dict(h_conv=1e4, emissivity=0.8),
+    dict(h_conv=1e5, T_amb=600.0),                       # heat enters through the top
+    dict(h_conv=1e4, emissivity=0.8, picard_iters=3),    # h_rad at the Picard iterate
+]
+
+
+def _energy_identity_with_loss(st, ref, tol):
+    for lvl in ("fine", "coarse"):
+        s_, l_, f_, x_ = (st[f"energy_{lvl}_{k}"] for k in ("stored", "laser", "flux", "loss"))
+        scale = max(abs(s_), abs(l_), abs(x_))
+        assert abs(s_ - l_ - f_ + x_) <= tol * scale, (lvl, s_, l_, f_, x_)
+        o = ref.energy[f"{lvl}_loss"]
+        assert o != 0.0 and abs(x_ - o) <= 10 * tol * scale, (lvl, x_, o)
+
+
+@pytest.mark.parametrize("over", SURFACE_CASES)
+def test_top_surface_losses_against_oracle(over):
+    cfg = workloads.workload("single_track_tiny", **over)
+    prob, ref, _ = run_both(cfg, 16, check_every=4)
+    plain = tl.Problem(workloads.workload("single_track_tiny"))
+    plain.macro_steps(16)
+    assert rel(prob.temperature(tl.TL_FINE)[0], plain.temperature(tl.TL_FINE)[0]) > 1e-6  # the term matters
+    plain.close()
+    _energy_identity_with_loss(prob.stats(), ref, 1e-9)
+    prob.close()
+
+
+@pytest.mark.parametrize("inner_tiles", [1, 2])
+def test_top_surface_losses_refined_against_oracle(inner_tiles):
+    """The precision form with both inner tilings on the ragged 72 x 18 x 12
+    patch (wide tiles: a ragged x tile and y row), radiation included."""
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5,
+                             inner_tiles=inner_tiles, pNXc=12, pNYc=3, pNZc=2, r=6, m=2, h_conv=1e4,
+                             emissivity=0.8)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg)
+    for _ in range(3):
+        prob.macro_steps(2)
+        ref.run(2)
+        Tf, org = prob.temperature(tl.TL_FINE)
+        Tc, _ = prob.temperature(tl.TL_COARSE)
+        assert tuple(org) == tuple(ref.origin)
+        assert rel(Tf, ref.Tf) <= REFINED_TOL and rel(Tc, ref.Tc) <= REFINED_TOL
+        assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+    _energy_identity_with_loss(prob.stats(), ref, 1e-7)
+    prob.close()
+
+
+def test_top_surface_losses_in_a_batch_equal_alone():
+    base = workloads.workload("single_track_tiny", h_conv=1e4, emissivity=0.8)
+    jobs = [dict(base, macro_steps=6), dict(base, macro_steps=4, P=150.0, precision=tl.TL_FP32_REFINED,
+                                             tol=1e-10, tol_inner=1e-5)]
+    alone = []
+    for cfg in jobs:
+        p = tl.Problem(cfg)
+        p.macro_steps(cfg["macro_steps"])
+        alone.append(p.temperature(tl.TL_FINE)[0])
+        p.close()
+    probs = [tl.Problem(c) for c in jobs]
+    b = tl.Batch(launches_per_round=3, max_jobs=4)
+    for p, c in zip(probs, jobs):
+        b.add(p, c["macro_steps"])
+    b.run()
+    b.close()
+    for p, c, a in zip(probs, jobs, alone):
+        assert p.sync() == tl.TL_OK
+        tol = 1e-6 if c.get("precision", 0) == tl.TL_FP32_REFINED else 1e-9
+        assert rel(p.temperature(tl.TL_FINE)[0], a) <= tol
+        p.close()
