@@ -76,9 +76,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="full", choices=["full", "plain", "batch", "serve", "roofline"],
+    ap.add_argument("--no-autotune", action="store_true", help="plain: cost-model tilings only")
+    ap.add_argument("--mode", default="full", choices=["full", "plain", "batch", "serve", "roofline", "launch"],
                     help="full: the plate in both precisions plus the roofline probe, the batch and the serve "
-                         "sub-objects; plain: the plate only; batch / serve / roofline: one of them alone")
+                         "sub-objects; plain: the plate only; batch / serve / roofline: one of them alone; "
+                         "launch: one macro step, then a predictor and one fine micro step (the 12th solve "
+                         "launch), for profiler captures")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1], help="launch: 0 FP64, 1 precision form")
     ap.add_argument("--jobs", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
@@ -371,13 +375,15 @@ def measure_plate(args, tl, torch, sp, stream, ws):
     against the stored oracle fields."""
     import numpy as np
     form = dict(coupling_sweeps=args.coupling_sweeps, latent=args.latent, picard_iters=args.picard,
-                h_conv=args.h_conv, emissivity=args.emissivity)
+                h_conv=args.h_conv, emissivity=args.emissivity, autotune=0 if args.no_autotune else 1)
     cfg64 = workloads.workload(args.workload, precision=0, tol=1e-12, **form)
     cfg32 = workloads.workload(args.workload, precision=1, tol=1e-10, tol_inner=1e-5, **form)
     nfn, m, K = fine_nodes(cfg64), cfg64["m"], args.steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    for c in (cfg64, cfg32):  # warm-up on throw-away problems
+    tilings = {}
+    for name, c in (("fp64", cfg64), ("fp32", cfg32)):  # warm-up on throw-away problems (tunes the tilings)
         wp = tl.Problem(c, stream=sp)
+        tilings[name] = {"fine": wp.tiling(tl.TL_FINE), "coarse": wp.tiling(tl.TL_COARSE)}
         for _ in range(args.warmup):
             wp.macro_steps(1)
         wp.close()
@@ -400,6 +406,7 @@ def measure_plate(args, tl, torch, sp, stream, ws):
         "fp32_refined_vs_oracle": versus_oracle(tl, cfg32, sp),
         "fp64_vs_oracle": versus_oracle(tl, cfg64, sp),
     }
+    accuracy["tilings"] = tilings
     return cfg64, cfg32, out, accuracy
 
 
@@ -715,10 +722,32 @@ def _single(args, what):
     return 0
 
 
+def run_launch(args):
+    """A short fixed launch sequence for profiler captures: the problem, one
+    macro step, then PREDICT and one fine micro step."""
+    torch, tl, rank, ws, local, stream, sp = _setup(args)
+    prec = args.precision
+    cfg = workloads.workload(args.workload, precision=prec, tol=1e-10 if prec else 1e-12, tol_inner=1e-5)
+    p = tl.Problem(cfg, stream=sp)
+    p.macro_steps(1)
+    p.predict()
+    p.fine_substeps(1)
+    status = p.sync()
+    st = p.stats()
+    p.close()
+    if rank == 0:
+        print(json.dumps({"mode": "launch", "workload": cfg["name"], "precision": prec, "status": status,
+                          "cg_iters_fine": st["cg_iters_fine"], "solves_fine": st["solves_fine"]}), flush=True)
+    ranks.finish(ws)
+    return 0 if status == 0 else 1
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "launch":
+        return run_launch(args)
     if args.mode in ("batch", "serve", "roofline"):
         return _single(args, args.mode)
     return run_ours(args)

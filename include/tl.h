@@ -154,6 +154,11 @@ typedef struct {
    * TL_ETIMEOUT and leaves the problem's fields and states as the last
    * complete solve left them. */
   double barrier_timeout;
+  /* 1: time candidate tilings of each level with at least 65,536 nodes at
+   * creation and keep the fastest (cached per mesh shape in the process;
+   * results then depend on the pick only through the FP32 summation order);
+   * 0: cost models only. */
+  int autotune;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
   /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks
    * must be 16-byte aligned (else tl_create_problem returns TL_EINVAL) */
@@ -239,6 +244,13 @@ tl_status tl_get_state(const tl_problem* p, tl_level level, uint8_t* host_out, s
 
 /* Copy the counters (synchronises). */
 tl_status tl_get_stats(const tl_problem* p, tl_stats* out);
+
+/* Tilings a level's solves use: out[0..2] element tiles (ex, ey, ez),
+ * out[3..5] wide tiles of the refined inner CG (0 when not used), out[6..8]
+ * the preconditioner pass's node tiles (columns x, rows y, layers z),
+ * out[9] the cooperative grid, out[10] 1 if the autotuner chose them.
+ * Errors: TL_EINVAL. */
+tl_status tl_get_tiling(const tl_problem* p, tl_level level, int32_t out[11]);
 
 /* Phase timeline of the most recent solve on a level: *n_out pairs
  * (marker, device time in ns) are recorded, the first min(n, cap) are copied

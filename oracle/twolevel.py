@@ -51,6 +51,13 @@ One macro step t_n -> t_n + Dt (Algorithm 1), this oracle's reading:
      max|T+^{n+1,(k)} - T+^{n+1,(k-1)}| <= coupling_tol max|T+^{n+1,(k)}| or
      coupling_sweeps corrections were made.  Only the final solves count in
      the energy account.
+  6. Flux-jump coupling (interface_coupling = 1; the alternate global problem
+     of Section 3, Eq. globalPbmAlternate): instead of steps 4-5 the
+     correction redoes the coarse backward-Euler step from T+^n with only the
+     plate's own boundary conditions and the interface load
+     G_I = int_gamma (kappa_+ - kappa_-) dT-/dn phi_I dA added to its source
+     (see interface_load); the fine field enters the global problem through
+     that load alone.
 
 Coefficients are lagged: each backward-Euler step evaluates rho c_e and k_e
 at the element mean of the step's starting temperature and the element's
@@ -532,10 +539,133 @@ class TwoLevel:
                     del self.step_energy[j]
                     break
 
+    # -- flux-jump coupling (Section 3, Eqs. deltaDef and globalPbmAlternate) --
+    def interface_faces(self, origin=None):
+        """The patch faces immersed in the plate (the interface gamma): x-,
+        x+, y-, y+ where the patch does not touch the plate's side, and the
+        bottom unless it lies on the plate's bottom."""
+        o = self.origin if origin is None else origin
+        xm, xp, ym, yp, _ = self.dirichlet_faces(o)
+        return (xm, xp, ym, yp, o[2] > 0)
+
+    def interface_load(self, Tf=None, k_fine=None, k_coarse=None):
+        """G_I = int_gamma (kappa_+ - kappa_-) dT-/dn phi_I dA for every coarse
+        node I (Eq. deltaDef's functional of the flux jump), n the outward
+        normal of the local domain.  dT-/dn is the normal derivative of the
+        fine trilinear field inside the fine element next to the face;
+        kappa_- that element's conductivity and kappa_+ the conductivity of the
+        coarse element just outside the patch at that face; phi_I the coarse
+        trilinear hats.  On each fine face the integrand is a product of two
+        bilinear functions, integrated exactly by 2 x 2 Gauss points.
+        Defaults: Tf the current fine field; kappa_- from its element means
+        and the fine states; kappa_+ from the element means of the coarse field
+        and the coarse states (the global step's own lagged coefficients)."""
+        T = self.Tf if Tf is None else Tf
+        mesh = self.fine_mesh()
+        C = self.coarse
+        if k_fine is None:
+            _, k_fine = self.mat.coefficients(mesh.element_mean(T), self.fine_state().reshape(-1))
+        if k_coarse is None:
+            _, k_coarse = self.mat.coefficients(C.element_mean(self.Tc), self.state_c)
+        k_fine = np.broadcast_to(np.asarray(k_fine, dtype=np.float64), (mesh.nelem,))
+        k_coarse = np.broadcast_to(np.asarray(k_coarse, dtype=np.float64), (C.nelem,))
+        o, r = self.origin, self.r
+        nx, ny, nz = self.nf
+        h = self.hf
+        G = np.zeros(C.nnode)
+        g = 1.0 / np.sqrt(3.0)
+        gp = (0.5 * (1.0 - g), 0.5 * (1.0 + g))  # Gauss points on [0, 1], weights 1/2 each
+        faces = self.interface_faces()
+        # (normal axis d, side s (0 low, 1 high), outward sign)
+        for d, side, on in ((0, 0, faces[0]), (0, 1, faces[1]), (1, 0, faces[2]), (1, 1, faces[3]),
+                            (2, 0, faces[4])):
+            if not on:
+                continue
+            a1, a2 = [ax for ax in range(3) if ax != d]
+            n_t = (nx, ny, nz)
+            cnt1, cnt2 = n_t[a1], n_t[a2]
+            sign = 1.0 if side else -1.0
+            e_d = 0 if side == 0 else n_t[d] - 1            # fine element index across d
+            for u1 in range(2):
+                for u2 in range(2):
+                    xi1, xi2, w = gp[u1], gp[u2], 0.25
+                    e1, e2 = np.meshgrid(np.arange(cnt1), np.arange(cnt2), indexing="ij")
+                    e1, e2 = e1.ravel(), e2.ravel()
+                    eidx = [0, 0, 0]
+                    eidx[d], eidx[a1], eidx[a2] = np.full(e1.shape, e_d), e1, e2
+                    # dT/dx_d in the element at in-plane reference point (xi1, xi2)
+                    grad = np.zeros(e1.shape)
+                    for b1 in range(2):
+                        for b2 in range(2):
+                            wt = (xi1 if b1 else 1.0 - xi1) * (xi2 if b2 else 1.0 - xi2)
+                            nid = []
+                            for bd in range(2):
+                                idx = [None, None, None]
+                                idx[d] = eidx[d] + bd
+                                idx[a1] = eidx[a1] + b1
+                                idx[a2] = eidx[a2] + b2
+                                nid.append(mesh.node_id(idx[0], idx[1], idx[2]))
+                            grad += wt * (T[nid[1]] - T[nid[0]]) / h[d]
+                    dTdn = sign * grad
+                    fe = eidx[0] + nx * (eidx[1] + ny * eidx[2])
+                    kminus = k_fine[fe]
+                    # global fine coordinates of the Gauss point (in fine index units)
+                    gf = [None, None, None]
+                    gf[d] = np.full(e1.shape, float((e_d + side) + [o[0], o[1], o[2]][d] * r))
+                    gf[a1] = e1 + xi1 + [o[0], o[1], o[2]][a1] * r
+                    gf[a2] = e2 + xi2 + [o[0], o[1], o[2]][a2] * r
+                    # coarse element just outside the patch, and the hats of the face
+                    cc = [np.floor(gf[ax] / r).astype(np.int64) for ax in range(3)]
+                    out_d = [o[0], o[1], o[2]][d] + (self.pN[d] if side else 0) - (0 if side else 1)
+                    cc[d] = np.full(e1.shape, out_d)
+                    kplus = k_coarse[cc[0] + C.nx * (cc[1] + C.ny * cc[2])]
+                    jump = (kplus - kminus) * dTdn * w * h[a1] * h[a2]
+                    # coarse hats on the face plane: bilinear in the two in-plane axes
+                    Id = [o[0], o[1], o[2]][d] + (self.pN[d] if side else 0)
+                    for c1 in range(2):
+                        for c2 in range(2):
+                            ci = [None, None, None]
+                            ci[d] = np.full(e1.shape, Id)
+                            ci[a1] = cc[a1] + c1
+                            ci[a2] = cc[a2] + c2
+                            t1 = gf[a1] / r - cc[a1]
+                            t2 = gf[a2] / r - cc[a2]
+                            phi = (t1 if c1 else 1.0 - t1) * (t2 if c2 else 1.0 - t2)
+                            np.add.at(G, C.node_id(ci[0], ci[1], ci[2]), jump * phi)
+        return G
+
+    def _flux_correction(self):
+        """The global backward-Euler step of Eq. globalPbmAlternate from T+^n
+        with the interface load of the fine field at the end of the macro step
+        (not committed): returns (T+^{n+1}, coarse states, energy terms)."""
+        c = self.cfg
+        G = self.interface_load()
+        F = self.coarse_load(self.n)
+        g = np.full(len(self.coarse_bottom), float(c["T_bottom"]))
+        Tn, rc, k, H = be_picard(self.coarse, self.Tc, self._coarse_coefficients, self.Dt, F + G,
+                                 self.coarse_bottom, g, c.get("picard_iters", 1), self.surf_c)
+        e = None
+        if self.track_energy:
+            e = energy_terms(self.coarse, self.Tc, Tn, rc / self.Dt, k, F + G, self.coarse_bottom, self.Dt, H,
+                             self.surf_c.T_amb)
+            gi = self.Dt * float(G.sum())
+            e["laser"] -= gi       # the interface heat counts as flux through the boundary
+            e["flux"] += gi
+            e["interface"] = gi
+        return Tn, self.mat.update_state(self.coarse.element_mean(Tn), self.state_c), e
+
     def restrict_and_correct(self):
         """Steps 4 and 5: correction, iterated with re-solves of the last
         micro step while coupling_sweeps allows and the coarse field moves."""
         c = self.cfg
+        if int(c.get("interface_coupling", 0)) == 1:
+            Tn, state, e = self._flux_correction()
+            if self.track_energy:
+                self._add_energy("coarse", e)
+            self.state_c = state
+            self.Tc = Tn
+            self.Tc_pred = None
+            return
         sweeps = int(c.get("coupling_sweeps", 1))
         tol = float(c.get("coupling_tol", 1e-10))
         Tn, state, e = self._correction()

@@ -8,7 +8,10 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "tl.h"
@@ -25,7 +28,9 @@ struct Level {
   Tiling t{};
   Tiling tb{};   // tiling used in batched launches (a slice of the grid)
   Tiling tw{};   // refined path on large meshes: wide tiles of the FP32 inner CG
+  Tiling tp{};   // node tiles of the tensor preconditioner's pass
   int wide = 0;
+  int tuned = 0; // 1: the tilings were chosen by timing (the autotuner)
   int grid = 0;  // cooperative grid size
   double* T = nullptr;    // current temperature
   double* T2 = nullptr;   // coarse: predictor T~+; fine: move double buffer
@@ -91,7 +96,9 @@ struct tl_problem {
   int* status = nullptr;
   double* red = nullptr;
   float* red32 = nullptr;
-  int red_stride = 0;
+  int red_stride = 0;   // reduction slots per row: the cooperative grid cap
+  int max_slice = 0;    // the most blocks a solve of this problem uses
+  unsigned int* tune_bar = nullptr;  // barrier / status words of the tuner's timing runs
   DevStats* stats = nullptr;
   unsigned long long* d_diff = nullptr;  // iterated coupling: max |change|, max |T+| (IEEE bits)
   long long coupling_resolves = 0;
@@ -184,10 +191,11 @@ void element_constants(Level& L) {
 // shape (window columns and partial node layers cost extra), plus a fixed
 // cost per layer and tile for the block barriers, divided by the pipe
 // utilisation that one or two resident 8-warp blocks reach.
-void choose_tiling(Level& L, int nsm, int per_sm) {
+void choose_tiling(Level& L, int nsm, int per_sm, std::vector<Tiling>* ranked = nullptr) {
   const Grid3& g = L.g;
   double best = 1e300;
   Tiling bt{};
+  std::vector<std::pair<double, Tiling>> all;
   const int exs[] = {16, 8};
   const int eys[] = {8, 4, 2, 1};
   for (int ex0 : exs)
@@ -203,12 +211,23 @@ void choose_tiling(Level& L, int nsm, int per_sm) {
         const long long b = (G + nsm - 1) / nsm, tb = (T + G - 1) / G;
         const double eff = b >= 4 ? 0.85 : (b >= 2 ? 0.7 : 0.4);
         const double cost = (double)(b * tb) * per_tile / eff;
+        const Tiling t{ex, ey, ez, (g.nx + ex - 1) / ex, (g.ny + ey - 1) / ey, (g.nz + ez - 1) / ez};
+        if (ranked) all.push_back({cost, t});
         if (cost < best * (1 - 1e-9)) {
           best = cost;
-          bt = Tiling{ex, ey, ez, (g.nx + ex - 1) / ex, (g.ny + ey - 1) / ey, (g.nz + ez - 1) / ez};
+          bt = t;
         }
       }
   L.t = bt;
+  if (ranked) {  // distinct shapes, cheapest first
+    std::stable_sort(all.begin(), all.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    ranked->clear();
+    for (const auto& c : all) {
+      bool dup = false;
+      for (const Tiling& r : *ranked) dup |= r.ex == c.second.ex && r.ey == c.second.ey && r.ntz == c.second.ntz;
+      if (!dup) ranked->push_back(c.second);
+    }
+  }
 }
 
 // Wide tiles (AX x AY x ez elements) of the FP32 inner CG on large meshes.
@@ -223,17 +242,34 @@ Tiling wide_tiling(const Grid3& g, int /*nblk*/) {
 }
 
 // Node-owned tiles of the tensor preconditioner's pass: rows split into equal
-// widths of at most 32 columns, as many rows as fill the block, and z-chunks
-// for about four tiles per block.
+// widths of at most 32 columns, as many rows as fill the block, and the
+// z-depth ez that minimises the layer steps of the busiest block: a tile of ez
+// owned layers marches through ez + 2 layers and costs about PC_TILE_STEPS
+// more for its prologue and drain, and a block runs ceil(tiles / blocks)
+// tiles.  (On the 20 mm patch the earlier rule, about four tiles per block,
+// gave 3-layer tiles and 28 step-equivalents per block; this one gives
+// 13-layer tiles and 17.)
+constexpr int PC_TILE_STEPS = 2;
+
 Tiling pc_tiling(const Grid3& g, int nblk) {
   const int ntx = (g.nnx + 31) / 32;
   const int tx = (g.nnx + ntx - 1) / ntx;
   const int ty = std::max(1, std::min(g.nny, NT / tx));
   const int nty = (g.nny + ty - 1) / ty;
   const long long cols = (long long)ntx * nty;
-  const long long want = std::max(1LL, (4LL * std::max(1, nblk) + cols - 1) / cols);
-  const int ez = std::max(2, (int)((g.nnz + want - 1) / want));
-  return Tiling{tx, ty, ez, ntx, nty, (g.nnz + ez - 1) / ez};
+  const long long B = std::max(1, nblk);
+  int best_ez = g.nnz;
+  long long best = -1;
+  for (int ez = std::min(2, g.nnz); ez <= g.nnz; ++ez) {
+    const long long ntz = (g.nnz + ez - 1) / ez;
+    if (ez > 2 && (g.nnz + ez - 2) / (ez - 1) == ntz) continue;  // same chunk count as a thinner ez
+    const long long cost = (cols * ntz + B - 1) / B * (ez + 2 + PC_TILE_STEPS);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_ez = ez;
+    }
+  }
+  return Tiling{tx, ty, best_ez, ntx, nty, (g.nnz + best_ez - 1) / best_ez};
 }
 
 // With inner_tiles = 0 the refined path runs its inner CG on wide tiles when
@@ -418,7 +454,7 @@ void fill_common(const tl_problem* p, const Level& L, SolveArgs& a) {
   a.t = L.t;
   a.wide = L.wide;
   a.tw = L.tw;
-  a.tp = pc_tiling(L.g, L.grid);
+  a.tp = L.tp;
   a.u = L.u;
   a.r = L.r;
   a.r2 = L.r2;
@@ -852,6 +888,173 @@ tl_status coupled_correct(tl_problem* p) {
   return cuda_status(e);
 }
 
+// ---- the tiling autotuner -------------------------------------------------
+// Tilings only decide how the blocks of a solve walk the mesh; which one is
+// fastest depends on the mesh, the grid and the GPU in ways the cost models
+// above only approximate.  For a level of at least AUTOTUNE_MIN_NODES nodes the
+// tuner times dry solves (the level's first solve as it will run, committing
+// nothing but a scratch output, on separate barrier and status words) of a few
+// candidates per tiling, one tiling at a time: the preconditioner pass's
+// z-depth (the model's three cheapest), then the wide tiles' depth (refined
+// path on wide tiles: nz / 16 ... nz / 4) or the element tile shape (the cost
+// model's three cheapest shapes), keeping the fastest of each (the best of
+// two timed runs after one warm-up).  Picks are cached per mesh shape,
+// precision, preconditioner and grid cap for the life of the process.
+constexpr long long AUTOTUNE_MIN_NODES = 65536;
+
+struct TuneKey {
+  int nx, ny, nz, prec, precond, wide, grid_cap, fine;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nx, ny, nz, prec, precond, wide, grid_cap, fine) <
+           std::tie(o.nx, o.ny, o.nz, o.prec, o.precond, o.wide, o.grid_cap, o.fine);
+  }
+};
+struct TunePick {
+  Tiling t, tw, tp;
+  int grid;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TunePick> g_tune_cache;
+
+// Dry-run arguments of the level's first solve: a fine micro step (output
+// into the move buffer) or a coarse predictor (its output is the predictor
+// buffer, rewritten by the first real predictor).
+void dry_args(tl_problem* p, Level& L, bool fine, SolveArgs& a) {
+  if (fine) {
+    build_fine_args(p, 0, a);
+    a.T_out = L.T2;
+  } else {
+    build_coarse_args(p, false, false, a);
+  }
+  a.update_state = 0;
+  a.energy = 0;
+  a.dry = 1;
+  a.trace = nullptr;
+  a.bar = Barrier{reinterpret_cast<unsigned long long*>(p->tune_bar), (int*)(p->tune_bar + BAR_STATUS),
+                  barrier_limit_ns(p->cfg)};
+}
+
+// Best of `reps` timed dry solves after one warm-up, in ms; < 0 on a failed
+// run (then the tuner keeps the models' picks).
+float time_dry(tl_problem* p, Level& L, bool fine, cudaEvent_t e0, cudaEvent_t e1, int reps = 2) {
+  float best = -1.0f;
+  for (int k = 0; k <= reps; ++k) {
+    SolveArgs a{};
+    dry_args(p, L, fine, a);
+    if (cudaMemsetAsync(p->tune_bar, 0, BAR_WORDS * sizeof(unsigned int), p->stream) != cudaSuccess) return -1.0f;
+    cudaEventRecord(e0, p->stream);
+    void* args[] = {(void*)&a};
+    cudaError_t e = cudaLaunchCooperativeKernel(solve_kernel_for(pmode_of(p->cfg)), dim3(L.grid), dim3(NT), args,
+                                                STAGE_BYTES, p->stream);
+    cudaEventRecord(e1, p->stream);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, p->tune_bar + BAR_STATUS, sizeof st, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return -1.0f;
+    }
+    if (st != 0) return -1.0f;
+    if (k > 0 && (best < 0 || ms < best)) best = ms;
+  }
+  return best;
+}
+
+tl_status autotune_level(tl_problem* p, Level& L, bool fine) {
+  const long long nn = (long long)L.g.nnx * L.g.nny * L.g.nnz;
+  if (nn < AUTOTUNE_MIN_NODES) return TL_OK;
+  const tl_config& c = p->cfg;
+  const TuneKey key{L.g.nx, L.g.ny, L.g.nz, (int)c.precision, c.precond == 1 ? 1 : 0, L.wide, p->max_coop,
+                    fine ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      L.t = it->second.t;
+      L.tw = it->second.tw;
+      L.tp = it->second.tp;
+      L.grid = it->second.grid;
+      L.tuned = 1;
+      return TL_OK;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return TL_ECUDA;
+  }
+  bool ok = true;
+  float best = time_dry(p, L, fine, e0, e1);
+  ok = best >= 0;
+  // 1. the preconditioner pass's z-depth (tensor preconditioner only)
+  if (ok && c.precond != 1) {
+    const Tiling t0 = L.tp;
+    // half, one and a half and twice the model's depth
+    const int cands[3] = {t0.ez / 2, (3 * t0.ez + 1) / 2, 2 * t0.ez};
+    Tiling win = t0;
+    for (int ez0 : cands) {
+      const int ez = std::min(L.g.nnz, std::max(2, ez0));
+      if (ez == win.ez || ez == t0.ez) continue;
+      L.tp = Tiling{t0.ex, t0.ey, ez, t0.ntx, t0.nty, (L.g.nnz + ez - 1) / ez};
+      const float ms = time_dry(p, L, fine, e0, e1);
+      if (ms >= 0 && ms < best) {
+        best = ms;
+        win = L.tp;
+      }
+    }
+    L.tp = win;
+  }
+  // 2. the wide tiles' depth, or the element tile shape
+  if (ok && L.wide) {
+    const Tiling t0 = L.tw;
+    Tiling win = t0;
+    for (int div : {16, 12, 6, 4}) {
+      const int ez = std::max(1, (L.g.nz + div / 2) / div);
+      if (ez == win.ez || ez == t0.ez) continue;
+      L.tw = Tiling{AX, AY, ez, t0.ntx, t0.nty, (L.g.nz + ez - 1) / ez};
+      const float ms = time_dry(p, L, fine, e0, e1);
+      if (ms >= 0 && ms < best) {
+        best = ms;
+        win = L.tw;
+      }
+    }
+    L.tw = win;
+  } else if (ok) {
+    std::vector<Tiling> ranked;
+    Level tmp = L;
+    int per_sm = std::max(1, p->max_coop / std::max(1, p->nsm));
+    choose_tiling(tmp, p->nsm, per_sm, &ranked);
+    const Tiling t0 = L.t;
+    const int g0 = L.grid;
+    Tiling win = t0;
+    int wgrid = g0;
+    for (size_t k = 0; k < ranked.size() && k < 3; ++k) {
+      const Tiling& t = ranked[k];
+      if (t.ex == t0.ex && t.ey == t0.ey && t.ez == t0.ez) continue;
+      L.t = t;
+      L.grid = std::min(p->max_coop, t.ntx * t.nty * t.ntz);
+      const float ms = time_dry(p, L, fine, e0, e1);
+      if (ms >= 0 && ms < best) {
+        best = ms;
+        win = t;
+        wgrid = L.grid;
+      }
+    }
+    L.t = win;
+    L.grid = wgrid;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return TL_OK;  // a failed timing run: the models' picks stay
+  L.tuned = 1;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = TunePick{L.t, L.tw, L.tp, L.grid};
+  return TL_OK;
+}
+
 }  // namespace
 
 struct tl_batch {
@@ -942,16 +1145,19 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
   choose_tiling(F, p->nsm, per_sm);
   C.grid = std::min(p->max_coop, C.t.ntx * C.t.nty * C.t.ntz);
   F.grid = std::min(p->max_coop, F.t.ntx * F.t.nty * F.t.ntz);
-  p->red_stride = std::max(C.grid, F.grid);
+  p->red_stride = p->max_coop;
+  p->max_slice = std::max(C.grid, F.grid);
   for (Level* L : {&C, &F}) {
     L->wide = use_wide(c, L->g, L->grid);
     if (L->wide) L->tw = wide_tiling(L->g, L->grid);
+    L->tp = pc_tiling(L->g, L->grid);
   }
   if ((s = alloc_level(p, C, true)) != TL_OK || (s = alloc_level(p, F, false)) != TL_OK ||
       (s = alloc_n(p, &p->bar, BAR_WORDS)) != TL_OK ||
       (s = alloc_n(p, &p->red, (size_t)RS_N * p->red_stride)) != TL_OK ||
       (s = alloc_n(p, &p->red32, (size_t)RS_N * p->red_stride)) != TL_OK ||
-      (s = alloc_n(p, &p->stats, 1)) != TL_OK || (s = alloc_n(p, &p->d_diff, 2)) != TL_OK) {
+      (s = alloc_n(p, &p->stats, 1)) != TL_OK || (s = alloc_n(p, &p->d_diff, 2)) != TL_OK ||
+      (s = alloc_n(p, &p->tune_bar, BAR_WORDS)) != TL_OK) {
     release(p);
     delete p;
     return s;
@@ -994,6 +1200,16 @@ tl_status tl_create_problem(const tl_config* cfg, tl_problem** out) {
     release(p);
     delete p;
     return s;
+  }
+  if (c.autotune) {
+    for (Level* L : {&F, &C}) {
+      if ((s = autotune_level(p, *L, L == &F)) != TL_OK) {
+        release(p);
+        delete p;
+        return s;
+      }
+    }
+    p->max_slice = std::max(C.grid, F.grid);
   }
   *out = p;
   return TL_OK;
@@ -1298,6 +1514,15 @@ tl_status tl_get_stats(const tl_problem* p, tl_stats* out) {
   return TL_OK;
 }
 
+tl_status tl_get_tiling(const tl_problem* p, tl_level level, int32_t out[11]) {
+  if (!p || !out || (level != TL_COARSE && level != TL_FINE)) return TL_EINVAL;
+  const Level& L = level == TL_COARSE ? p->C : p->Fi;
+  const int32_t v[11] = {L.t.ex, L.t.ey, L.t.ez, L.wide ? L.tw.ex : 0, L.wide ? L.tw.ey : 0, L.wide ? L.tw.ez : 0,
+                         L.tp.ex, L.tp.ey, L.tp.ez, L.grid, L.tuned};
+  std::memcpy(out, v, sizeof v);
+  return TL_OK;
+}
+
 tl_status tl_trace_last_solve(const tl_problem* p, tl_level level, uint64_t* host_out, size_t cap, size_t* n_out) {
   if (!p || !host_out || !n_out || (level != TL_COARSE && level != TL_FINE)) return TL_EINVAL;
   const Level& L = level == TL_COARSE ? p->C : p->Fi;
@@ -1483,7 +1708,7 @@ tl_status tl_batch_round(tl_batch* b, int* active_out) {
     tab.nsolves[nj] = ns;
     b->round_ids.push_back((int)id);
     seen |= 1 << pmode_of(j.p->cfg);
-    capb.push_back(j.p->red_stride);
+    capb.push_back(j.p->max_slice);
     w.push_back(work);
     ++nj;
   }

@@ -370,6 +370,7 @@ struct SolveArgs {
   Tiling tp;       // pcg3: node-owned tiles of the preconditioner pass (ex x ey columns, ez layers)
   Tiling tw;
   int energy, update_state, level;
+  int dry;         // a timing run of the tiling tuner: no counters, nothing committed but T_out
   double Mc[8], Kc[8], Md, Kd, vol8;  // Mc, Kc: eigenvalue factors in pair form (to_pair_form)
   double Mhat[64], Khat[64];
   // heat loss through the top surface (Section 3.1): h_f (T - T_amb) per top
@@ -2241,7 +2242,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   }
   const int lvl = a.level;
   if (!conv) {
-    if (vg.bid == 0 && threadIdx.x == 0) {
+    if (vg.bid == 0 && threadIdx.x == 0 && !a.dry) {
       atomicCAS(a.bar.status, 0, (int)ST_NOCONV);
       a.stats->iters[lvl] += it;
       a.stats->outer[lvl] += outer;
@@ -2344,7 +2345,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       a.state[(ke * a.st_sy + je + a.st_oy) * a.st_sx + ie + a.st_ox] = __ldcg(a.st_new + e);
     });
   tr.mark(TR_END);
-  if (vg.bid == 0 && threadIdx.x == 0) {
+  if (vg.bid == 0 && threadIdx.x == 0 && !a.dry) {
     if (a.energy) {
       a.stats->e_stored[lvl] += te[0];
       a.stats->e_laser[lvl] += te[1];

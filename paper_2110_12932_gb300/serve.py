@@ -25,23 +25,53 @@ import numpy as np
 
 from . import tl, workloads
 
-# Device bytes per node of a level (FP64 path: T, T2, u, r x2, p x2, s x2, q x2,
-# 14 exchange arrays, dinv, load; refined path: the FP64 RHS arrays plus the
-# FP32 inner CG arrays) and per element (coefficients and eigenvalues).
-BYTES_PER_NODE = {0: 8 * 26, 1: 8 * 14 + 4 * 30}
-BYTES_PER_ELEM = {0: 8 * 10, 1: 8 * 10 + 4 * 8}
+# Allocation granularity allowance: each device allocation is rounded up to
+# this many bytes in the estimate (the CUDA allocator aligns blocks).
+ALLOC_ROUND = 512
+XB = 7        # exchange planes per partial buffer
+RS_N = 9      # reduction rows
+MAXRECT = 8   # load-table factors
+TRACE_CAP = 1024
+
+
+def _level_arrays(nnx, nny, nnz, nx, ny, nz, state_bytes, cfg, coarse):
+    """Byte sizes of the device arrays one level holds (the layout the
+    library allocates for a level)."""
+    nn, ne = nnx * nny * nnz, nx * ny * nz
+    xs = ((nn + 3) & ~3) * XB
+    prec = int(cfg.get("precision", 0))
+    a = [8 * nn] * 4 + [8 * nnx * nny, 8 * MAXRECT * (nnx + nny), 8 * nn, 8 * xs]
+    if prec == 0:
+        a += [8 * nn] * 6 + [8 * xs]
+    a += [8 * nn, 8 * ne, 8 * ne, 64 * ne]
+    if prec == 1:
+        a += [4 * nn] * 4 + [4 * xs, 4 * nn, 4 * xs] + [4 * nn] * 5 + [8 * ne]
+    if coarse:
+        a.append(8 * nn)
+    if int(cfg.get("coupling_sweeps", 1)) > 1:
+        a += ([8 * nn] * 2 if coarse else []) + [ne]
+    if int(cfg.get("picard_iters", 1)) > 1:
+        a.append(8 * nn)
+    a += [16 * TRACE_CAP, state_bytes, ne]
+    if cfg.get("h_conv", 0.0) > 0 or cfg.get("emissivity", 0.0) > 0:
+        a.append(8 * nx * ny)
+        if prec == 1:
+            a.append(4 * nx * ny)
+    return a
 
 
 def job_bytes(cfg):
-    """Device memory a job holds while resident (both levels, state map)."""
-    prec = int(cfg.get("precision", 0))
+    """Device memory a job holds while resident: every array of both levels
+    (the fine level's states in the plate-wide map), the reduction slots and
+    the small per-problem words, each rounded up to ALLOC_ROUND."""
     r = cfg["r"]
-    nf = workloads.fine_nodes(cfg)
-    ef = cfg["pNXc"] * cfg["pNYc"] * cfg["pNZc"] * r ** 3
-    nc = (cfg["NXc"] + 1) * (cfg["NYc"] + 1) * (cfg["NZc"] + 1)
-    ec = cfg["NXc"] * cfg["NYc"] * cfg["NZc"]
-    state_map = cfg["NXc"] * r * cfg["NYc"] * r * cfg["pNZc"] * r
-    return (nf + nc) * BYTES_PER_NODE[prec] + (ef + ec) * BYTES_PER_ELEM[prec] + state_map + nc + (1 << 20)
+    fx, fy, fz = cfg["pNXc"] * r, cfg["pNYc"] * r, cfg["pNZc"] * r
+    cx, cy, cz = cfg["NXc"], cfg["NYc"], cfg["NZc"]
+    arrays = _level_arrays(cx + 1, cy + 1, cz + 1, cx, cy, cz, cx * cy * cz, cfg, True)
+    arrays += _level_arrays(fx + 1, fy + 1, fz + 1, fx, fy, fz, cx * r * cy * r * fz, cfg, False)
+    grid = 2048  # reduction width: at most the grid cap
+    arrays += [16, 8 * RS_N * grid, 4 * RS_N * grid, 256, 16]
+    return sum((b + ALLOC_ROUND - 1) // ALLOC_ROUND * ALLOC_ROUND for b in arrays)
 
 
 class Server:

@@ -50,7 +50,7 @@ class tl_config(C.Structure):
         ("latent", C.c_double), ("T_solidus", C.c_double), ("T_liquidus", C.c_double),
         ("pc_sharpness", C.c_double), ("picard_iters", C.c_int),
         ("h_conv", C.c_double), ("emissivity", C.c_double), ("T_amb", C.c_double),
-        ("barrier_timeout", C.c_double),
+        ("barrier_timeout", C.c_double), ("autotune", C.c_int),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
@@ -97,7 +97,7 @@ EXPORTS = [
     "tl_sync", "tl_node_count", "tl_get_temperature", "tl_get_state", "tl_get_stats",
     "tl_destroy_problem", "tl_status_string", "tl_box_step_noalloc", "tl_trace_last_solve",
     "tl_batch_create", "tl_batch_add", "tl_batch_round", "tl_batch_poll", "tl_batch_info", "tl_batch_destroy",
-    "tl_checkpoint_size", "tl_checkpoint_save", "tl_checkpoint_load",
+    "tl_checkpoint_size", "tl_checkpoint_save", "tl_checkpoint_load", "tl_get_tiling",
 ]
 
 _lib = None
@@ -154,6 +154,8 @@ def load(path=LIB_PATH):
     lib.tl_batch_poll.restype = C.c_int
     lib.tl_batch_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
     lib.tl_batch_info.restype = C.c_int
+    lib.tl_get_tiling.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
+    lib.tl_get_tiling.restype = C.c_int
     lib.tl_batch_destroy.argtypes = [P]
     lib.tl_batch_destroy.restype = None
     _lib = lib
@@ -343,6 +345,13 @@ class Problem:
         _check(st, "tl_get_stats")
         return {name: (list(getattr(s, name)) if name == "origin" else getattr(s, name))
                 for name, _ in tl_stats._fields_}
+
+    def tiling(self, level):
+        """The level's tilings (see tl_get_tiling)."""
+        out = (C.c_int32 * 11)()
+        _check(load().tl_get_tiling(self.h, int(level), out), "tl_get_tiling")
+        v = list(out)
+        return {"element": v[0:3], "wide": v[3:6], "precond": v[6:9], "grid": v[9], "tuned": bool(v[10])}
 
     def trace(self, level):
         st, ev = tl_trace_last_solve(self.h, level)

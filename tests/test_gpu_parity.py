@@ -523,3 +523,22 @@ def test_top_surface_losses_in_a_batch_equal_alone():
         tol = 1e-6 if c.get("precision", 0) == tl.TL_FP32_REFINED else 1e-9
         assert rel(p.temperature(tl.TL_FINE)[0], a) <= tol
         p.close()
+
+
+def test_autotuned_tilings_keep_the_results():
+    """The autotuner only changes how blocks walk the mesh: an autotuned
+    problem matches the cost-model one (the FP32 summation order may differ:
+    precision form within 1e-8 of each other, FP64 within 1e-10), reports its
+    picks as tuned, and a second problem of the same shape reuses them."""
+    for prec, tol in ((tl.TL_FP32_REFINED, 1e-8), (tl.TL_FP64, 1e-10)):
+        base = workloads.workload("multitrack_10mm", precision=prec, tol=1e-10 if prec else 1e-12)
+        out, picks = [], []
+        for at in (0, 1, 1):
+            p = tl.Problem(dict(base, autotune=at))
+            picks.append(p.tiling(tl.TL_FINE))
+            p.macro_steps(3)
+            out.append((p.temperature(tl.TL_FINE)[0], p.state(tl.TL_FINE)))
+            p.close()
+        assert not picks[0]["tuned"] and picks[1]["tuned"] and picks[1] == picks[2]
+        assert rel(out[1][0], out[0][0]) <= tol and np.array_equal(out[1][1], out[0][1])
+        assert np.array_equal(out[1][0], out[2][0])

@@ -96,3 +96,24 @@ def test_failing_job_is_evicted_and_the_others_are_undisturbed():
         tol = 1e-6 if cfg.get("precision", 0) == tl.TL_FP32_REFINED else 1e-9
         rel = np.linalg.norm(got[k] - alone[idx]) / np.linalg.norm(alone[idx])
         assert rel <= tol, (k, rel)
+
+
+@pytest.mark.parametrize("name,precision", [("multitrack_10mm", 0), ("multitrack_10mm", 1), ("multitrack_20mm", 0),
+                                            ("multitrack_20mm", 1)])
+def test_admission_model_covers_the_real_allocation(name, precision):
+    """serve.job_bytes (the admission budget's estimate) against the device
+    memory a problem takes (free memory before and after tl_create_problem,
+    the library allocating with cudaMalloc): never below it, at most 25 %
+    above."""
+    torch = pytest.importorskip("torch")
+    cfg = workloads.workload(name, precision=precision, tol=1e-10 if precision else 1e-12)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    p = tl.Problem(cfg)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    p.close()
+    used = free0 - free1
+    est = serve.job_bytes(cfg)
+    assert used > 0
+    assert used <= est <= 1.25 * used, (used, est, est / used)

@@ -213,3 +213,116 @@ def test_error_saw_tooth_within_macro_steps():
         if n + 1 < nmacro:
             assert fine[n + 1][0] < e[-1], (n, e, fine[n + 1])
     assert all(c < 0.05 * p for c, p in zip(corr, pred)), (corr, pred)
+
+
+# ---- flux-jump coupling (Section 3, Eqs. deltaDef and globalPbmAlternate) ----
+
+def test_flux_jump_vanishes_when_the_conductivities_agree():
+    """With one conductivity law on both levels and no powder (kappa_+ ==
+    kappa_- everywhere) the interface term is zero, so the global problem of
+    Eq. globalPbmAlternate is the plain coarse heat equation: T+ equals the
+    single-level coarse solve for any patch position (the heat capacity may
+    still depend on T)."""
+    cfg = W.workload("single_track_tiny", interface_coupling=1, coarse_source=1, k1=0.0, powder_depth=0.0)
+    o = TL.TwoLevel(cfg)
+    sl = TL.SingleLevel(cfg, cfg["NXc"], cfg["NYc"], cfg["NZc"], cfg["dt_coarse"])
+    moved = 0
+    for n in range(12):
+        before = o.origin
+        o.macro_step()
+        moved += before != o.origin
+        sl.step()
+        assert not o.interface_load().any()
+        assert np.linalg.norm(o.Tc - sl.T) / np.linalg.norm(sl.T) < 1e-12, n
+    assert moved >= 2
+
+
+def test_flux_jump_load_of_a_linear_field():
+    """T- = T0 + a x + b y + c z has dT-/dn = +-a, +-b, -c on the patch faces;
+    with constant kappa_- and kappa_+ each coarse node interior to a face
+    plane gets (kappa_+ - kappa_-) (n . grad T) h1 h2 (the integral of its hat
+    over the plane), and the loads of the x+ face plane sum to
+    (kappa_+ - kappa_-) a times its area."""
+    cfg = W.workload("single_track_tiny", interface_coupling=1)
+    o = TL.TwoLevel(cfg, energy=False)
+    o.origin = (5, 2, 2)                     # every side and the bottom immersed
+    assert o.interface_faces() == (True, True, True, True, True)
+    x, y, z = o.fine_mesh().node_xyz()
+    a, b, c = 3.0e5, -1.0e5, 2.0e5
+    T = 293.0 + a * x + b * y + c * z
+    km, kp = 2.0, 5.0
+    G = o.interface_load(Tf=T, k_fine=km, k_coarse=kp)
+    C = o.coarse
+    hx, hy, hz = o.hc
+    (i0, j0, k0), (pnx, pny, pnz) = o.origin, o.pN
+    I, J, K = C.node_ijk()
+    jump = kp - km
+    xp = (I == i0 + pnx) & (J > j0) & (J < j0 + pny) & (K > k0) & (K < k0 + pnz)
+    ym = (J == j0) & (I > i0) & (I < i0 + pnx) & (K > k0) & (K < k0 + pnz)
+    zb = (K == k0) & (I > i0) & (I < i0 + pnx) & (J > j0) & (J < j0 + pny)
+    assert np.allclose(G[xp], jump * a * hy * hz, rtol=1e-12, atol=0)
+    assert np.allclose(G[ym], jump * (-b) * hx * hz, rtol=1e-12, atol=0)
+    assert np.allclose(G[zb], jump * (-c) * hx * hy, rtol=1e-12, atol=0)
+    plane = (I == i0 + pnx) & (J >= j0) & (J <= j0 + pny) & (K >= k0) & (K <= k0 + pnz)
+    # edge nodes of the plane also carry the y / z faces' loads: take the x+ part alone
+    Gx = o.interface_load(Tf=T, k_fine=km, k_coarse=kp) - o.interface_load(Tf=293.0 + b * y + c * z, k_fine=km,
+                                                                             k_coarse=kp)
+    assert abs(Gx[plane].sum() - jump * a * (pny * hy) * (pnz * hz)) <= 1e-12 * abs(jump * a * pny * hy * pnz * hz)
+
+
+def test_flux_jump_load_against_fine_quadrature():
+    """A random fine field and random conductivities: the 2 x 2 Gauss face
+    integrals equal an independent 5 x 5 Gauss evaluation of
+    int_gamma (kappa_+ - kappa_-) dT-/dn phi_I dA, with dT-/dn taken by a
+    one-sided difference of the trilinear interpolant (exact inside an
+    element) and phi_I from the trilinear interpolant of a unit coarse field."""
+    rng = np.random.default_rng(3)
+    cfg = W.workload("single_track_tiny", interface_coupling=1, pNXc=3, pNYc=2, pNZc=2, r=2)
+    o = TL.TwoLevel(cfg, energy=False)
+    o.origin = (4, 3, 2)
+    mesh, C = o.fine_mesh(), o.coarse
+    T = rng.uniform(300.0, 2000.0, mesh.nnode)
+    kf = rng.uniform(0.05, 20.0, mesh.nelem)
+    kc = rng.uniform(0.05, 20.0, C.nelem)
+    G = o.interface_load(Tf=T, k_fine=kf, k_coarse=kc)
+    xg, wg = np.polynomial.legendre.leggauss(5)
+    xg, wg = 0.5 * (xg + 1.0), 0.5 * wg
+    hf, hc = o.hf, o.hc
+    org = np.array([o.origin[d] * hc[d] for d in range(3)])
+    ext = np.array([o.pN[d] * hc[d] for d in range(3)])
+    eps = 1e-3
+    want = np.zeros(C.nnode)
+    for d, side in ((0, 0), (0, 1), (1, 0), (1, 1), (2, 0)):
+        a1, a2 = [ax for ax in range(3) if ax != d]
+        n1, n2 = int(round(ext[a1] / hf[a1])), int(round(ext[a2] / hf[a2]))
+        for e1 in range(n1):
+            for e2 in range(n2):
+                for q1, w1 in zip(xg, wg):
+                    for q2, w2 in zip(xg, wg):
+                        p = org.copy()
+                        p[d] += ext[d] if side else 0.0
+                        p[a1] += (e1 + q1) * hf[a1]
+                        p[a2] += (e2 + q2) * hf[a2]
+                        inward = -1.0 if side else 1.0
+                        pin = p.copy()
+                        pin[d] += inward * eps * hf[d]
+                        local = fem.BoxMesh(*o.nf, *hf, origin=tuple(org))
+                        t0 = fem.trilinear(local, T, *[np.array([v]) for v in p])[0]
+                        t1 = fem.trilinear(local, T, *[np.array([v]) for v in pin])[0]
+                        dTdn = (t0 - t1) / (eps * hf[d])
+                        ie = [min(int((p[ax] - org[ax]) / hf[ax]), o.nf[ax] - 1) for ax in range(3)]
+                        ie[d] = 0 if side == 0 else o.nf[d] - 1
+                        km = kf[ie[0] + o.nf[0] * (ie[1] + o.nf[1] * ie[2])]
+                        ce = [int(p[ax] / hc[ax]) for ax in range(3)]
+                        ce[d] = o.origin[d] + (o.pN[d] if side else -1)
+                        kp = kc[ce[0] + C.nx * (ce[1] + C.ny * ce[2])]
+                        wgt = (kp - km) * dTdn * w1 * w2 * hf[a1] * hf[a2]
+                        # hats of the eight nodes of the coarse cell holding p: the
+                        # interpolant of a unit field at each
+                        base = [int(np.floor(p[ax] / hc[ax] + 1e-12)) for ax in range(3)]
+                        for cand in range(8):
+                            nid = C.node_id(*[base[ax] + ((cand >> ax) & 1) for ax in range(3)])
+                            e = np.zeros(C.nnode)
+                            e[nid] = 1.0
+                            want[nid] += wgt * fem.trilinear(C, e, *[np.array([v]) for v in p])[0]
+    assert np.allclose(G, want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
