@@ -159,6 +159,18 @@ typedef struct {
    * results then depend on the pick only through the FP32 summation order);
    * 0: cost models only. */
   int autotune;
+  /* how the correction step receives the fine solution: 0 = restriction
+   * (the fine values injected at the coarse nodes that coincide with free
+   * fine nodes, held as Dirichlet data of the coarse step); 1 = the flux
+   * jump of the alternate global problem (Section 3, Eq. globalPbmAlternate):
+   * tl_restrict forms G_I = int_gamma (kappa_+ - kappa_-) dT-/dn phi_I dA over
+   * the patch faces immersed in the plate from the fine field at the end of
+   * the macro step (kappa_- the fine element's conductivity there, kappa_+
+   * the coarse element's just outside the patch), and the correction solves
+   * the coarse step with only the plate's own boundary conditions and G added
+   * to its load.  1 requires coupling_sweeps <= 1 and keeps the problem out
+   * of batches. */
+  int interface_coupling;
   void* stream;           /* cudaStream_t to run on; NULL = legacy default     */
   /* optional device allocator: both NULL -> cudaMalloc / cudaFree; blocks
    * must be 16-byte aligned (else tl_create_problem returns TL_EINVAL) */
@@ -214,8 +226,9 @@ tl_status tl_coarse_step(tl_problem* p, tl_phase phase);
 tl_status tl_fine_substeps(tl_problem* p, int nsub);
 
 /* Inject the fine temperature into the coarse nodes that coincide with free
- * fine nodes (Algorithm 1, correction input).  Errors: TL_ESTATE unless all
- * m micro steps of the macro step are done. */
+ * fine nodes (Algorithm 1, correction input), or, with interface_coupling 1,
+ * form the interface load of the flux-jump coupling.  Errors: TL_ESTATE
+ * unless all m micro steps of the macro step are done. */
 tl_status tl_restrict(tl_problem* p);
 
 /* Convenience: nmacro full macro steps (predict, m micro steps, restrict,
@@ -294,8 +307,9 @@ tl_status tl_batch_create(void* stream, int launches_per_round, int max_jobs, tl
 
 /* Add a problem for macro_steps more macro steps; *id_out gets its job id.
  * Errors: TL_ESTATE (not between macro steps), TL_ENOMEM (batch full),
- * TL_EINVAL (a problem with coupling_sweeps > 1 or picard_iters > 1: batched
- * sequences run one solve per step and the one-pass correction). */
+ * TL_EINVAL (a problem with coupling_sweeps > 1, picard_iters > 1 or
+ * interface_coupling 1: batched sequences run one solve per step and the
+ * one-pass restriction correction). */
 tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out);
 
 /* Enqueue one round (asynchronous after a synchronisation with the previous

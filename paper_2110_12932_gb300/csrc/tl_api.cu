@@ -615,6 +615,13 @@ void build_coarse_args(tl_problem* p, bool correct, bool fused_inject, SolveArgs
   a.energy = correct ? c.energy : 0;
   a.update_state = correct ? 1 : 0;
   a.level = 0;
+  if (correct && c.interface_coupling == 1) {
+    // flux-jump coupling: the plate's own boundary conditions and the
+    // interface load the restriction step formed (in the injection buffer)
+    a.dir.box[0] = 1; a.dir.box[1] = 0; a.dir.box[2] = 1; a.dir.box[3] = 0; a.dir.box[4] = 1; a.dir.box[5] = 0;
+    a.dv.kind = 1;
+    a.Fx = L.inj;
+  }
 }
 
 tl_status coarse_solve(tl_problem* p, bool correct) {
@@ -684,6 +691,9 @@ tl_status validate(const tl_config* c) {
   if (c->precond < 0 || c->precond > 2) return TL_EINVAL;
   if ((c->alloc == nullptr) != (c->free == nullptr)) return TL_EINVAL;
   if (!(c->barrier_timeout >= 0) || c->barrier_timeout > 60.0) return TL_EINVAL;
+  if (c->autotune < 0 || c->autotune > 1) return TL_EINVAL;
+  if (c->interface_coupling < 0 || c->interface_coupling > 1) return TL_EINVAL;
+  if (c->interface_coupling == 1 && c->coupling_sweeps > 1) return TL_EINVAL;
   if (!(c->h_conv >= 0) || !(c->emissivity >= 0) || c->emissivity > 1.0) return TL_EINVAL;
   if ((c->h_conv > 0 || c->emissivity > 0) && !(c->T_amb > 0)) return TL_EINVAL;
   // the surface term rides on the apply of the stored CG direction, which the
@@ -776,6 +786,41 @@ void next_batched_solve(tl_problem* p, SolveArgs& a, long long* weight) {
   *weight = (long long)p->C.g.nx * p->C.g.ny * p->C.g.nz;
 }
 
+
+// Flux-jump coupling: the interface load of the fine field at the end of the
+// macro step into the coarse level's `inj` buffer (cleared first).
+tl_status launch_interface_load(tl_problem* p) {
+  const tl_config& c = p->cfg;
+  Level& C = p->C;
+  const size_t nc = (size_t)C.g.nnx * C.g.nny * C.g.nnz;
+  cudaError_t e = cudaMemsetAsync(C.inj, 0, nc * sizeof(double), p->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  IfaceSpec sp{};
+  sp.fg = p->Fi.g;
+  sp.cg = C.g;
+  sp.oi = p->oi;
+  sp.oj = p->oj;
+  sp.ok = p->ok;
+  sp.r = c.r;
+  sp.pnx = c.pNXc;
+  sp.pny = c.pNYc;
+  sp.pnz = c.pNZc;
+  const int f = fine_dir_faces(p);
+  sp.faces = (f & 15) | (p->ok > 0 ? 16 : 0);
+  sp.Tf = p->Fi.T;
+  sp.Tc = C.T;
+  sp.st_f = p->Fi.state;
+  sp.st_sx = p->Fi.st_sx;
+  sp.st_sy = p->Fi.st_sy;
+  sp.st_c = C.state;
+  sp.mat = Material{c.rho, c.c0, c.c1, c.k0, c.k1, c.Tref, c.powder_factor, c.T_melt,
+                    c.latent, c.pc_sharpness, 0.5 * (c.T_solidus + c.T_liquidus)};
+  sp.G = C.inj;
+  const long long nb = (long long)(c.pNXc + 1) * (c.pNYc + 1) * (c.NZc - p->ok + 1);
+  interface_load_kernel<<<(int)std::min<long long>(1024, (nb + 127) / 128), 128, 0, p->stream>>>(sp);
+  p->launches++;
+  return cuda_status(cudaGetLastError());
+}
 
 // Injection of the fine field at the coarse nodes that coincide with free
 // fine nodes (into the coarse level's `inj`).
@@ -1256,7 +1301,7 @@ tl_status tl_fine_substeps(tl_problem* p, int nsub) {
 tl_status tl_restrict(tl_problem* p) {
   if (!p) return TL_EINVAL;
   if (p->phase != IN_SUBSTEPS || p->sub != p->cfg.m) return TL_ESTATE;
-  tl_status s = launch_restrict(p);
+  tl_status s = p->cfg.interface_coupling == 1 ? launch_interface_load(p) : launch_restrict(p);
   if (s != TL_OK) return s;
   p->phase = NEED_CORRECT;
   return TL_OK;
@@ -1363,7 +1408,8 @@ static uint64_t config_hash(const tl_problem* p) {
                       c.emissivity, c.T_amb};
   const int32_t i[] = {c.NXc, c.NYc, c.NZc, c.pNXc, c.pNYc, c.pNZc, c.r, c.m, c.coarse_source,
                        c.bc_weight_literal, c.energy, (int32_t)c.precision, c.max_iter, c.inner_tiles,
-                       c.coupling_sweeps, c.precond, c.picard_iters, (int32_t)p->tracks.size()};
+                       c.coupling_sweeps, c.precond, c.picard_iters, c.autotune, c.interface_coupling,
+                       (int32_t)p->tracks.size()};
   add(d, sizeof d);
   add(i, sizeof i);
   for (const tl_track& k : p->tracks) {
@@ -1594,6 +1640,7 @@ tl_status tl_batch_add(tl_batch* b, tl_problem* p, int macro_steps, int* id_out)
   if (!b || !p || macro_steps < 0 || !id_out) return TL_EINVAL;
   if (p->cfg.coupling_sweeps > 1) return TL_EINVAL;  // batched sequences use the one-pass correction
   if (p->cfg.picard_iters > 1) return TL_EINVAL;     // ... and one solve per step
+  if (p->cfg.interface_coupling != 0) return TL_EINVAL;  // ... and the restriction coupling
   if (p->phase != NEED_PREDICT) return TL_ESTATE;  // join only between macro steps
   int active = 0;
   for (const auto& j : b->jobs) active += j.active ? 1 : 0;

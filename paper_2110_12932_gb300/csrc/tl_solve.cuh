@@ -355,6 +355,7 @@ struct SolveArgs {
   float* dinv32;
   float* sk32;   // refined path: FP32 s_e, k_e ([2][nelem]); eigenvalues rebuilt in registers
   double* F;     // top-face load, (nx+1)(ny+1)
+  const double* Fx;  // extra nodal load (the flux-jump coupling's interface load), or NULL
   double* G;     // load factor tables, MAXRECT (nnx + nny)
   uint8_t* state;
   uint8_t* st_new;  // the new element states (one per element, patch order) until the commit
@@ -637,6 +638,21 @@ __device__ inline TileBox tile_box(const Grid3& g, const Tiling& t, int tile) {
   const int tiy = trem / t.ntx, tix = trem - tiy * t.ntx;
   const int ie0 = tix * t.ex, je0 = tiy * t.ey;
   return TileBox{ie0, je0, min(t.ex, g.nx - ie0), min(t.ey, g.ny - je0), min(tiz * t.ez + t.ez, g.nz) == g.nz};
+}
+
+// Whether the node window of a tile (its elements' nodes) holds a node of one
+// of the Dirichlet sets.
+__device__ inline bool tile_touches_dirichlet(const Grid3& g, const Tiling& t, int tile, const DirSpec& d) {
+  const int txy = t.ntx * t.nty;
+  const int tiz = tile / txy, trem = tile - tiz * txy;
+  const int tiy = trem / t.ntx, tix = trem - tiy * t.ntx;
+  const int i0 = tix * t.ex, j0 = tiy * t.ey, k0 = tiz * t.ez;
+  const int i1 = min(i0 + t.ex, g.nx), j1 = min(j0 + t.ey, g.ny), k1 = min(k0 + t.ez, g.nz);
+  if (((d.faces & 1) && i0 == 0) || ((d.faces & 2) && i1 == g.nx) || ((d.faces & 4) && j0 == 0) ||
+      ((d.faces & 8) && j1 == g.ny) || ((d.faces & 16) && k0 == 0))
+    return true;
+  return d.box[0] <= i1 && d.box[1] >= i0 && d.box[2] <= j1 && d.box[3] >= j0 && d.box[4] <= k1 && d.box[5] >= k0 &&
+         d.box[0] <= d.box[1] && d.box[2] <= d.box[3] && d.box[4] <= d.box[5];
 }
 
 // Top-surface transfer term of one tile (the Robin condition of Section 3.1):
@@ -2027,13 +2043,17 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     auto no_lam_fetch = [](int, double*) {};
     for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
       const TileBox tb = tile_box(g, t, tile);
-      apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.u}, fin, no_lam_fetch,
-                                      lam_full, emit1);
-      if (a.surf && tb.top) surface_partials<double>(g, tb, a.u, a.hf, a.Mfx, a.Mfy, a.q, a.X);
       apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.T_in}, fin,
-                                      no_lam_fetch, lam_k, emit2);
+                                      no_lam_fetch, lam_k, emit1);
       // the surface term of T^k too: its ambient part enters the load below
       if (a.surf && tb.top) surface_partials<double>(g, tb, a.T_in, a.hf, a.Mfx, a.Mfy, a.q, a.X);
+      // u holds the Dirichlet increments and zeros: A u is zero on tiles whose
+      // window holds no Dirichlet node
+      if (tile_touches_dirichlet(g, t, tile, a.dir)) {
+        apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.u}, fin,
+                                        no_lam_fetch, lam_full, emit2);
+        if (a.surf && tb.top) surface_partials<double>(g, tb, a.u, a.hf, a.Mfx, a.Mfy, a.q, a.X);
+      }
     }
   }
   if (!grid_sync(a.bar, vg)) return;
@@ -2054,8 +2074,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
           Fa = a.T_amb * hs * (0.25 * g.hx * g.hy);
         }
       }
+      const double Fxn = a.Fx ? __ldcg(a.Fx + n) : 0.0;
       if (!is_dir(g, a.dir, i, j, k))
-        rr = (Fn + Fa) - gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
+        rr = ((Fn + Fa) + Fxn) - gather_partials((const double*)a.q, (const double*)a.X, nn, n,
+                                                 low_faces(g, t, i, ly, lz));
       a.r[n] = rr;
       v[0] += rr * rr * __ldcg(a.dinv + n);
       v[1] += rr * rr;
@@ -2285,6 +2307,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     tr.mark(TR_END_ELEMS);
     if (a.energy) {
       for (int n = gtid; n < S; n += gstride) v[1] += a.dt * __ldcg(a.F + n);
+      if (a.Fx)  // the interface load counts as heat through the boundary
+        for (int n = gtid; n < nn; n += gstride) v[2] += a.dt * __ldcg(a.Fx + n);
       if (a.surf) {  // heat lost through the top: dt 1^T H (T^{k+1} - T_amb), face by face
         const int top = S * g.nz;
         for (int f = gtid; f < g.nx * g.ny; f += gstride) {
@@ -2460,6 +2484,101 @@ __global__ void restrict_kernel(Grid3 fg, Grid3 cg, const double* __restrict__ T
        n += (long long)gridDim.x * blockDim.x) {
     int I = bi0 + (int)(n % bx), J = bj0 + (int)((n / bx) % by), K = bk0 + (int)(n / ((long long)bx * by));
     inj[node_id(cg, I, J, K)] = Tf[node_id(fg, (I - oi) * r, (J - oj) * r, (K - ok) * r)];
+  }
+}
+
+// Flux-jump coupling (Section 3, Eqs. deltaDef and globalPbmAlternate): the
+// interface load G_I = int_gamma (kappa_+ - kappa_-) dT-/dn phi_I dA of every
+// coarse node of the patch's bounding box [oi, oi + pnx] x [oj, oj + pny] x
+// [ok, nz] (zero elsewhere: the caller clears G).  gamma = the patch faces
+// immersed in the plate (faces bit 0 x-, 1 x+, 2 y-, 3 y+, 4 bottom); n the
+// local domain's outward normal; dT-/dn the normal derivative of the fine
+// trilinear field (T- = Tf, at the end of the macro step) inside the fine
+// element next to the face; kappa_- that element's conductivity (element mean
+// of Tf, fine state after the step), kappa_+ the conductivity of the coarse
+// element just outside the patch (element mean of the coarse field Tc at t_n,
+// coarse state).  Each fine face's integrand is a product of two bilinear
+// functions, integrated by 2 x 2 Gauss points; one thread per coarse node
+// sums its faces in a fixed order.
+struct IfaceSpec {
+  Grid3 fg, cg;
+  int oi, oj, ok, r, pnx, pny, pnz, faces;
+  const double* Tf;
+  const double* Tc;
+  const uint8_t* st_f;  // plate-wide fine state map, (sx, sy) plane strides
+  int st_sx, st_sy;
+  const uint8_t* st_c;
+  Material mat;
+  double* G;
+};
+
+__device__ inline double iface_k(const Material& m, double Tb, uint8_t st) {
+  double k = m.k0 + m.k1 * (Tb - m.Tref);
+  return st == POWDER ? m.powder_factor * k : k;
+}
+
+__global__ void interface_load_kernel(IfaceSpec s) {
+  const int bx = s.pnx + 1, by = s.pny + 1, bz = s.cg.nz - s.ok + 1;
+  const long long nb = (long long)bx * by * bz;
+  const double gq[2] = {0.21132486540518711775, 0.78867513459481288225};  // (1 -+ 1/sqrt 3) / 2
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nb;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int ci[3] = {s.oi + (int)(q % bx), s.oj + (int)((q / bx) % by), s.ok + (int)(q / ((long long)bx * by))};
+    const int o[3] = {s.oi, s.oj, s.ok}, pn[3] = {s.pnx, s.pny, s.pnz};
+    const int nf[3] = {s.fg.nx, s.fg.ny, s.fg.nz};
+    const double hf[3] = {s.fg.hx, s.fg.hy, s.fg.hz};
+    double Gsum = 0.0;
+    for (int plane = 0; plane < 5; ++plane) {
+      if (!((s.faces >> plane) & 1)) continue;
+      const int d = plane / 2, side = plane & 1;  // plane 4: z, low side
+      const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      if (ci[d] != o[d] + (side ? pn[d] : 0)) continue;
+      const int lo1 = o[a1], hi1 = o[a1] + pn[a1], lo2 = o[a2], hi2 = o[a2] + pn[a2];
+      const double sign = side ? 1.0 : -1.0;
+      const int ed = side ? nf[d] - 1 : 0;                // fine element layer next to the plane
+      for (int c2 = max(ci[a2] - 1, lo2); c2 <= min(ci[a2], hi2 - 1); ++c2)
+        for (int c1 = max(ci[a1] - 1, lo1); c1 <= min(ci[a1], hi1 - 1); ++c1) {
+          // the coarse element outside the patch across this coarse face
+          int ce[3];
+          ce[d] = side ? o[d] + pn[d] : o[d] - 1;
+          ce[a1] = c1;
+          ce[a2] = c2;
+          const double Tcb = elem_mean(s.Tc, s.cg, ce[0], ce[1], ce[2]);
+          const double kp = iface_k(s.mat, Tcb, s.st_c[ce[0] + s.cg.nx * (ce[1] + s.cg.ny * ce[2])]);
+          for (int f2 = 0; f2 < s.r; ++f2)
+            for (int f1 = 0; f1 < s.r; ++f1) {
+              int fe[3];
+              fe[d] = ed;
+              fe[a1] = (c1 - o[a1]) * s.r + f1;
+              fe[a2] = (c2 - o[a2]) * s.r + f2;
+              const double Tfb = elem_mean(s.Tf, s.fg, fe[0], fe[1], fe[2]);
+              const uint8_t stf = s.st_f[(size_t)s.st_sx * s.st_sy * fe[2] + (size_t)s.st_sx * (fe[1] + o[1] * s.r) +
+                                         fe[0] + o[0] * s.r];
+              const double jump = kp - iface_k(s.mat, Tfb, stf);
+              for (int g2 = 0; g2 < 2; ++g2)
+                for (int g1 = 0; g1 < 2; ++g1) {
+                  const double xi1 = gq[g1], xi2 = gq[g2];
+                  double grad = 0.0;
+                  for (int b2 = 0; b2 < 2; ++b2)
+                    for (int b1 = 0; b1 < 2; ++b1) {
+                      const double w = (b1 ? xi1 : 1.0 - xi1) * (b2 ? xi2 : 1.0 - xi2);
+                      int lo[3], hi[3];
+                      lo[d] = fe[d];
+                      hi[d] = fe[d] + 1;
+                      lo[a1] = hi[a1] = fe[a1] + b1;
+                      lo[a2] = hi[a2] = fe[a2] + b2;
+                      grad += w * (__ldcg(s.Tf + node_id(s.fg, hi[0], hi[1], hi[2])) -
+                                   __ldcg(s.Tf + node_id(s.fg, lo[0], lo[1], lo[2]))) / hf[d];
+                    }
+                  // the coarse hat of node ci on this coarse face, bilinear in the plane
+                  const double t1 = (f1 + xi1) / s.r, t2 = (f2 + xi2) / s.r;
+                  const double phi = (c1 == ci[a1] - 1 ? t1 : 1.0 - t1) * (c2 == ci[a2] - 1 ? t2 : 1.0 - t2);
+                  Gsum += jump * (sign * grad) * 0.25 * hf[a1] * hf[a2] * phi;
+                }
+            }
+        }
+    }
+    s.G[node_id(s.cg, ci[0], ci[1], ci[2])] = Gsum;
   }
 }
 

@@ -25,8 +25,11 @@ import numpy as np
 
 from . import tl, workloads
 
-# Allocation granularity allowance: each device allocation is rounded up to
-# this many bytes in the estimate (the CUDA allocator aligns blocks).
+# Allocation granularity of the estimate: the CUDA allocator gives blocks of
+# more than 1 MiB whole 2 MiB pages and packs smaller blocks (512-byte
+# aligned) into shared 2 MiB pages, one page allowed per problem.
+ALLOC_PAGE = 2 << 20
+ALLOC_SMALL = 1 << 20
 ALLOC_ROUND = 512
 XB = 7        # exchange planes per partial buffer
 RS_N = 9      # reduction rows
@@ -63,15 +66,21 @@ def _level_arrays(nnx, nny, nnz, nx, ny, nz, state_bytes, cfg, coarse):
 def job_bytes(cfg):
     """Device memory a job holds while resident: every array of both levels
     (the fine level's states in the plate-wide map), the reduction slots and
-    the small per-problem words, each rounded up to ALLOC_ROUND."""
+    the small per-problem words, with the allocator's granularity (blocks
+    above ALLOC_SMALL in whole ALLOC_PAGE pages, smaller ones rounded to
+    ALLOC_ROUND, plus one page for them)."""
     r = cfg["r"]
     fx, fy, fz = cfg["pNXc"] * r, cfg["pNYc"] * r, cfg["pNZc"] * r
     cx, cy, cz = cfg["NXc"], cfg["NYc"], cfg["NZc"]
     arrays = _level_arrays(cx + 1, cy + 1, cz + 1, cx, cy, cz, cx * cy * cz, cfg, True)
     arrays += _level_arrays(fx + 1, fy + 1, fz + 1, fx, fy, fz, cx * r * cy * r * fz, cfg, False)
     grid = 2048  # reduction width: at most the grid cap
-    arrays += [16, 8 * RS_N * grid, 4 * RS_N * grid, 256, 16]
-    return sum((b + ALLOC_ROUND - 1) // ALLOC_ROUND * ALLOC_ROUND for b in arrays)
+    arrays += [16, 8 * RS_N * grid, 4 * RS_N * grid, 256, 16, 16]
+
+    def rounded(b):
+        g = ALLOC_PAGE if b > ALLOC_SMALL else ALLOC_ROUND
+        return (b + g - 1) // g * g
+    return sum(rounded(b) for b in arrays) + ALLOC_PAGE
 
 
 class Server:

@@ -50,7 +50,7 @@ class tl_config(C.Structure):
         ("latent", C.c_double), ("T_solidus", C.c_double), ("T_liquidus", C.c_double),
         ("pc_sharpness", C.c_double), ("picard_iters", C.c_int),
         ("h_conv", C.c_double), ("emissivity", C.c_double), ("T_amb", C.c_double),
-        ("barrier_timeout", C.c_double), ("autotune", C.c_int),
+        ("barrier_timeout", C.c_double), ("autotune", C.c_int), ("interface_coupling", C.c_int),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]

@@ -84,6 +84,7 @@ def _einval(lib, **over):
     dict(latent=-1.0), dict(latent=2.86e5, pc_sharpness=0.0), dict(latent=2.86e5, T_liquidus=1800.0),
     dict(h_conv=-1.0), dict(emissivity=1.5), dict(emissivity=-0.1), dict(h_conv=10.0, T_amb=0.0),
     dict(barrier_timeout=-1.0), dict(barrier_timeout=61.0), dict(h_conv=10.0, precond=1),
+    dict(interface_coupling=2), dict(interface_coupling=1, coupling_sweeps=2, coupling_tol=1e-10), dict(autotune=2),
 ])
 def test_invalid_config_is_rejected_on_host(lib, over):
     assert _einval(lib, **over) == tl.TL_EINVAL

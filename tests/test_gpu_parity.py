@@ -360,7 +360,8 @@ def test_coupled_correction_multitrack_first_macro_step():
     prob.close()
 
 
-@pytest.mark.parametrize("over", [dict(coupling_sweeps=3), dict(picard_iters=3, latent=2.86e5)])
+@pytest.mark.parametrize("over", [dict(coupling_sweeps=3), dict(picard_iters=3, latent=2.86e5),
+                                  dict(interface_coupling=1)])
 def test_coupled_and_picard_problems_stay_out_of_batches(over):
     cfg = workloads.workload("single_track_tiny", **over)
     p = tl.Problem(cfg)
@@ -542,3 +543,51 @@ def test_autotuned_tilings_keep_the_results():
         assert not picks[0]["tuned"] and picks[1]["tuned"] and picks[1] == picks[2]
         assert rel(out[1][0], out[0][0]) <= tol and np.array_equal(out[1][1], out[0][1])
         assert np.array_equal(out[1][0], out[2][0])
+
+
+# ---- flux-jump coupling (Section 3, Eq. globalPbmAlternate) -------------------
+
+@pytest.mark.parametrize("over", [dict(), dict(h_conv=1e4, emissivity=0.8), dict(coarse_source=1, r=2, m=3)])
+def test_flux_jump_coupling_against_oracle(over):
+    """The correction solves the global problem with the interface load
+    (kappa_+ - kappa_-) dT-/dn on the immersed patch faces instead of the
+    injected values: fields and states against the oracle every 4 macro
+    steps (the patch starts at the plate's edge, where its x- face is not
+    immersed), and the coarse energy account with the interface heat in the
+    flux term."""
+    cfg = workloads.workload("single_track_tiny", interface_coupling=1, **over)
+    prob, ref, _ = run_both(cfg, 16, check_every=4)
+    st = prob.stats()
+    s_, l_, f_, x_ = (st[f"energy_coarse_{k}"] for k in ("stored", "laser", "flux", "loss"))
+    assert abs(s_ - l_ - f_ + x_) <= 1e-9 * max(abs(s_), abs(l_))
+    assert abs(f_ - ref.energy["coarse_flux"]) <= 1e-8 * max(abs(f_), abs(l_))
+    iface = sum(e.get("interface", 0.0) for lvl, e in ref.step_energy if lvl == "coarse")
+    assert abs(iface) > 1e-3 * abs(l_)  # the interface term matters
+    prob.close()
+
+
+def test_flux_jump_refined_against_oracle():
+    cfg = workloads.workload("single_track_tiny", interface_coupling=1, precision=tl.TL_FP32_REFINED, tol=1e-10,
+                             tol_inner=1e-5)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    for _ in range(3):
+        prob.macro_steps(5)
+        ref.run(5)
+        assert rel(prob.temperature(tl.TL_FINE)[0], ref.Tf) <= REFINED_TOL
+        assert rel(prob.temperature(tl.TL_COARSE)[0], ref.Tc) <= REFINED_TOL
+        assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+    prob.close()
+
+
+def test_flux_jump_with_agreeing_conductivities_is_the_single_level_coarse_solve():
+    """One conductivity law and no powder: the interface load vanishes and the
+    coarse field is the single-level coarse solve (Gaussian source)."""
+    cfg = workloads.workload("single_track_tiny", interface_coupling=1, coarse_source=1, k1=0.0, powder_depth=0.0)
+    prob = tl.Problem(cfg)
+    sl = TL.SingleLevel(cfg, cfg["NXc"], cfg["NYc"], cfg["NZc"], cfg["dt_coarse"])
+    for n in range(10):
+        prob.macro_steps(1)
+        sl.step()
+        assert rel(prob.temperature(tl.TL_COARSE)[0], sl.T) <= 1e-9, n
+    prob.close()

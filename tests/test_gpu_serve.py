@@ -102,18 +102,20 @@ def test_failing_job_is_evicted_and_the_others_are_undisturbed():
                                             ("multitrack_20mm", 1)])
 def test_admission_model_covers_the_real_allocation(name, precision):
     """serve.job_bytes (the admission budget's estimate) against the device
-    memory a problem takes (free memory before and after tl_create_problem,
-    the library allocating with cudaMalloc): never below it, at most 25 %
+    memory problems take (free memory before and after creating two of them,
+    the library allocating with cudaMalloc; two so that the driver's page
+    packing of small blocks averages out): never below it, at most 30 %
     above."""
     torch = pytest.importorskip("torch")
     cfg = workloads.workload(name, precision=precision, tol=1e-10 if precision else 1e-12)
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
-    p = tl.Problem(cfg)
+    ps = [tl.Problem(cfg), tl.Problem(cfg)]
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
-    p.close()
-    used = free0 - free1
+    for p in ps:
+        p.close()
+    used = (free0 - free1) / 2
     est = serve.job_bytes(cfg)
     assert used > 0
-    assert used <= est <= 1.25 * used, (used, est, est / used)
+    assert used <= est <= 1.3 * used, (used, est, est / used)
