@@ -591,3 +591,26 @@ def test_flux_jump_with_agreeing_conductivities_is_the_single_level_coarse_solve
         sl.step()
         assert rel(prob.temperature(tl.TL_COARSE)[0], sl.T) <= 1e-9, n
     prob.close()
+
+
+@pytest.mark.parametrize("dims", [(11, 3, 3, 5), (7, 5, 2, 4)])
+def test_refined_wide_tiles_ragged_everywhere_against_oracle(dims):
+    """Wide inner tiles with the preconditioner fused into the apply on
+    patches ragged in x (55 or 28 elements of a 64-wide tile), in y (15 or 20
+    rows in 4-row tiles) and in z (15 or 8 layers in tiles of about nz / 8),
+    the patch touching the plate's sides in some macro steps."""
+    pnx, pny, pnz, r = dims
+    cfg = workloads.workload("single_track_tiny", precision=tl.TL_FP32_REFINED, tol=1e-10, tol_inner=1e-5,
+                             inner_tiles=2, pNXc=pnx, pNYc=pny, pNZc=pnz, r=r, m=2)
+    prob = tl.Problem(cfg)
+    ref = TL.TwoLevel(cfg, energy=False)
+    for _ in range(3):
+        prob.macro_steps(2)
+        ref.run(2)
+        Tf, org = prob.temperature(tl.TL_FINE)
+        assert tuple(org) == tuple(ref.origin)
+        assert rel(Tf, ref.Tf) <= REFINED_TOL
+        assert rel(prob.temperature(tl.TL_COARSE)[0], ref.Tc) <= REFINED_TOL
+        assert np.array_equal(prob.state(tl.TL_FINE), ref.fine_state().reshape(-1))
+    assert prob.tiling(tl.TL_FINE)["wide"][0] == 64
+    prob.close()
