@@ -417,9 +417,7 @@ def measure_probe(tl, torch):
     device phase tracer (block 0's view: a phase ends when the grid barrier
     after it is passed)."""
     peak, src = hbm_peak()
-    base = workloads.workload("multitrack_10mm", Lx=5e-3, Ly=5e-3, Lz=2.5e-3, NXc=40, NYc=40, NZc=20,
-                              pNXc=32, pNYc=32, pNZc=16, r=8, m=8,
-                              tracks=[(1e-3, 2.5e-3, 4e-3, 2.5e-3, 0.8)])
+    base = workloads.workload("probe_256")
     nn = fine_nodes(base)
     ne = fine_elems(base)
     out = {}

@@ -940,10 +940,11 @@ tl_status coupled_correct(tl_problem* p) {
 // tuner times dry solves (the level's first solve as it will run, committing
 // nothing but a scratch output, on separate barrier and status words) of a few
 // candidates per tiling, one tiling at a time: the preconditioner pass's
-// z-depth (the model's three cheapest), then the wide tiles' depth (refined
-// path on wide tiles: nz / 16 ... nz / 4) or the element tile shape (the cost
-// model's three cheapest shapes), keeping the fastest of each (the best of
-// two timed runs after one warm-up).  Picks are cached per mesh shape,
+// z-depth (the model's, half, one and a half and twice it), then on the
+// refined path the inner tile family (wide or element tiles, unless
+// inner_tiles forces one), then the wide tiles' depth (nz / 16 ... nz / 4) or
+// the element tile shape (the cost model's three cheapest shapes), keeping
+// the fastest of each (the best of two timed runs after one warm-up).  Picks are cached per mesh shape,
 // precision, preconditioner and grid cap for the life of the process.
 constexpr long long AUTOTUNE_MIN_NODES = 65536;
 
@@ -1052,7 +1053,22 @@ tl_status autotune_level(tl_problem* p, Level& L, bool fine) {
     }
     L.tp = win;
   }
-  // 2. the wide tiles' depth, or the element tile shape
+  // 2. the refined path's inner tile family: wide tiles where the size rule
+  // chose element tiles, and the other way round (not when inner_tiles forces one)
+  if (ok && c.precision == TL_FP32_REFINED && c.inner_tiles == 0) {
+    const int w0 = L.wide;
+    const Tiling tw0 = L.tw;
+    L.wide = !w0;
+    if (L.wide) L.tw = wide_tiling(L.g, L.grid);
+    const float ms = time_dry(p, L, fine, e0, e1);
+    if (ms >= 0 && ms < best) {
+      best = ms;
+    } else {
+      L.wide = w0;
+      L.tw = tw0;
+    }
+  }
+  // 3. the wide tiles' depth, or the element tile shape
   if (ok && L.wide) {
     const Tiling t0 = L.tw;
     Tiling win = t0;

@@ -114,6 +114,20 @@ def multitrack_20mm():
     )
 
 
+def probe_256():
+    """Roofline probe: a 256 x 256 x 128-element fine patch (8.5M nodes, a
+    working set above the 129 MB L2): 32 x 32 x 16 coarse elements refined 8x
+    on a 5 x 5 x 2.5 mm plate of 40 x 40 x 20 coarse hexes, m = 8, one 3 mm
+    track."""
+    return _base(
+        name="probe_256",
+        Lx=5e-3, Ly=5e-3, Lz=2.5e-3, NXc=40, NYc=40, NZc=20,
+        pNXc=32, pNYc=32, pNZc=16, r=8, m=8, dt_coarse=50e-6,
+        tracks=[(1e-3, 2.5e-3, 4e-3, 2.5e-3, 0.8)],
+        macro_steps=4, precision=1, tol=1e-10,
+    )
+
+
 def batch_jobs(n_jobs=64, seed=20211025):
     """Independent jobs of uneven size: domain length 2-8 mm (width L/2,
     depth L/4), P 100-300 W, speed 0.4-1.5 m/s, 1-6 tracks, refinement 4 or
@@ -182,6 +196,7 @@ WORKLOADS = {
     "single_track_tiny": single_track_tiny,
     "multitrack_10mm": multitrack_10mm,
     "multitrack_20mm": multitrack_20mm,
+    "probe_256": probe_256,
 }
 
 
