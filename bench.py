@@ -80,8 +80,8 @@ def parse():
     ap.add_argument("--mode", default="full", choices=["full", "plain", "batch", "serve", "roofline", "launch"],
                     help="full: the plate in both precisions plus the roofline probe, the batch and the serve "
                          "sub-objects; plain: the plate only; batch / serve / roofline: one of them alone; "
-                         "launch: one macro step, then a predictor and one fine micro step (the 12th solve "
-                         "launch), for profiler captures")
+                         "launch: one macro step and a predictor, then one fine micro step between "
+                         "cudaProfilerStart and cudaProfilerStop, for profiler captures")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1], help="launch: 0 FP64, 1 precision form")
     ap.add_argument("--jobs", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
@@ -725,12 +725,16 @@ def run_launch(args):
     macro step, then PREDICT and one fine micro step."""
     torch, tl, rank, ws, local, stream, sp = _setup(args)
     prec = args.precision
-    cfg = workloads.workload(args.workload, precision=prec, tol=1e-10 if prec else 1e-12, tol_inner=1e-5)
+    cfg = workloads.workload(args.workload, precision=prec, tol=1e-10 if prec else 1e-12, tol_inner=1e-5,
+                             autotune=0 if args.no_autotune else 1)
     p = tl.Problem(cfg, stream=sp)
     p.macro_steps(1)
     p.predict()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees this launch only
     p.fine_substeps(1)
     status = p.sync()
+    torch.cuda.profiler.stop()
     st = p.stats()
     p.close()
     if rank == 0:

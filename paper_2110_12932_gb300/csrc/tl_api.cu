@@ -957,7 +957,7 @@ struct TuneKey {
 };
 struct TunePick {
   Tiling t, tw, tp;
-  int grid;
+  int grid, wide;
 };
 std::mutex g_tune_mutex;
 std::map<TuneKey, TunePick> g_tune_cache;
@@ -1022,6 +1022,7 @@ tl_status autotune_level(tl_problem* p, Level& L, bool fine) {
       L.tw = it->second.tw;
       L.tp = it->second.tp;
       L.grid = it->second.grid;
+      L.wide = it->second.wide;
       L.tuned = 1;
       return TL_OK;
     }
@@ -1112,7 +1113,7 @@ tl_status autotune_level(tl_problem* p, Level& L, bool fine) {
   if (!ok) return TL_OK;  // a failed timing run: the models' picks stay
   L.tuned = 1;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache[key] = TunePick{L.t, L.tw, L.tp, L.grid};
+  g_tune_cache[key] = TunePick{L.t, L.tw, L.tp, L.grid, L.wide};
   return TL_OK;
 }
 

@@ -70,3 +70,24 @@ def test_checkpoint_errors():
     assert tl.tl_checkpoint_load(r.h, bad) == tl.TL_EINVAL
     r.restore(buf)
     r.close()
+
+
+@pytest.mark.parametrize("over", [dict(P=150.0), dict(k0=7.0), dict(tol=1e-11), dict(coarse_source=1),
+                                  dict(tracks=[(0.0, 0.5e-3, 1.9e-3, 0.5e-3, 0.8)]), dict(interface_coupling=1)])
+def test_checkpoint_from_another_configuration_is_refused(over):
+    """Same mesh and sizes, one value that changes the physics or the solver:
+    the buffer is refused (TL_EINVAL) and the problem is untouched; the time
+    limit of the barriers does not change the results and is accepted."""
+    cfg = workloads.workload("single_track_tiny")
+    p = tl.Problem(cfg)
+    p.macro_steps(2)
+    buf = p.checkpoint()
+    p.close()
+    q = tl.Problem(dict(cfg, **over))
+    before = q.temperature(tl.TL_FINE)[0]
+    assert tl.tl_checkpoint_load(q.h, buf) == tl.TL_EINVAL
+    assert np.array_equal(q.temperature(tl.TL_FINE)[0], before)
+    q.close()
+    ok = tl.Problem(dict(cfg, barrier_timeout=5.0))
+    ok.restore(buf)
+    ok.close()
