@@ -236,6 +236,19 @@ def cpu_baseline(cfg, budget_s=20.0):
                       f"host has {os.cpu_count()} cores"}
 
 
+def line_config(args, ws):
+    """The `config` of both arms' JSON lines: the workload the metric is
+    quoted on and how it is run."""
+    cfg = workloads.workload(args.workload)
+    return {"workload": cfg["name"], "fine_nodes": fine_nodes(cfg), "fine_elements": fine_elems(cfg),
+            "coarse_nodes": (cfg["NXc"] + 1) * (cfg["NYc"] + 1) * (cfg["NZc"] + 1),
+            "m": cfg["m"], "r": cfg["r"], "precision": "fp32_refined", "tol": 1e-10, "tol_inner": 1e-5,
+            "coupling_sweeps": args.coupling_sweeps, "latent": args.latent, "picard_iters": args.picard,
+            "h_conv": args.h_conv, "emissivity": args.emissivity,
+            "parallelism": f"replicas{ws}" if ws > 1 else "single",
+            "l2": "flushed (256 MB write) between timed macro steps, outside the events"}
+
+
 def run_reference(args):
     """The oracle on the same workload: a step is one solve of its Algorithm-1
     sequence (coarse predictor / corrector or fine micro step); the value
@@ -246,17 +259,16 @@ def run_reference(args):
     cfg = workloads.workload(args.workload)
     budget = 120.0
     t_start = time.perf_counter()
-    warm = max(0, min(args.warmup, 1))
+    warm = max(0, args.warmup)
     val, done, nc, nf, dt = oracle_sample(cfg, budget, max_solves=max(2, args.steps), warmup=warm)
-    sample = (f"{done} solves of {cfg['name']} ({nc} coarse, {nf} fine) after {warm} warm-up solve, "
+    sample = (f"{done} solves of {cfg['name']} ({nc} coarse, {nf} fine) after {warm} warm-up solves, "
               f"single-threaded FP64 SciPy oracle, {dt:.1f} s (time-capped at {budget:.0f} s), mean solve "
               f"times scaled to a macro step (2 coarse + {cfg['m']} fine)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DOF-substeps/s",
             "n_gpus": args.gpus, "steps": done, "warmup": warm,
             "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "fine_nodes": fine_nodes(cfg), "m": cfg["m"],
-                       "step": "one oracle solve"},
+            "config": line_config(args, 1),
             "cpu_baseline": {"value": val, "unit": "DOF-substeps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": "DOF-substeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -683,13 +695,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": b["value"], "unit": "DOF-substeps/s", "n_gpus": ws, "steps": K,
                 "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": cfg32["name"], "fine_nodes": nfn, "fine_elements": ne,
-                           "coarse_nodes": (cfg32["NXc"] + 1) * (cfg32["NYc"] + 1) * (cfg32["NZc"] + 1),
-                           "m": m, "r": cfg32["r"], "precision": "fp32_refined", "tol": 1e-10, "tol_inner": 1e-5,
-                           "coupling_sweeps": args.coupling_sweeps, "latent": args.latent,
-                           "picard_iters": args.picard, "h_conv": args.h_conv, "emissivity": args.emissivity,
-                           "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                           "l2": "flushed (256 MB write) between timed macro steps, outside the events"},
+                "config": line_config(args, ws),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(sum_over_ranks(b["stats"]["launches"], ws)),
                 "clocks": clk, "wall_s": wall,
