@@ -242,7 +242,8 @@ Tiling wide_tiling(const Grid3& g, int /*nblk*/) {
 }
 
 // Node-owned tiles of the tensor preconditioner's pass: rows split into equal
-// widths of at most 32 columns, as many rows as fill the block, and the
+// widths of at most 64 columns (two per thread), as many rows as fill the
+// block, and the
 // z-depth ez that minimises the layer steps of the busiest block: a tile of ez
 // owned layers marches through ez + 2 layers and costs about PC_TILE_STEPS
 // more for its prologue and drain, and a block runs ceil(tiles / blocks)
@@ -252,9 +253,11 @@ Tiling wide_tiling(const Grid3& g, int /*nblk*/) {
 constexpr int PC_TILE_STEPS = 2;
 
 Tiling pc_tiling(const Grid3& g, int nblk) {
-  const int ntx = (g.nnx + 31) / 32;
-  const int tx = (g.nnx + ntx - 1) / ntx;
-  const int ty = std::max(1, std::min(g.nny, NT / tx));
+  const int ntx = (g.nnx + 63) / 64;
+  const int tx = (g.nnx + ntx - 1) / ntx;                 // at most 64 columns, two per thread
+  // rows: as many as the block's threads cover, the window ((tx + 2) x
+  // (ty + 2) nodes) at most PC_WN_MAX
+  const int ty = std::max(1, std::min({g.nny, NT / ((tx + 1) / 2), PC_WN_MAX / (tx + 2) - 2}));
   const int nty = (g.nny + ty - 1) / ty;
   const long long cols = (long long)ntx * nty;
   const long long B = std::max(1, nblk);

@@ -1492,9 +1492,12 @@ __device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
 //   A  (tiles): partials of w = A u; sum <w,u>.
 // ---------------------------------------------------------------------------
 constexpr double PC_C = 0.2;
-// Preconditioner tiles are at least two columns wide and at most NT columns in
-// all, so a window holds at most (2 + 2) (NT / 2 + 2) nodes: PC_WM per thread.
-constexpr int PC_WN_MAX = 4 * (NT / 2 + 2);
+// Preconditioner tiles: each thread owns two adjacent node columns of a tile
+// row, so a tile is at most 64 columns wide (32 threads per row) and holds at
+// most 2 NT columns; the host caps the tile height so that the window (halo
+// one node) has at most PC_WN_MAX nodes, the window of a 64 x 5 tile.
+constexpr int PC_CPT = 2;
+constexpr int PC_WN_MAX = (64 + 2) * (NT / 32 + 2);
 constexpr int PC_WM = (PC_WN_MAX + NT - 1) / NT;
 
 template <typename R>
@@ -1688,44 +1691,53 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
 }
 
 // Preconditioner phase of pcg3: u = sq (Q_z Q_y Q_x v) and the block's sum of
-// <r,u>.  Node-owned tiles of tp.ex x tp.ey columns (at most NT) and tp.ez
-// node layers; a tile marches up from one layer below its range to one above,
-// loads the (ex+2) x (ey+2) window of v of each layer into shared memory
-// (zeros outside the mesh, which drops the missing neighbours), applies
-// Q_x Q_y there, and keeps three consecutive layers of the result per column
-// in registers for Q_z.  The windows (with sq and r of the owned nodes)
-// arrive by cp.async several layers ahead in a ring of slots; one block
-// barrier per layer.
+// <r,u>.  Node-owned tiles of tp.ex x tp.ey columns and tp.ez node layers;
+// each thread owns two adjacent columns of a tile row (a tile step covers up
+// to 2 NT nodes); a tile marches up from one layer below its range to one
+// above, loads the (ex+2) x (ey+2) window of v of each layer into shared
+// memory (zeros outside the mesh, which drops the missing neighbours),
+// applies Q_x Q_y there, and keeps three consecutive layers of the result per
+// column in registers for Q_z.  The windows (with sq and r of the owned
+// nodes) arrive by cp.async several layers ahead in a ring of slots; one
+// block barrier per layer.
 template <typename R>
 static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const PCVecs<R> c, R* win_raw,
                                           const VGrid vg) {
   const int S = g.nnx * g.nny;
   // NS ring slots, D = NS - 1 layers in flight: a tile column is narrow, so
   // several layers must be in flight to cover the memory latency.  A slot
-  // holds the layer's window of v and sq of the owned nodes (FP32), then r of
-  // the owned nodes (R).
-  constexpr int NS = 8, D = NS - 1;
-  constexpr int SLOT_MAX = ((PC_WN_MAX + NT) * 4 + NT * (int)sizeof(R) + 15) / 16 * 16;
+  // holds the layer's window of v and sq of the owned columns (FP32), then r
+  // of the owned columns (R).
+  constexpr int NS = sizeof(R) == 4 ? 7 : 5, D = NS - 1;
+  constexpr int SLOT_MAX = ((PC_WN_MAX + PC_CPT * NT) * 4 + PC_CPT * NT * (int)sizeof(R) + 15) / 16 * 16;
   static_assert(NS * SLOT_MAX <= STAGE_BYTES, "ring of the widest window fits the dynamic shared memory");
   const int TX = tp.ex, TY = tp.ey, WXP = TX + 2, WN = (TX + 2) * (TY + 2);
-  const int RB = ((WN + NT) * 4 + 15) / 16 * 16;                 // byte offset of r in a slot
-  const int SB = (RB + NT * (int)sizeof(R) + 15) / 16 * 16;      // slot bytes
+  const int TXT = (TX + PC_CPT - 1) / PC_CPT;                        // threads per tile row
+  const int RB = ((WN + PC_CPT * NT) * 4 + 15) / 16 * 16;             // byte offset of r in a slot
+  const int SB = (RB + PC_CPT * NT * (int)sizeof(R) + 15) / 16 * 16;  // slot bytes
   unsigned char* ring = reinterpret_cast<unsigned char*>(win_raw);
   const int ntiles = tp.ntx * tp.nty * tp.ntz;
   const float cw = (float)PC_C;
   const int tid = threadIdx.x;
-  const int ty = tid / TX, tx = tid - ty * TX;
+  const int ty = tid / TXT, tx0 = PC_CPT * (tid - ty * TXT);  // the thread's first column in the tile
   R gam = R(0);
   for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
     const int txy = tp.ntx * tp.nty;
     const int tiz = tile / txy, trem = tile - tiz * txy;
     const int tiy = trem / tp.ntx, tix = trem - tiy * tp.ntx;
     const int i0 = tix * TX, j0 = tiy * TY, k0 = tiz * tp.ez, k1 = min(k0 + tp.ez, g.nnz);
-    const int i = i0 + tx, j = j0 + ty;
-    const bool own = ty < TY && i < g.nnx && j < g.nny;
-    float tm = 0.0f, tc = 0.0f;  // xy-filtered values of layers L - 2, L - 1
-    float sq_c = 0.0f;           // sq, r of the column's node at layer L - 1
-    R r_c = R(0);
+    const int j = j0 + ty;
+    bool own[PC_CPT];
+#pragma unroll
+    for (int q = 0; q < PC_CPT; ++q) own[q] = ty < TY && tx0 + q < TX && i0 + tx0 + q < g.nnx && j < g.nny;
+    float tm[PC_CPT], tc[PC_CPT];  // xy-filtered values of layers L - 2, L - 1
+    float sq_c[PC_CPT];            // sq, r of the columns' nodes at layer L - 1
+    R r_c[PC_CPT];
+#pragma unroll
+    for (int q = 0; q < PC_CPT; ++q) {
+      tm[q] = tc[q] = sq_c[q] = 0.0f;
+      r_c[q] = R(0);
+    }
     // this thread's window entries (w = tid + m NT) and their in-layer node
     // offsets, -1 outside the mesh; fixed for the tile
     int woff[PC_WM];
@@ -1736,7 +1748,7 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
       const int gi = i0 - 1 + wx, gj = j0 - 1 + wy;
       woff[m] = (w < WN && gi >= 0 && gi < g.nnx && gj >= 0 && gj < g.nny) ? gi + g.nnx * gj : -1;
     }
-    const int own_off = i + g.nnx * j;
+    const int own_off = i0 + tx0 + g.nnx * j;
     // slot of layer L: async copies, zeros outside the mesh, one group per layer
     auto load_layer = [&](int L, int slot) {
       if (L >= 0 && L < g.nnz && L <= k1) {
@@ -1750,10 +1762,14 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
           else if (w < WN)
             buf[w] = 0.0f;
         }
-        if (own && L >= k0 && L < k1) {
+        if (L >= k0 && L < k1) {
           const size_t n = (size_t)S * L + own_off;
-          cp_async<4>(buf + WN + tid, c.sq + n);
-          cp_async<sizeof(R)>(reinterpret_cast<R*>(ring + slot * SB + RB) + tid, c.r + n);
+#pragma unroll
+          for (int q = 0; q < PC_CPT; ++q)
+            if (own[q]) {
+              cp_async<4>(buf + WN + q * NT + tid, c.sq + n + q);
+              cp_async<sizeof(R)>(reinterpret_cast<R*>(ring + slot * SB + RB) + q * NT + tid, c.r + n + q);
+            }
         }
       }
       cp_async_commit();
@@ -1765,29 +1781,51 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
       __syncthreads();         // ... for every thread; the slot of layer L - 1 is free again
       load_layer(L + D, sl == 0 ? NS - 1 : sl - 1);
       const float* buf = reinterpret_cast<const float*>(ring + sl * SB);
-      float tl = 0.0f;
-      if (own && L >= 0 && L < g.nnz) {
-        float acc = 0.0f;
+      float tl[PC_CPT];
+#pragma unroll
+      for (int q = 0; q < PC_CPT; ++q) tl[q] = 0.0f;
+      if (ty < TY && L >= 0 && L < g.nnz) {
+        float acc[PC_CPT];
+#pragma unroll
+        for (int q = 0; q < PC_CPT; ++q) acc[q] = 0.0f;
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-          const float* row = buf + (ty + dy) * WXP + tx;
-          const float t = fmaf(-cw, row[0] + row[2], row[1]);
-          acc = dy == 1 ? acc + t : fmaf(-cw, t, acc);
+          const float* row = buf + (ty + dy) * WXP + tx0;  // window columns tx0 .. tx0 + PC_CPT + 1
+          float rv[PC_CPT + 2];
+#pragma unroll
+          for (int e = 0; e < PC_CPT + 2; ++e) rv[e] = (tx0 + e < WXP) ? row[e] : 0.0f;
+#pragma unroll
+          for (int q = 0; q < PC_CPT; ++q) {
+            const float t = fmaf(-cw, rv[q] + rv[q + 2], rv[q + 1]);
+            acc[q] = dy == 1 ? acc[q] + t : fmaf(-cw, t, acc[q]);
+          }
         }
-        tl = acc;
+#pragma unroll
+        for (int q = 0; q < PC_CPT; ++q) tl[q] = own[q] ? acc[q] : 0.0f;
       }
-      if (own && L >= k0 + 1) {  // layer L - 1 is complete
-        const int n = i + g.nnx * j + S * (L - 1);
-        const R un = (R)(sq_c * fmaf(-cw, tm + tl, tc));
-        c.u[n] = un;
-        if (sq_c != 0.0f) gam = fma(r_c, un, gam);
+      if (L >= k0 + 1) {  // layer L - 1 is complete
+#pragma unroll
+        for (int q = 0; q < PC_CPT; ++q)
+          if (own[q]) {
+            const int n = own_off + q + S * (L - 1);
+            const R un = (R)(sq_c[q] * fmaf(-cw, tm[q] + tl[q], tc[q]));
+            c.u[n] = un;
+            if (sq_c[q] != 0.0f) gam = fma(r_c[q], un, gam);
+          }
       }
-      if (own && L >= k0 && L < k1) {
-        sq_c = buf[WN + tid];
-        r_c = reinterpret_cast<const R*>(ring + sl * SB + RB)[tid];
+      if (L >= k0 && L < k1) {
+#pragma unroll
+        for (int q = 0; q < PC_CPT; ++q)
+          if (own[q]) {
+            sq_c[q] = buf[WN + q * NT + tid];
+            r_c[q] = reinterpret_cast<const R*>(ring + sl * SB + RB)[q * NT + tid];
+          }
       }
-      tm = tc;
-      tc = tl;
+#pragma unroll
+      for (int q = 0; q < PC_CPT; ++q) {
+        tm[q] = tc[q];
+        tc[q] = tl[q];
+      }
       sl = sl == NS - 1 ? 0 : sl + 1;
     }
     cp_async_wait<0>();
