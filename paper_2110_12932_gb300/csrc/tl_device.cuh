@@ -115,6 +115,15 @@ __device__ inline unsigned long long ld_acquire_u64(const unsigned long long* p)
 __device__ inline void atom_add_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// Arrival: one RMW with acquire and release semantics.  Every arrival and the
+// release are RMWs of the same word, so they form one release sequence: the
+// last arrival acquires every earlier block's writes, and a waiter that
+// acquires the released generation sees all of them (no separate fences).
+__device__ inline unsigned long long atom_add_acqrel_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long o;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(o) : "l"(p), "l"(v) : "memory");
+  return o;
+}
 __device__ inline int ld_volatile_i32(const int* p) {
   return *(volatile const int*)p;
 }
@@ -176,11 +185,11 @@ __device__ inline bool grid_sync(const Barrier& b, const VGrid& vg) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int g = *bar_gen_local();
-    __threadfence();  // release side: this block's writes
     bool ok = true;
-    const unsigned long long old = atomicAdd(b.word, 1ull);
+    // the block barrier above orders the block's writes before thread 0's
+    // release (cumulativity)
+    const unsigned long long old = atom_add_acqrel_u64(b.word, 1ull);
     if ((unsigned int)old == (unsigned int)vg.nblk - 1u) {
-      __threadfence();  // acquire side: every block's arrival
       atom_add_release_u64(b.word, (1ull << 32) - (unsigned long long)(unsigned int)vg.nblk);
     } else {
       ok = bar_wait(b, g, vg.nblk);
