@@ -43,6 +43,12 @@ __device__ inline void cp_async(void* smem, const void* gmem) {
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// 8-byte asynchronous copy of which only the first src_bytes (0, 4 or 8) are
+// read; the rest of the 8 shared-memory bytes is zero-filled.
+__device__ inline void cp_async8_fill(void* smem, const void* gmem, int src_bytes) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
 static_assert(NT >= WX * WY, "a block must cover a tile's window columns");
 static_assert(NT <= 32 * (RED_W + 1), "block_reduce_store parks the lanes of warps 1 .. RED_W");
 constexpr int MAXRECT = 8;
@@ -1695,6 +1701,151 @@ static __device__ __noinline__ R pc_update(const Grid3 g, const Tiling t, const 
   return vrr;
 }
 
+// FP32 update phase of pcg3 (k >= 0) with its inputs staged in shared
+// memory.  The same arithmetic on the same node pairs as pc_update<float>
+// (thread gtid takes pairs gtid, gtid + gstride, ...; bitwise equal results),
+// but a thread's inputs arrive by asynchronous copies two pairs ahead, so its
+// L2 round trips overlap instead of following one another: the register
+// version waits one round trip per pair, and keeping more pairs in flight in
+// registers spills.  Every thread copies into and reads only its own slots
+// (no block barrier).  Per stage a thread holds 8 bytes of each of 13
+// arrays: r, q, x, u, p, s, sq and the x-face partials in `ra`, the y-face,
+// xy-edge, z-face, xz-edge and yz-edge partials in `rb`; a partial plane no
+// node of the pair gathers is zero-filled without a read, and so are p and s
+// in the first iteration (p = s = 0).  The rare corner partials (x, y and z
+// faces at once) are loaded directly.  Returns the thread's <r,r>.
+constexpr int UST = 3, UNA = 8, UNB = 5;  // stages; arrays in ra / rb per stage
+template <int NA>
+struct UStage {
+  float2 a[NA][NT];
+};
+static_assert(UST * sizeof(UStage<UNA>) <= STAGE_BYTES, "staged update inputs fit the dynamic ring");
+static_assert(UST * sizeof(UStage<UNB>) <= sizeof(ApplySmem<double>), "staged partials fit the apply's buffers");
+static __device__ __noinline__ float pc_update_staged(const Grid3 g, const Tiling t, const PCVecs<float> c,
+                                                      float alpha, float beta, bool first, int gtid, int gstride,
+                                                      UStage<UNA>* ra, UStage<UNB>* rb) {
+  const int nn = g.nnx * g.nny * g.nnz;
+  const size_t xs = xplane(nn);
+  const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny), mz = div_magic(t.ez);
+  const int ngroups = (nn + 1) / 2;
+  const int tid = threadIdx.x;
+  float vrr = 0.0f;
+  // low tile faces of the pair's nodes, node 0 in bits 0-2, node 1 in bits 3-5
+  auto faces = [&](int q) {
+    const int n0 = 2 * q;
+    const int row = div_by(n0, g.nnx, mx);
+    int i = n0 - row * g.nnx;
+    int kz = div_by(row, g.nny, my);
+    int j = row - kz * g.nny;
+    auto node = [&]() {
+      const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
+      const bool lz = kz > 0 && kz < g.nz && kz - div_by(kz, t.ez, mz) * t.ez == 0;
+      return low_faces(g, t, i, ly, lz);
+    };
+    const int f0 = node();
+    if (n0 + 1 >= nn) return f0;
+    if (++i == g.nnx) {
+      i = 0;
+      if (++j == g.nny) {
+        j = 0;
+        ++kz;
+      }
+    }
+    return f0 | (node() << 3);
+  };
+  auto issue = [&](int q, int st, int lf) {
+    if (q < ngroups) {
+      const int n0 = 2 * q;
+      const int sb = min(2, nn - n0) * 4;  // bytes that lie in the arrays
+      float2* A = &ra[st].a[0][tid];
+      float2* B = &rb[st].a[0][tid];
+      const int f0 = lf & 7, f1 = lf >> 3;
+      auto any = [&](int m) { return ((f0 & m) == m || (f1 & m) == m) ? sb : 0; };
+      cp_async8_fill(A + 0 * NT, c.r + n0, sb);
+      cp_async8_fill(A + 1 * NT, c.q + n0, sb);
+      cp_async8_fill(A + 2 * NT, c.x + n0, sb);
+      cp_async8_fill(A + 3 * NT, c.u + n0, sb);
+      cp_async8_fill(A + 4 * NT, c.p + n0, first ? 0 : sb);
+      cp_async8_fill(A + 5 * NT, c.s + n0, first ? 0 : sb);
+      cp_async8_fill(A + 6 * NT, c.sq + n0, sb);
+      cp_async8_fill(A + 7 * NT, c.X + 0 * xs + n0, any(1));
+      cp_async8_fill(B + 0 * NT, c.X + 1 * xs + n0, any(2));
+      cp_async8_fill(B + 1 * NT, c.X + 2 * xs + n0, any(3));
+      cp_async8_fill(B + 2 * NT, c.X + 3 * xs + n0, any(4));
+      cp_async8_fill(B + 3 * NT, c.X + 4 * xs + n0, any(5));
+      cp_async8_fill(B + 4 * NT, c.X + 5 * xs + n0, any(6));
+    }
+    cp_async_commit();
+  };
+  int q = gtid;
+  int lf0 = q < ngroups ? faces(q) : 0;
+  int lf1 = q + gstride < ngroups ? faces(q + gstride) : 0;
+  issue(q, 0, lf0);
+  issue(q + gstride, 1, lf1);
+  int st = 0, st2 = 2;
+  for (; q < ngroups; q += gstride) {
+    const int q2 = q + 2 * gstride;
+    const int lf2 = q2 < ngroups ? faces(q2) : 0;
+    issue(q2, st2, lf2);
+    cp_async_wait<UST - 1>();  // the pair q has landed
+    const float2* A = &ra[st].a[0][tid];
+    const float2* B = &rb[st].a[0][tid];
+    const int n0 = 2 * q;
+    const int cnt = min(2, nn - n0);
+    const float2 rk2 = A[0 * NT], w2 = A[1 * NT], xk2 = A[2 * NT], uk2 = A[3 * NT];
+    const float2 pk2 = A[4 * NT], sk2 = A[5 * NT], sq2 = A[6 * NT];
+    const float rk[2] = {rk2.x, rk2.y}, w[2] = {w2.x, w2.y}, xk[2] = {xk2.x, xk2.y}, uk[2] = {uk2.x, uk2.y};
+    const float pk[2] = {pk2.x, pk2.y}, sk[2] = {sk2.x, sk2.y}, sqv[2] = {sq2.x, sq2.y};
+    float pn[2], sn[2], rn[2], xn[2], vn[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      pn[m] = pk[m];
+      sn[m] = sk[m];
+      rn[m] = rk[m];
+      xn[m] = xk[m];
+      vn[m] = 0.0f;
+      if (m >= cnt || sqv[m] == 0.0f) continue;
+      const int f = m == 0 ? (lf0 & 7) : (lf0 >> 3);
+      float wv = w[m];
+      if (f) {  // neighbours' partials, in the order gather_partials uses
+        auto part = [&](const float2* P) { return m == 0 ? P->x : P->y; };
+        if (f & 1) wv += part(A + 7 * NT);
+        if (f & 2) wv += part(B + 0 * NT);
+        if ((f & 3) == 3) wv += part(B + 1 * NT);
+        if (f & 4) wv += part(B + 2 * NT);
+        if ((f & 5) == 5) wv += part(B + 3 * NT);
+        if ((f & 6) == 6) wv += part(B + 4 * NT);
+        if (f == 7) wv += __ldcg(c.X + 6 * xs + n0 + m);
+      }
+      pn[m] = first ? uk[m] : fmaf(beta, pk[m], uk[m]);
+      sn[m] = first ? wv : fmaf(beta, sk[m], wv);
+      rn[m] = fmaf(-alpha, sn[m], rk[m]);
+      xn[m] = fmaf(alpha, pn[m], xk[m]);
+      vn[m] = sqv[m] * rn[m];
+      vrr = fmaf(rn[m], rn[m], vrr);
+    }
+    if (cnt == 2) {
+      *reinterpret_cast<float2*>(c.p + n0) = make_float2(pn[0], pn[1]);
+      *reinterpret_cast<float2*>(c.s + n0) = make_float2(sn[0], sn[1]);
+      *reinterpret_cast<float2*>(c.r + n0) = make_float2(rn[0], rn[1]);
+      *reinterpret_cast<float2*>(c.x + n0) = make_float2(xn[0], xn[1]);
+      *reinterpret_cast<float2*>(c.v + n0) = make_float2(vn[0], vn[1]);
+    } else {
+      c.p[n0] = pn[0];
+      c.s[n0] = sn[0];
+      c.r[n0] = rn[0];
+      c.x[n0] = xn[0];
+      c.v[n0] = vn[0];
+    }
+    lf0 = lf1;
+    lf1 = lf2;
+    st = st == UST - 1 ? 0 : st + 1;
+    st2 = st2 == UST - 1 ? 0 : st2 + 1;
+  }
+  cp_async_wait<0>();  // no copy into the slots outlives the phase
+  return vrr;
+}
+
 // Preconditioner phase of pcg3: u = sq (Q_z Q_y Q_x v) and the block's sum of
 // <r,u>.  Node-owned tiles of tp.ex x tp.ey columns and tp.ez node layers;
 // each thread owns two adjacent columns of a tile row (a tile step covers up
@@ -1844,7 +1995,7 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
 // reduction rows RS_PQ..RS_RR and RS_ES..RS_EF.
 template <typename R, class ApplyZ>
 __device__ int pcg3(const SolveArgs& a, const VGrid& vg, const Tiling& t, const PCVecs<R>& c, ApplyZ apply_z,
-                    R* win, R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
+                    R* win, unsigned char* aux, R thresh, int max_iter, R* red, int* iters, Tracer& tr) {
   R* s_scal = red_scalars<R>();
   const int ntiles = t.ntx * t.nty * t.ntz;
   const int gtid = vg.bid * blockDim.x + threadIdx.x, gstride = vg.nblk * blockDim.x;
@@ -1856,7 +2007,14 @@ __device__ int pcg3(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
     R* rslots = red + (((k + 1) & 1) ? RS_ES : RS_PQ) * a.red_stride;
     tr.mark(TR_CG_U0);
     {
-      R v[1] = {pc_update<R>(a.g, t, c, alpha, beta, k, gtid, gstride)};
+      R v[1];
+      if constexpr (sizeof(R) == 4) {  // FP32: staged update after the first pass
+        v[0] = k < 0 ? pc_update<R>(a.g, t, c, alpha, beta, k, gtid, gstride)
+                     : pc_update_staged(a.g, t, c, alpha, beta, k == 0, gtid, gstride,
+                                        reinterpret_cast<UStage<UNA>*>(win), reinterpret_cast<UStage<UNB>*>(aux));
+      } else {
+        v[0] = pc_update<R>(a.g, t, c, alpha, beta, k, gtid, gstride);
+      }
       tr.mark(TR_CG_U1);
       block_reduce_store<1>(v, rslots + 2 * a.red_stride, a.red_stride, vg);
     }
@@ -2163,7 +2321,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
         }
         return vd;
       };
-      res = pcg3<double>(a, vg, t, c3, apply_z, stage64, thresh, a.max_iter, a.red, &it, tr);
+      res = pcg3<double>(a, vg, t, c3, apply_z, stage64, smem_raw, thresh, a.max_iter, a.red, &it, tr);
     } else {
       res = pcg1<double, false, NRAW>(a, vg, sm64, stage64, c, no_fetch64, lam64, thresh, a.max_iter, a.red, &it,
                                       tr);
@@ -2233,7 +2391,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
           }
           return vd;
         };
-        res = pcg3<float>(a, vg, a.tw, c3, apply_z, stage32, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+        res = pcg3<float>(a, vg, a.tw, c3, apply_z, stage32, smem_raw, ti * ti * t32[1], a.max_iter, a.red32,
+                          &inner, tr);
       } else {
         auto apply_z = [&](int tile) {
           float vd = 0.0f;
@@ -2250,7 +2409,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
           }
           return vd;
         };
-        res = pcg3<float>(a, vg, t, c3, apply_z, stage32, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
+        res = pcg3<float>(a, vg, t, c3, apply_z, stage32, smem_raw, ti * ti * t32[1], a.max_iter, a.red32, &inner, tr);
       }
     } else if (a.wide) {
       CGVecs<float> c2{a.d32, a.r32, a.p0f, a.s0f, a.r32b, a.q32, a.X32, a.dinv32};
