@@ -933,15 +933,38 @@ __device__ int pcg1(const SolveArgs& a, const VGrid& vg, ApplySmem<R>& sm, R* st
 // start there (lane 31 also column AX).  Within a row the x-direction stays in
 // registers, warp shuffles and shared memory, the neighbouring node row
 // passes through shared memory, and an element layer takes two block
-// barriers.  Inputs (window values and element data) arrive by cp.async two
-// layers ahead in a four-stage per-thread ring.  Partials of window nodes on
-// the tile's high faces go to the exchange arrays, as with apply_tile.
+// barriers.  Inputs arrive by cp.async two layers ahead in a four-stage ring
+// of dense layers (each thread reads its pairs with 8-byte loads): the window
+// values by their owners, 4 bytes a column (window rows do not start on 16
+// bytes), the element data by 128 threads, 16 bytes each (zero-filled past
+// the tile), which keeps the copies per thread and layer at 3 instead of 7:
+// the pass is bound by issuing memory instructions, not by bytes.  Partials
+// of window nodes on the tile's high faces go to the exchange arrays, as with
+// apply_tile.
 // ---------------------------------------------------------------------------
 constexpr int AX = 64, AY = 4;
-constexpr int WSLOTS = 8;    // ring slots per stage: u(c0), u(c1), u(AX), s0, k0, s1, k1, spare
 constexpr int WSTAGES = 4;
+constexpr int WUX = AX + 4;  // a staged window row: AX + 1 values, padded to 16 bytes
+struct WideStage {
+  float u[AY + 1][WUX];      // window node values of one node layer
+  float sk[2][AY][AX];       // s_e and k_e of one element layer
+};
 static_assert(NT == 32 * (AY + 1), "one warp per window row");
-static_assert(WSTAGES * WSLOTS * NT * 4 <= STAGE_BYTES, "staging ring fits the dynamic shared memory");
+static_assert(2 * AY * AX / 4 <= NT, "one 16-byte element copy per thread");
+static_assert(sizeof(WideStage) % 16 == 0, "16-byte aligned stages");
+static_assert(WSTAGES * sizeof(WideStage) <= STAGE_BYTES, "staging ring fits the dynamic shared memory");
+
+// 16-byte asynchronous copy (L2 only) of which the first src_bytes are read
+// and the rest zero-filled.
+__device__ inline void cp_async16_fill(void* smem, const void* gmem, int src_bytes) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+// 4-byte asynchronous copy with zero fill (src_bytes 0 or 4).
+__device__ inline void cp_async4_fill(void* smem, const void* gmem, int src_bytes) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
 
 struct WideSmem {
   float ZS[AY + 1][AX + 2];   // z-sum and z-difference of each window column (current layer pair)
@@ -981,10 +1004,8 @@ static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Ti
   const int c0 = 2 * lane, c1 = c0 + 1;
   const bool v0 = row_on && c0 <= ex, v1 = row_on && c1 <= ex;
   const bool vx = row_on && lane == 31 && ex == AX;  // column AX
-  const bool ok0 = has_el && c0 < ex, ok1 = has_el && c1 < ex;
   const int nb = ie0 + g.nnx * (je0 + (row_on ? wy : 0));
-  const float* up = z + nb;                                            // node (ie0, row, 0)
-  const float* ep = sk + ie0 + g.nx * (je0 + (has_el ? wy : 0)) + c0;  // element (ie0 + c0, row, 0)
+  const float* up = z + nb;  // node (ie0, row, 0)
   // exchange slots: the tile's high-y node row; column AX is on the high-x
   // face only when another tile follows in x (a ragged last column is the
   // plate's own boundary); the top node layer adds the high-z bit
@@ -992,34 +1013,37 @@ static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Ti
   const int sx = ys | ((ie0 + AX < g.nx) ? 1 : 0);
   float* o01 = (ys ? X + (size_t)(ys - 1) * xplane(nn) : q) + nb;
   float* ox = (sx ? X + (size_t)(sx - 1) * xplane(nn) : q) + nb + AX;
-  float* my = ring + threadIdx.x;
+  WideStage* ws = reinterpret_cast<WideStage*>(ring);
+  // the thread's element copy: array ea (s or k), row er, columns 4 ec .. 4 ec + 3
+  const int ea = threadIdx.x >> 6, er = (threadIdx.x >> 4) & 3, ec = threadIdx.x & 15;
+  const bool ecopy = threadIdx.x < 2 * AY * AX / 4;
+  const int evalid = (ecopy && er < ey) ? max(0, min(4, ex - 4 * ec)) : 0;  // columns inside the tile
+  const float* eg = sk + (size_t)ea * ne + ie0 + 4 * ec + (size_t)g.nx * (je0 + er);
+  // 16-byte copies need 16-byte element rows (nx a multiple of 4, aligned base)
+  const bool e16 = (g.nx & 3) == 0 && ((reinterpret_cast<uintptr_t>(sk) & 15) == 0);
 #pragma unroll
   for (int st = 0; st < WSTAGES; ++st) {
-    float* r = my + st * WSLOTS * NT;
-    if (!v0) r[0] = 0.0f;
-    if (!v1) r[NT] = 0.0f;
-    if (!vx) r[2 * NT] = 0.0f;
-    if (!ok0) r[3 * NT] = r[4 * NT] = 0.0f;
-    if (!ok1) r[5 * NT] = r[6 * NT] = 0.0f;
+    if (!v0) ws[st].u[wy][c0] = 0.0f;
+    if (!v1) ws[st].u[wy][c1] = 0.0f;
+    if (lane == 31 && !vx) ws[st].u[wy][AX] = 0.0f;
   }
   auto issue = [&](int st) {  // stage st: z at node layer ke0 + st, s/k at element layer ke0 + st
-    float* r = my + (st & (WSTAGES - 1)) * WSLOTS * NT;
+    WideStage& w = ws[st & (WSTAGES - 1)];
     const int kn = ke0 + st;
     if (kn <= ke1) {
       const float* ub = up + (size_t)S * kn;
-      if (v0) cp_async<4>(r, ub + c0);
-      if (v1) cp_async<4>(r + NT, ub + c1);
-      if (vx) cp_async<4>(r + 2 * NT, ub + AX);
+      if (v0) cp_async<4>(&w.u[wy][c0], ub + c0);
+      if (v1) cp_async<4>(&w.u[wy][c1], ub + c1);
+      if (vx) cp_async<4>(&w.u[wy][AX], ub + AX);
     }
-    if (kn < ke1) {
-      const float* eb = ep + (size_t)Se * kn;
-      if (ok0) {
-        cp_async<4>(r + 3 * NT, eb);
-        cp_async<4>(r + 4 * NT, eb + ne);
-      }
-      if (ok1) {
-        cp_async<4>(r + 5 * NT, eb + 1);
-        cp_async<4>(r + 6 * NT, eb + ne + 1);
+    if (kn < ke1 && ecopy) {
+      float* dst = &w.sk[ea][er][4 * ec];
+      const float* src = eg + (size_t)Se * kn;
+      if (e16) {
+        cp_async16_fill(dst, evalid ? src : sk, 4 * evalid);
+      } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) cp_async4_fill(dst + m, m < evalid ? src + m : sk, m < evalid ? 4 : 0);
       }
     }
     cp_async_commit();
@@ -1028,17 +1052,17 @@ static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Ti
   issue(1);
   issue(2);
   cp_async_wait<2>();
-  float uL0 = my[0], uL1 = my[NT], uL2 = my[2 * NT];
+  float uL0 = ws[0].u[wy][c0], uL1 = ws[0].u[wy][c1], uL2 = lane == 31 ? ws[0].u[wy][AX] : 0.0f;
   float carry0 = 0.0f, carry1 = 0.0f, carry2 = 0.0f;
   float vd = 0.0f;
   for (int ke = ke0; ke < ke1; ++ke) {
     const int j = ke - ke0;
     issue(j + 3);
-    cp_async_wait<2>();  // stages j and j + 1 have landed
-    const float* rc = my + (j & (WSTAGES - 1)) * WSLOTS * NT;
-    const float* rn = my + ((j + 1) & (WSTAGES - 1)) * WSLOTS * NT;
-    const float uH0 = rn[0], uH1 = rn[NT], uH2 = rn[2 * NT];
-    const float s0 = rc[3 * NT], k0 = rc[4 * NT], s1 = rc[5 * NT], k1 = rc[6 * NT];
+    cp_async_wait<2>();  // the thread's copies of stages j and j + 1 have landed
+    const WideStage& wc = ws[j & (WSTAGES - 1)];
+    const WideStage& wn = ws[(j + 1) & (WSTAGES - 1)];
+    const float2 uH = *reinterpret_cast<const float2*>(&wn.u[wy][c0]);
+    const float uH0 = uH.x, uH1 = uH.y, uH2 = lane == 31 ? wn.u[wy][AX] : 0.0f;  // column AX: lane 31 only
     // z-direction per own column
     const float zs0 = uL0 + uH0, zs1 = uL1 + uH1, zs2 = uL2 + uH2;
     const float zd0 = uL0 - uH0, zd1 = uL1 - uH1, zd2 = uL2 - uH2;
@@ -1054,6 +1078,11 @@ static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Ti
     // elements of row wy: y-forward, x-direction with scaling, y-backward
     float r0s0 = 0.0f, r0s1 = 0.0f, r0s2 = 0.0f, r0d0 = 0.0f, r0d1 = 0.0f, r0d2 = 0.0f;
     if (has_el) {
+      // element data of the thread's two elements (copied by other threads:
+      // read after the block barrier)
+      const float2 sv = *reinterpret_cast<const float2*>(&wc.sk[0][wy][c0]);
+      const float2 kv = *reinterpret_cast<const float2*>(&wc.sk[1][wy][c0]);
+      const float s0 = sv.x, s1 = sv.y, k0 = kv.x, k1 = kv.y;
       const float2 ns = *reinterpret_cast<const float2*>(&sm.ZS[wy + 1][c0]);
       const float2 nd = *reinterpret_cast<const float2*>(&sm.ZD[wy + 1][c0]);
       const float s2 = sm.ZS[wy][c0 + 2], d2 = sm.ZD[wy][c0 + 2];
