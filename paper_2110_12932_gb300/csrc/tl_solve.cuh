@@ -2180,6 +2180,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
     const double se = rc * inv_dt;
     a.s_e[e] = se;
     a.k_e[e] = k;
+    // the element's share of the Jacobi diagonal, parked in r (unused until
+    // the residual phase, which comes after the next grid barrier)
+    a.r[e] = fma(se, a.Md, k * a.Kd);
 #pragma unroll
     for (int m = 0; m < 8; ++m) a.lam[m * ne + e] = se * a.Mc[m] + k * a.Kc[m];
     if (refined) {
@@ -2235,26 +2238,27 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
       if (p < w) a.G[2 * w + p] = gauss_hat_entry(a.ld, g, a.G, p);
     }
   }
+  // the precision form needs only the FP32 diagonal (its FP64 solves are
+  // applies and residual updates, and the FP64 residual norm is <r,r>)
   for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool, bool) {
-    double di = 0.0;
+    double d = 0.0;
     if (!is_dir(g, a.dir, i, j, k)) {
-      double d = 0.0;
       for (int dz = -1; dz <= 0; ++dz)
         for (int dy = -1; dy <= 0; ++dy)
           for (int dx = -1; dx <= 0; ++dx) {
             int ie = i + dx, je = j + dy, ke = k + dz;
             if (ie < 0 || je < 0 || ke < 0 || ie >= g.nx || je >= g.ny || ke >= g.nz) continue;
-            int e = ie + g.nx * (je + g.ny * ke);
-            d += __ldcg(a.s_e + e) * a.Md + __ldcg(a.k_e + e) * a.Kd;
+            d += __ldcg(a.r + ie + g.nx * (je + g.ny * ke));
           }
       if (a.surf && k == g.nz)
         for (int je = max(j - 1, 0); je <= min(j, g.ny - 1); ++je)
           for (int ie = max(i - 1, 0); ie <= min(i, g.nx - 1); ++ie)
             d += __ldcg(a.hf + ie + g.nx * je) * a.Mfx[0] * a.Mfy[0];
-      di = 1.0 / d;
     }
-    a.dinv[n] = di;
-    if (refined) a.dinv32[n] = (float)di;
+    if (refined)
+      a.dinv32[n] = d > 0.0 ? 1.0f / (float)d : 0.0f;
+    else
+      a.dinv[n] = d > 0.0 ? 1.0 / d : 0.0;
   });
   {
     // partials of A u_D (u holds the Dirichlet increments, 0 elsewhere) + K T^k
@@ -2309,7 +2313,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
         rr = ((Fn + Fa) + Fxn) - gather_partials((const double*)a.q, (const double*)a.X, nn, n,
                                                  low_faces(g, t, i, ly, lz));
       a.r[n] = rr;
-      v[0] += rr * rr * __ldcg(a.dinv + n);
+      if (!refined) v[0] += rr * rr * __ldcg(a.dinv + n);
       v[1] += rr * rr;
     });
     block_reduce_store<2>(v, a.red + RS_RZ0 * a.red_stride, a.red_stride, vg);
