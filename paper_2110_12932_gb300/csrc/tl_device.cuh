@@ -134,10 +134,10 @@ __device__ inline int* bar_ok_flag() {
 }
 
 // Each block keeps the generation of its next barrier in shared memory (thread
-// 0 reads and writes it): every use of a barrier releases exactly one
-// generation, and none is released before every block has arrived, so the
-// copy read once by bar_begin stays exact, and the arrival path needs no read
-// of the word.
+// 0 reads and writes it), read once per launch by bar_begin (at a launch's
+// start every reset of the previous launch has been applied): every use of a
+// barrier moves the generation by exactly one, so the copy stays exact, and
+// the arrival path needs no read of the word.
 __device__ inline unsigned int* bar_gen_local() {
   __shared__ unsigned int gen;
   return &gen;
@@ -147,26 +147,30 @@ __device__ inline void bar_begin(const Barrier& b) {
   __syncthreads();
 }
 
-// Waits (thread 0) until generation g is released; false if the time limit
+// Arrivals still counted in the word for barrier g (the block's local
+// generation) when the word reads w: the generation part of w may lag g by
+// the resets not yet applied, each of which will take nblk away.
+__device__ inline unsigned int bar_count(unsigned long long w, unsigned int g, int nblk) {
+  return (unsigned int)w - (g - (unsigned int)(w >> 32)) * (unsigned int)nblk;
+}
+
+// Waits (thread 0) until barrier g is complete; false if the time limit
 // passed (the arrival is withdrawn and the time-out recorded) or another block
-// recorded a time-out.  A block passes only once the generation has moved:
-// every arrival at the next barrier then comes after this release in the
-// word's order, so its count starts from zero.  Once every block has arrived
-// the release is on its way and the wait never gives up.  The status word and
-// the clock are looked at every 16th poll, or at every poll under a limit
-// shorter than a millisecond.
+// recorded a time-out.  The barrier is complete once its count reaches nblk
+// or its reset (generation g + 1) has been applied.  Once complete, the wait
+// never gives up.  The status word and the clock are looked at every 16th
+// poll, or at every poll under a limit shorter than a millisecond.
 __device__ inline bool bar_wait(const Barrier& b, unsigned int g, int nblk) {
   const unsigned long long t0 = global_ns();
   const bool every = b.limit_ns < 1000000ull;
   for (unsigned int poll = 1;; ++poll) {
     unsigned long long w = ld_acquire_u64(b.word);
-    if ((unsigned int)(w >> 32) != g) return true;
-    if ((every || (poll & 15) == 0) && (unsigned int)w != (unsigned int)nblk) {
+    if ((unsigned int)(w >> 32) == g + 1u || bar_count(w, g, nblk) >= (unsigned int)nblk) return true;
+    if (every || (poll & 15) == 0) {
       if (ld_volatile_i32(b.status) == ST_TIMEOUT) return false;
       if (global_ns() - t0 > b.limit_ns) {
         for (;;) {  // withdraw the arrival while the count is incomplete
-          if ((unsigned int)(w >> 32) != g) return true;
-          if ((unsigned int)w == (unsigned int)nblk) break;  // complete: wait for the release
+          if ((unsigned int)(w >> 32) == g + 1u || bar_count(w, g, nblk) >= (unsigned int)nblk) return true;
           const unsigned long long prev = atomicCAS(b.word, w, w - 1ull);
           if (prev == w) {
             atomicExch(b.status, (int)ST_TIMEOUT);
@@ -180,6 +184,11 @@ __device__ inline bool bar_wait(const Barrier& b, unsigned int g, int nblk) {
   }
 }
 
+// All arrivals are RMWs of one word (acquire-release), so a waiter that
+// acquires a value at or after the last arrival sees every block's writes.
+// Waiters pass as soon as the count is complete; the last arrival then resets
+// the count and moves the generation with one more add, which may land after
+// blocks have already arrived at the next barrier (bar_count accounts for it).
 __device__ inline bool grid_sync(const Barrier& b, const VGrid& vg) {
   int* s_ok = bar_ok_flag();
   __syncthreads();
@@ -189,7 +198,7 @@ __device__ inline bool grid_sync(const Barrier& b, const VGrid& vg) {
     // the block barrier above orders the block's writes before thread 0's
     // release (cumulativity)
     const unsigned long long old = atom_add_acqrel_u64(b.word, 1ull);
-    if ((unsigned int)old == (unsigned int)vg.nblk - 1u) {
+    if (bar_count(old, g, vg.nblk) == (unsigned int)vg.nblk - 1u) {
       atom_add_release_u64(b.word, (1ull << 32) - (unsigned long long)(unsigned int)vg.nblk);
     } else {
       ok = bar_wait(b, g, vg.nblk);

@@ -2126,7 +2126,7 @@ __device__ inline double elem_mean_sum(const double* T, const double* u, const G
 // a.precision at run time).  Each kernel instantiates only the paths it runs,
 // so the FP64 and FP32 loops do not share one register budget.
 template <int PMODE>
-__device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
+__device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, bool first_of_launch) {
   __shared__ __align__(16) unsigned char smem_raw[sizeof(ApplySmem<double>)];
   static_assert(sizeof(WideSmem) <= sizeof(ApplySmem<double>), "wide-tile buffers share the apply's shared memory");
   extern __shared__ __align__(16) unsigned char stage_raw[];  // STAGE_BYTES of staged inputs
@@ -2134,7 +2134,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
   ApplySmem<float>& sm32 = *reinterpret_cast<ApplySmem<float>*>(smem_raw);
   double* stage64 = reinterpret_cast<double*>(stage_raw);
   float* stage32 = reinterpret_cast<float*>(stage_raw);
-  bar_begin(a.bar);
+  if (first_of_launch) bar_begin(a.bar);  // later solves of a batch launch keep the block's copy
   if (ld_volatile_i32(a.bar.status) != 0) return;  // an earlier solve failed: leave state untouched
   Tracer tr{a.trace, vg.bid};
   tr.mark(TR_START);
@@ -2628,7 +2628,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg) {
 // own copy (the two-level path and the allocation-free single step).
 template <int PMODE>
 static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_kernel(const SolveArgs a) {
-  solve_body<PMODE>(a, VGrid{(int)blockIdx.x, (int)gridDim.x});
+  solve_body<PMODE>(a, VGrid{(int)blockIdx.x, (int)gridDim.x}, true);
 }
 
 // A batch of independent jobs in one cooperative launch: job j runs on the
@@ -2673,7 +2673,7 @@ static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_batch_kernel(cons
     __syncthreads();  // the previous solve is done with s_args
     for (int w = threadIdx.x; w < (int)(sizeof(SolveArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
     __syncthreads();
-    solve_body<PMODE>(s_args, vg);
+    solve_body<PMODE>(s_args, vg, sv == 0);
     if (sv + 1 < ns) {
       if (!grid_sync(s_args.bar, vg)) break;  // the next solve reads this one's results
       if (ld_volatile_i32(s_args.bar.status) != 0) break;
