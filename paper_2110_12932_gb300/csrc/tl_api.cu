@@ -255,9 +255,9 @@ constexpr int PC_TILE_STEPS = 2;
 Tiling pc_tiling(const Grid3& g, int nblk) {
   const int ntx = (g.nnx + 63) / 64;
   const int tx = (g.nnx + ntx - 1) / ntx;                 // at most 64 columns, two per thread
-  // rows: as many as the block's threads cover, the window ((tx + 2) x
-  // (ty + 2) nodes) at most PC_WN_MAX
-  const int ty = std::max(1, std::min({g.nny, NT / ((tx + 1) / 2), PC_WN_MAX / (tx + 2) - 2}));
+  // rows: as many as the block's threads cover, the stored window (rows of
+  // tx + 2 nodes at an even pitch, ty + 2 rows) at most PC_WN_MAX
+  const int ty = std::max(1, std::min({g.nny, NT / ((tx + 1) / 2), PC_WN_MAX / ((tx + 3) & ~1) - 2}));
   const int nty = (g.nny + ty - 1) / ty;
   const long long cols = (long long)ntx * nty;
   const long long B = std::max(1, nblk);

@@ -720,20 +720,31 @@ __device__ inline double surface_row(const Grid3& g, const double* hf, const dou
   return acc;
 }
 
-// Grid-wide loop over node rows (j, k): each warp takes whole rows, its lanes
-// walk i, so the only division is one per row.  body(n, i, j, k, row_low_faces).
+// floor(n / d) for 0 <= n < 2^31 and a runtime divisor d >= 1, as the high
+// 64 bits of n * M with M = floor(2^64 / d) + 1 (M = 2^64 / d when d is a
+// power of two): the error n (d - 2^64 mod d) / (d 2^64) < 1/d cannot carry
+// the quotient past an integer.  div_magic(d) computes M; d = 1 returns n.
+__device__ inline unsigned long long div_magic(int d) {
+  return d == 1 ? 0ull : ~0ull / (unsigned long long)d + 1ull;
+}
+__device__ inline int div_by(int n, int d, unsigned long long M) {
+  return d == 1 ? n : (int)__umul64hi((unsigned long long)n, M);
+}
+
+// Grid-wide loop over the nodes, flat (thread gtid takes nodes gtid, gtid +
+// gstride, ...): every lane has a node in every step (rows of nnx = 32 m + 1
+// nodes taken by warps would leave one lane busy in every fifth step).
+// body(n, i, j, k, ly, lz) with the node's low tile-face flags in y and z.
 template <class Body>
 __device__ inline void for_nodes(const Grid3& g, const Tiling& t, const VGrid& vg, Body body) {
-  const int lane = threadIdx.x & 31;
-  const int wg = (vg.bid * blockDim.x + threadIdx.x) >> 5;
-  const int nwg = (vg.nblk * blockDim.x) >> 5;
-  const int rows = g.nny * g.nnz;
-  for (int row = wg; row < rows; row += nwg) {
-    const int k = row / g.nny, j = row - k * g.nny;
+  const int nn = g.nnx * g.nny * g.nnz;
+  const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny), mz = div_magic(t.ez);
+  for (int n = vg.bid * blockDim.x + threadIdx.x; n < nn; n += vg.nblk * blockDim.x) {
+    const int row = div_by(n, g.nnx, mx), i = n - row * g.nnx;
+    const int k = div_by(row, g.nny, my), j = row - k * g.nny;
     const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
-    const bool lz = k > 0 && k < g.nz && (k % t.ez) == 0;
-    const int base = row * g.nnx;
-    for (int i = lane; i < g.nnx; i += 32) body(base + i, i, j, k, ly, lz);
+    const bool lz = k > 0 && k < g.nz && k - div_by(k, t.ez, mz) * t.ez == 0;
+    body(n, i, j, k, ly, lz);
   }
 }
 
@@ -1212,17 +1223,6 @@ struct CGVecs {
   const R* dinv;  // Jacobi inverse diagonal, 0 on Dirichlet nodes
 };
 
-// floor(n / d) for 0 <= n < 2^31 and a runtime divisor d >= 1, as the high
-// 64 bits of n * M with M = floor(2^64 / d) + 1 (M = 2^64 / d when d is a
-// power of two): the error n (d - 2^64 mod d) / (d 2^64) < 1/d cannot carry
-// the quotient past an integer.  div_magic(d) computes M; d = 1 returns n.
-__device__ inline unsigned long long div_magic(int d) {
-  return d == 1 ? 0ull : ~0ull / (unsigned long long)d + 1ull;
-}
-__device__ inline int div_by(int n, int d, unsigned long long M) {
-  return d == 1 ? n : (int)__umul64hi((unsigned long long)n, M);
-}
-
 template <typename R> struct Vec16;
 template <> struct Vec16<float> { using T = float4; };
 template <> struct Vec16<double> { using T = double2; };
@@ -1532,9 +1532,10 @@ __device__ int pcg2(const SolveArgs& a, const VGrid& vg, const Tiling& t, const 
 constexpr double PC_C = 0.2;
 // Preconditioner tiles: each thread owns two adjacent node columns of a tile
 // row, so a tile is at most 64 columns wide (32 threads per row) and holds at
-// most 2 NT columns; the host caps the tile height so that the window (halo
-// one node) has at most PC_WN_MAX nodes, the window of a 64 x 5 tile.
-constexpr int PC_CPT = 2;
+// most 2 NT columns; the host caps the tile height so that the stored window
+// (halo one node, rows at an even pitch) has at most PC_WN_MAX entries, the
+// window of a 64 x 5 tile.
+constexpr int PC_CPT = 2;  // the pass reads and writes column pairs
 constexpr int PC_WN_MAX = (64 + 2) * (NT / 32 + 2);
 constexpr int PC_WM = (PC_WN_MAX + NT - 1) / NT;
 
@@ -1896,9 +1897,12 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
   constexpr int NS = sizeof(R) == 4 ? 7 : 5, D = NS - 1;
   constexpr int SLOT_MAX = ((PC_WN_MAX + PC_CPT * NT) * 4 + PC_CPT * NT * (int)sizeof(R) + 15) / 16 * 16;
   static_assert(NS * SLOT_MAX <= STAGE_BYTES, "ring of the widest window fits the dynamic shared memory");
-  const int TX = tp.ex, TY = tp.ey, WXP = TX + 2, WN = (TX + 2) * (TY + 2);
+  // window rows of WXP nodes, stored with an even pitch WXPP so that a
+  // thread's column pair starts on 8 bytes (the pad column is never used)
+  const int TX = tp.ex, TY = tp.ey, WXP = TX + 2, WN = WXP * (TY + 2);
+  const int WXPP = (WXP + 1) & ~1, WNP = WXPP * (TY + 2);
   const int TXT = (TX + PC_CPT - 1) / PC_CPT;                        // threads per tile row
-  const int RB = ((WN + PC_CPT * NT) * 4 + 15) / 16 * 16;             // byte offset of r in a slot
+  const int RB = ((WNP + PC_CPT * NT) * 4 + 15) / 16 * 16;            // byte offset of r in a slot
   const int SB = (RB + PC_CPT * NT * (int)sizeof(R) + 15) / 16 * 16;  // slot bytes
   unsigned char* ring = reinterpret_cast<unsigned char*>(win_raw);
   const int ntiles = tp.ntx * tp.nty * tp.ntz;
@@ -1923,15 +1927,16 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
       tm[q] = tc[q] = sq_c[q] = 0.0f;
       r_c[q] = R(0);
     }
-    // this thread's window entries (w = tid + m NT) and their in-layer node
-    // offsets, -1 outside the mesh; fixed for the tile
-    int woff[PC_WM];
+    // this thread's window entries (w = tid + m NT): their in-layer node
+    // offsets (-1 outside the mesh) and places in the slot; fixed for the tile
+    int woff[PC_WM], soff[PC_WM];
 #pragma unroll
     for (int m = 0; m < PC_WM; ++m) {
       const int w = tid + m * NT;
       const int wy = w / WXP, wx = w - wy * WXP;
       const int gi = i0 - 1 + wx, gj = j0 - 1 + wy;
       woff[m] = (w < WN && gi >= 0 && gi < g.nnx && gj >= 0 && gj < g.nny) ? gi + g.nnx * gj : -1;
+      soff[m] = wy * WXPP + wx;
     }
     const int own_off = i0 + tx0 + g.nnx * j;
     // slot of layer L: async copies, zeros outside the mesh, one group per layer
@@ -1943,17 +1948,17 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
         for (int m = 0; m < PC_WM; ++m) {
           const int w = tid + m * NT;
           if (woff[m] >= 0)
-            cp_async<4>(buf + w, vL + woff[m]);
+            cp_async<4>(buf + soff[m], vL + woff[m]);
           else if (w < WN)
-            buf[w] = 0.0f;
+            buf[soff[m]] = 0.0f;
         }
         if (L >= k0 && L < k1) {
           const size_t n = (size_t)S * L + own_off;
 #pragma unroll
           for (int q = 0; q < PC_CPT; ++q)
             if (own[q]) {
-              cp_async<4>(buf + WN + q * NT + tid, c.sq + n + q);
-              cp_async<sizeof(R)>(reinterpret_cast<R*>(ring + slot * SB + RB) + q * NT + tid, c.r + n + q);
+              cp_async<4>(buf + WNP + PC_CPT * tid + q, c.sq + n + q);
+              cp_async<sizeof(R)>(reinterpret_cast<R*>(ring + slot * SB + RB) + PC_CPT * tid + q, c.r + n + q);
             }
         }
       }
@@ -1975,10 +1980,12 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
         for (int q = 0; q < PC_CPT; ++q) acc[q] = 0.0f;
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-          const float* row = buf + (ty + dy) * WXP + tx0;  // window columns tx0 .. tx0 + PC_CPT + 1
-          float rv[PC_CPT + 2];
-#pragma unroll
-          for (int e = 0; e < PC_CPT + 2; ++e) rv[e] = (tx0 + e < WXP) ? row[e] : 0.0f;
+          // window columns tx0 .. tx0 + 3 in two 8-byte loads (column tx0 + 3
+          // may be the pad, which only the unowned column tx0 + 1 = TX uses)
+          const float* row = buf + (ty + dy) * WXPP + tx0;
+          const float2 ra = *reinterpret_cast<const float2*>(row);
+          const float2 rb = *reinterpret_cast<const float2*>(row + 2);
+          const float rv[PC_CPT + 2] = {ra.x, ra.y, rb.x, rb.y};
 #pragma unroll
           for (int q = 0; q < PC_CPT; ++q) {
             const float t = fmaf(-cw, rv[q] + rv[q + 2], rv[q + 1]);
@@ -1999,12 +2006,17 @@ static __device__ __noinline__ R pc_apply(const Grid3 g, const Tiling tp, const 
           }
       }
       if (L >= k0 && L < k1) {
-#pragma unroll
-        for (int q = 0; q < PC_CPT; ++q)
-          if (own[q]) {
-            sq_c[q] = buf[WN + q * NT + tid];
-            r_c[q] = reinterpret_cast<const R*>(ring + sl * SB + RB)[q * NT + tid];
-          }
+        using V2 = typename Vec2<R>::T;  // the thread's pair of sq and of r
+        const float2 sqp = *reinterpret_cast<const float2*>(buf + WNP + PC_CPT * tid);
+        const V2 rp = *reinterpret_cast<const V2*>(reinterpret_cast<const R*>(ring + sl * SB + RB) + PC_CPT * tid);
+        if (own[0]) {
+          sq_c[0] = sqp.x;
+          r_c[0] = rp.x;
+        }
+        if (own[1]) {
+          sq_c[1] = sqp.y;
+          r_c[1] = rp.y;
+        }
       }
 #pragma unroll
       for (int q = 0; q < PC_CPT; ++q) {
@@ -2596,8 +2608,16 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, b
       const double ts = __ldcg(Tcoef + n);
       a.T_relax[n] = ts + 0.5 * (__ldcg(a.T_in + n) + __ldcg(a.u + n) - ts);
     }
-  } else {
-    for (int n = gtid; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
+  } else {  // four nodes per thread and step, loads first (element-wise, so T_out may be T_in)
+    int n = gtid;
+    for (; n + 3 * gstride < nn; n += 4 * gstride) {
+      double v[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v[m] = __ldcg(a.T_in + n + m * gstride) + __ldcg(a.u + n + m * gstride);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) a.T_out[n + m * gstride] = v[m];
+    }
+    for (; n < nn; n += gstride) a.T_out[n] = __ldcg(a.T_in + n) + __ldcg(a.u + n);
   }
   if (a.update_state)
     for_elems(g, vg, [&](int e, int ie, int je, int ke) {
