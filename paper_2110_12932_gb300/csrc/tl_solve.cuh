@@ -1093,45 +1093,44 @@ static __device__ __noinline__ float apply_wide_partials(const Grid3 g, const Ti
       // read after the block barrier)
       const float2 sv = *reinterpret_cast<const float2*>(&wc.sk[0][wy][c0]);
       const float2 kv = *reinterpret_cast<const float2*>(&wc.sk[1][wy][c0]);
-      const float s0 = sv.x, s1 = sv.y, k0 = kv.x, k1 = kv.y;
       const float2 ns = *reinterpret_cast<const float2*>(&sm.ZS[wy + 1][c0]);
       const float2 nd = *reinterpret_cast<const float2*>(&sm.ZD[wy + 1][c0]);
       const float s2 = sm.ZS[wy][c0 + 2], d2 = sm.ZD[wy][c0 + 2];
       const float ns2 = sm.ZS[wy + 1][c0 + 2], nd2 = sm.ZD[wy + 1][c0 + 2];
-      const float S0[3] = {zs0, zs1, s2}, D0[3] = {zd0, zd1, d2};
-      const float S1[3] = {ns.x, ns.y, ns2}, D1[3] = {nd.x, nd.y, nd2};
-      float Y[4][3];  // (y, z) mode m4 = my + 2 mz, per column
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Y[0][c] = S0[c] + S1[c];
-        Y[1][c] = S0[c] - S1[c];
-        Y[2][c] = D0[c] + D1[c];
-        Y[3][c] = D0[c] - D1[c];
-      }
-      float B[4][3];
+      // packed FP32 pairs (the same operations as one column at a time):
+      // columns (c0, c1) of the (y, z) modes, and per mode m4 the eigenvalue
+      // pairs (la, mb), (lb, ma) and the x-results of columns (c0, c0 + 2)
+      const float2 M1 = make_float2(-1.0f, -1.0f);
+      const float2 S0 = make_float2(zs0, zs1), D0 = make_float2(zd0, zd1);
+      const float2 Yp[4] = {__fadd2_rn(S0, ns), __ffma2_rn(ns, M1, S0), __fadd2_rn(D0, nd), __ffma2_rn(nd, M1, D0)};
+      const float Ys[4] = {s2 + ns2, s2 - ns2, d2 + nd2, d2 - nd2};
+      float2 Be[4];  // (B[m4][c0], B[m4][c0 + 2])
+      float Bm[4];   // B[m4][c0 + 1]
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) {
-        const float la = fmaf(s0, cf.mp[2 * m4], k0 * cf.kp[2 * m4]);
-        const float lb = fmaf(s0, cf.mp[2 * m4 + 1], k0 * cf.kp[2 * m4 + 1]);
-        const float ma = fmaf(s1, cf.mp[2 * m4], k1 * cf.kp[2 * m4]);
-        const float mb = fmaf(s1, cf.mp[2 * m4 + 1], k1 * cf.kp[2 * m4 + 1]);
-        const float a0 = Y[m4][0], a1 = Y[m4][1], a2 = Y[m4][2];
-        B[m4][0] = fmaf(la, a0, lb * a1);
-        B[m4][1] = fmaf(lb, a0, fmaf(la + ma, a1, mb * a2));
-        B[m4][2] = fmaf(mb, a1, ma * a2);
+        const float2 L1 = __ffma2_rn(sv, make_float2(cf.mp[2 * m4], cf.mp[2 * m4 + 1]),
+                                     __fmul2_rn(kv, make_float2(cf.kp[2 * m4], cf.kp[2 * m4 + 1])));  // (la, mb)
+        const float2 L2 = __ffma2_rn(sv, make_float2(cf.mp[2 * m4 + 1], cf.mp[2 * m4]),
+                                     __fmul2_rn(kv, make_float2(cf.kp[2 * m4 + 1], cf.kp[2 * m4])));  // (lb, ma)
+        const float a0 = Yp[m4].x, a1 = Yp[m4].y, a2 = Ys[m4];
+        Be[m4] = __ffma2_rn(L1, Yp[m4], __fmul2_rn(L2, make_float2(a1, a2)));
+        Bm[m4] = fmaf(L2.x, a0, fmaf(L1.x + L2.y, a1, L1.y * a2));
       }
+      const float2 R0S = __fadd2_rn(Be[0], Be[1]), R0D = __fadd2_rn(Be[2], Be[3]);
+      const float2 R1S = __ffma2_rn(Be[1], M1, Be[0]), R1D = __ffma2_rn(Be[3], M1, Be[2]);
       float r1s[3], r1d[3];
-      r0s0 = B[0][0] + B[1][0];
-      r0s1 = B[0][1] + B[1][1];
-      r0s2 = B[0][2] + B[1][2];
-      r0d0 = B[2][0] + B[3][0];
-      r0d1 = B[2][1] + B[3][1];
-      r0d2 = B[2][2] + B[3][2];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        r1s[c] = B[0][c] - B[1][c];
-        r1d[c] = B[2][c] - B[3][c];
-      }
+      r0s0 = R0S.x;
+      r0s1 = Bm[0] + Bm[1];
+      r0s2 = R0S.y;
+      r0d0 = R0D.x;
+      r0d1 = Bm[2] + Bm[3];
+      r0d2 = R0D.y;
+      r1s[0] = R1S.x;
+      r1s[1] = Bm[0] - Bm[1];
+      r1s[2] = R1S.y;
+      r1d[0] = R1D.x;
+      r1d[1] = Bm[2] - Bm[3];
+      r1d[2] = R1D.y;
       // column 2l + 2 is the next lane's first column (lane 31 keeps it: column AX)
       const float t0 = __shfl_up_sync(FULL, r0s2, 1), t1 = __shfl_up_sync(FULL, r0d2, 1);
       const float t2 = __shfl_up_sync(FULL, r1s[2], 1), t3 = __shfl_up_sync(FULL, r1d[2], 1);
