@@ -661,6 +661,49 @@ __device__ inline bool tile_touches_dirichlet(const Grid3& g, const Tiling& t, i
          d.box[0] <= d.box[1] && d.box[2] <= d.box[3] && d.box[4] <= d.box[5];
 }
 
+// The right-hand side's tiles of one block, at most RHS_ROUNDS of them
+// (ntiles <= RHS_ROUNDS nblk): the tiles are ranked with the ones that touch
+// Dirichlet nodes first (in tile order), then the others, and rank p goes to
+// round p / nblk and, in even rounds, to block p % nblk, in odd rounds to
+// block nblk - 1 - p % nblk.  Returns the block's shared list indexed by
+// round (-1: no tile in that round).  All threads of the block call it; each
+// scans a contiguous chunk of the tiles twice (count, then place) around one
+// block-wide prefix sum of the counts.
+constexpr int RHS_ROUNDS = 8;
+__device__ inline int* rhs_items(const Grid3& g, const Tiling& t, const DirSpec& d, int ntiles, const VGrid& vg) {
+  __shared__ int items[RHS_ROUNDS];
+  __shared__ int wsum[NT / 32 + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int chunk = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int c0 = min(tid * chunk, ntiles), c1 = min(c0 + chunk, ntiles);
+  int cnt = 0;
+  for (int tile = c0; tile < c1; ++tile) cnt += tile_touches_dirichlet(g, t, tile, d) ? 1 : 0;
+  // block-wide exclusive prefix sum of cnt (warp scans, then the warp totals)
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (tid < RHS_ROUNDS) items[tid] = -1;
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int before = 0, nd = 0;
+  for (int w = 0; w < nwarps; ++w) {
+    if (w < warp) before += wsum[w];
+    nd += wsum[w];
+  }
+  int rd = before + incl - cnt;  // rank of the chunk's first Dirichlet tile
+  int ri = nd + (c0 - (before + incl - cnt));  // position of its first other tile
+  for (int tile = c0; tile < c1; ++tile) {
+    const int p = tile_touches_dirichlet(g, t, tile, d) ? rd++ : ri++;
+    const int round = p / vg.nblk, off = p - round * vg.nblk;
+    if (((round & 1) ? vg.nblk - 1 - off : off) == vg.bid) items[round] = tile;
+  }
+  __syncthreads();
+  return items;
+}
+
 // Top-surface transfer term of one tile (the Robin condition of Section 3.1):
 // for every node of the tile's window on the plate's top layer, the tile's
 // share sum over its top faces f next to the node of
@@ -2286,7 +2329,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, b
     auto emit2 = [&](int n, int slot, double y, double) { store_partial(a.q, a.X, nn, n, slot, y, true); };
     const FinishArray<double, double> fin;
     auto no_lam_fetch = [](int, double*) {};
-    for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) {
+    auto rhs_tile = [&](int tile) {
       const TileBox tb = tile_box(g, t, tile);
       apply_tile<double, false, NRAW>(g, t, tile, sm64, stage64, StageArray<double, double>{a.T_in}, fin,
                                       no_lam_fetch, lam_k, emit1);
@@ -2299,6 +2342,17 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, b
                                         no_lam_fetch, lam_full, emit2);
         if (a.surf && tb.top) surface_partials<double>(g, tb, a.u, a.hf, a.Mfx, a.Mfy, a.q, a.X);
       }
+    };
+    if (ntiles <= RHS_ROUNDS * vg.nblk) {
+      // a tile with Dirichlet nodes costs two applies: deal the tiles with
+      // them first, then the others, in snake order over the blocks, so no
+      // block gets two heavy tiles while another has fewer tiles
+      int* items = rhs_items(g, t, a.dir, ntiles, vg);
+      const int rounds = (ntiles + vg.nblk - 1) / vg.nblk;
+      for (int m = 0; m < rounds; ++m)
+        if (items[m] >= 0) rhs_tile(items[m]);
+    } else {
+      for (int tile = vg.bid; tile < ntiles; tile += vg.nblk) rhs_tile(tile);
     }
   }
   if (!grid_sync(a.bar, vg)) return;
