@@ -778,16 +778,58 @@ __device__ inline int div_by(int n, int d, unsigned long long M) {
 // gstride, ...): every lane has a node in every step (rows of nnx = 32 m + 1
 // nodes taken by warps would leave one lane busy in every fifth step).
 // body(n, i, j, k, ly, lz) with the node's low tile-face flags in y and z.
+struct NodeIx {
+  int i, j, k;
+  bool ly, lz;  // on a low tile face in y / z
+};
+struct NodeDiv {
+  unsigned long long mx, my, mz;
+  __device__ NodeDiv(const Grid3& g, const Tiling& t)
+      : mx(div_magic(g.nnx)), my(div_magic(g.nny)), mz(div_magic(t.ez)) {}
+  __device__ NodeIx operator()(const Grid3& g, const Tiling& t, int n) const {
+    NodeIx x;
+    const int row = div_by(n, g.nnx, mx);
+    x.i = n - row * g.nnx;
+    x.k = div_by(row, g.nny, my);
+    x.j = row - x.k * g.nny;
+    x.ly = t.nty > 1 && x.j > 0 && x.j < g.ny && (x.j & (t.ey - 1)) == 0;
+    x.lz = x.k > 0 && x.k < g.nz && x.k - div_by(x.k, t.ez, mz) * t.ez == 0;
+    return x;
+  }
+};
 template <class Body>
 __device__ inline void for_nodes(const Grid3& g, const Tiling& t, const VGrid& vg, Body body) {
   const int nn = g.nnx * g.nny * g.nnz;
-  const unsigned long long mx = div_magic(g.nnx), my = div_magic(g.nny), mz = div_magic(t.ez);
+  const NodeDiv nd(g, t);
   for (int n = vg.bid * blockDim.x + threadIdx.x; n < nn; n += vg.nblk * blockDim.x) {
-    const int row = div_by(n, g.nnx, mx), i = n - row * g.nnx;
-    const int k = div_by(row, g.nny, my), j = row - k * g.nny;
-    const bool ly = t.nty > 1 && j > 0 && j < g.ny && (j & (t.ey - 1)) == 0;
-    const bool lz = k > 0 && k < g.nz && k - div_by(k, t.ez, mz) * t.ez == 0;
-    body(n, i, j, k, ly, lz);
+    const NodeIx x = nd(g, t, n);
+    body(n, x.i, x.j, x.k, x.ly, x.lz);
+  }
+}
+// Loads of a node pass batched: thread gtid takes the nodes gtid, gtid +
+// gstride, ... (the order of for_nodes) NODE_BATCH at a time, first
+// v = load(n, x) for all of them (the loads of one node do not wait for
+// another's stores; v is a small struct kept in registers), then store(n, v)
+// in node order.
+constexpr int NODE_BATCH = 4;
+template <class Load, class Store>
+__device__ inline void for_nodes_batched(const Grid3& g, const Tiling& t, const VGrid& vg, Load load, Store store) {
+  using V = decltype(load(0, NodeIx{}));
+  const int nn = g.nnx * g.nny * g.nnz;
+  const NodeDiv nd(g, t);
+  const int gstride = vg.nblk * blockDim.x;
+  for (int n0 = vg.bid * blockDim.x + threadIdx.x; n0 < nn; n0 += NODE_BATCH * gstride) {
+    V v[NODE_BATCH];
+#pragma unroll
+    for (int m = 0; m < NODE_BATCH; ++m) {
+      const int n = n0 + m * gstride;
+      if (n < nn) v[m] = load(n, nd(g, t, n));
+    }
+#pragma unroll
+    for (int m = 0; m < NODE_BATCH; ++m) {
+      const int n = n0 + m * gstride;
+      if (n < nn) store(n, v[m]);
+    }
   }
 }
 
@@ -2359,28 +2401,37 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, b
   tr.mark(TR_RHS);
   {
     double v[2] = {0.0, 0.0};
-    for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool ly, bool lz) {
-      double rr = 0.0;
-      double Fn = 0.0;
-      double Fa = 0.0;  // ambient part of the surface term: T_amb sum_f h_f int_f phi_n dA
-      if (k == g.nz) {  // the top-face load, kept for the energy account
-        Fn = top_load_tab(a.ld, g, a.G, i, j);
-        a.F[n - S * g.nz] = Fn;
-        if (a.surf) {
-          double hs = 0.0;
-          for (int je = max(j - 1, 0); je <= min(j, g.ny - 1); ++je)
-            for (int ie = max(i - 1, 0); ie <= min(i, g.nx - 1); ++ie) hs += __ldcg(a.hf + ie + g.nx * je);
-          Fa = a.T_amb * hs * (0.25 * g.hx * g.hy);
-        }
-      }
-      const double Fxn = a.Fx ? __ldcg(a.Fx + n) : 0.0;
-      if (!is_dir(g, a.dir, i, j, k))
-        rr = ((Fn + Fa) + Fxn) - gather_partials((const double*)a.q, (const double*)a.X, nn, n,
-                                                 low_faces(g, t, i, ly, lz));
-      a.r[n] = rr;
-      if (!refined) v[0] += rr * rr * __ldcg(a.dinv + n);
-      v[1] += rr * rr;
-    });
+    struct ResidV {
+      double rr, Fn, dinv;
+      bool top;
+    };
+    for_nodes_batched(
+        g, t, vg,
+        [&](int n, const NodeIx& x) {
+          ResidV o{0.0, 0.0, 0.0, x.k == g.nz};
+          double Fa = 0.0;  // ambient part of the surface term: T_amb sum_f h_f int_f phi_n dA
+          if (o.top) {      // the top-face load, kept for the energy account
+            o.Fn = top_load_tab(a.ld, g, a.G, x.i, x.j);
+            if (a.surf) {
+              double hs = 0.0;
+              for (int je = max(x.j - 1, 0); je <= min(x.j, g.ny - 1); ++je)
+                for (int ie = max(x.i - 1, 0); ie <= min(x.i, g.nx - 1); ++ie) hs += __ldcg(a.hf + ie + g.nx * je);
+              Fa = a.T_amb * hs * (0.25 * g.hx * g.hy);
+            }
+          }
+          const double Fxn = a.Fx ? __ldcg(a.Fx + n) : 0.0;
+          if (!is_dir(g, a.dir, x.i, x.j, x.k))
+            o.rr = ((o.Fn + Fa) + Fxn) - gather_partials((const double*)a.q, (const double*)a.X, nn, n,
+                                                         low_faces(g, t, x.i, x.ly, x.lz));
+          if (!refined) o.dinv = __ldcg(a.dinv + n);
+          return o;
+        },
+        [&](int n, const ResidV& o) {
+          if (o.top) a.F[n - S * g.nz] = o.Fn;
+          a.r[n] = o.rr;
+          if (!refined) v[0] += o.rr * o.rr * o.dinv;
+          v[1] += o.rr * o.rr;
+        });
     block_reduce_store<2>(v, a.red + RS_RZ0 * a.red_stride, a.red_stride, vg);
   }
   double tot0[2];
@@ -2547,14 +2598,30 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, b
     if (!grid_sync(a.bar, vg)) return;
     tr.mark(TR_OUTER_APPLY);
     double v[1] = {0.0};
-    for_nodes(g, t, vg, [&](int n, int i, int j, int k, bool ly, bool lz) {
-      if (is_dir(g, a.dir, i, j, k)) return;
-      double y = gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, i, ly, lz));
-      double rn = fma(-sigma, y, __ldcg(a.r + n));  // partials are of A d; the correction is sigma d
-      a.r[n] = rn;
-      a.u[n] = fma(sigma, (double)__ldcg(a.d32 + n), __ldcg(a.u + n));
-      v[0] += rn * rn;
-    });
+    struct CorrV {
+      double y, rk, uk;
+      float dk;
+      bool free;
+    };
+    for_nodes_batched(
+        g, t, vg,
+        [&](int n, const NodeIx& x) {
+          CorrV o{0.0, 0.0, 0.0, 0.0f, !is_dir(g, a.dir, x.i, x.j, x.k)};
+          if (o.free) {
+            o.y = gather_partials((const double*)a.q, (const double*)a.X, nn, n, low_faces(g, t, x.i, x.ly, x.lz));
+            o.rk = __ldcg(a.r + n);
+            o.uk = __ldcg(a.u + n);
+            o.dk = __ldcg(a.d32 + n);
+          }
+          return o;
+        },
+        [&](int n, const CorrV& o) {
+          if (!o.free) return;
+          const double rn = fma(-sigma, o.y, o.rk);  // partials are of A d; the correction is sigma d
+          a.r[n] = rn;
+          a.u[n] = fma(sigma, (double)o.dk, o.uk);
+          v[0] += rn * rn;
+        });
     block_reduce_store<1>(v, a.red + RS_RR * a.red_stride, a.red_stride, vg);
     double trr[1];
     if (!grid_sync_total<1>(a.bar, vg, a.red + RS_RR * a.red_stride, a.red_stride, trr)) return;
