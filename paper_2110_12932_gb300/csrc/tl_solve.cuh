@@ -810,23 +810,24 @@ __device__ inline void for_nodes(const Grid3& g, const Tiling& t, const VGrid& v
 // gstride, ... (the order of for_nodes) NODE_BATCH at a time, first
 // v = load(n, x) for all of them (the loads of one node do not wait for
 // another's stores; v is a small struct kept in registers), then store(n, v)
-// in node order.
+// in node order.  NB = 1 is the plain loop (the batched kernel, whose
+// register budget is tighter, measured slower with four).
 constexpr int NODE_BATCH = 4;
-template <class Load, class Store>
+template <int NB, class Load, class Store>
 __device__ inline void for_nodes_batched(const Grid3& g, const Tiling& t, const VGrid& vg, Load load, Store store) {
   using V = decltype(load(0, NodeIx{}));
   const int nn = g.nnx * g.nny * g.nnz;
   const NodeDiv nd(g, t);
   const int gstride = vg.nblk * blockDim.x;
-  for (int n0 = vg.bid * blockDim.x + threadIdx.x; n0 < nn; n0 += NODE_BATCH * gstride) {
-    V v[NODE_BATCH];
+  for (int n0 = vg.bid * blockDim.x + threadIdx.x; n0 < nn; n0 += NB * gstride) {
+    V v[NB];
 #pragma unroll
-    for (int m = 0; m < NODE_BATCH; ++m) {
+    for (int m = 0; m < NB; ++m) {
       const int n = n0 + m * gstride;
       if (n < nn) v[m] = load(n, nd(g, t, n));
     }
 #pragma unroll
-    for (int m = 0; m < NODE_BATCH; ++m) {
+    for (int m = 0; m < NB; ++m) {
       const int n = n0 + m * gstride;
       if (n < nn) store(n, v[m]);
     }
@@ -2221,7 +2222,7 @@ __device__ inline double elem_mean_sum(const double* T, const double* u, const G
 // PMODE: 0 plain FP64 solves only, 1 refined solves only, 2 either (chosen by
 // a.precision at run time).  Each kernel instantiates only the paths it runs,
 // so the FP64 and FP32 loops do not share one register budget.
-template <int PMODE>
+template <int PMODE, int NB = NODE_BATCH>
 __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, bool first_of_launch) {
   __shared__ __align__(16) unsigned char smem_raw[sizeof(ApplySmem<double>)];
   static_assert(sizeof(WideSmem) <= sizeof(ApplySmem<double>), "wide-tile buffers share the apply's shared memory");
@@ -2405,7 +2406,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, b
       double rr, Fn, dinv;
       bool top;
     };
-    for_nodes_batched(
+    for_nodes_batched<NB>(
         g, t, vg,
         [&](int n, const NodeIx& x) {
           ResidV o{0.0, 0.0, 0.0, x.k == g.nz};
@@ -2603,7 +2604,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VGrid vg, b
       float dk;
       bool free;
     };
-    for_nodes_batched(
+    for_nodes_batched<NB>(
         g, t, vg,
         [&](int n, const NodeIx& x) {
           CorrV o{0.0, 0.0, 0.0, 0.0f, !is_dir(g, a.dir, x.i, x.j, x.k)};
@@ -2813,7 +2814,7 @@ static __global__ void __launch_bounds__(NT, MIN_BLOCKS) solve_batch_kernel(cons
     __syncthreads();  // the previous solve is done with s_args
     for (int w = threadIdx.x; w < (int)(sizeof(SolveArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
     __syncthreads();
-    solve_body<PMODE>(s_args, vg, sv == 0);
+    solve_body<PMODE, 1>(s_args, vg, sv == 0);
     if (sv + 1 < ns) {
       if (!grid_sync(s_args.bar, vg)) break;  // the next solve reads this one's results
       if (ld_volatile_i32(s_args.bar.status) != 0) break;
